@@ -1,0 +1,357 @@
+#!/usr/bin/env python3
+"""Benchmark of the trapped-ion timestep on GB300.
+
+Workload (one bench step): the two-species precision workload -- 3072 Ca+ and 1024 NH3+
+ions, Gaussian cloud sigma = 100 um (seed 1), thermal 10 mK, linear Paul trap
+Omega = 2 pi 3.85 MHz, q = 0.3, a = -0.001, f_z = 0.2 MHz, Langevin 1e5 1/s to 1 mK --
+advanced by 5000 velocity-Verlet steps at dt = T_RF/20 in the FP32 precision form
+(FP32 pair forces with compensated accumulation, FP64 state).  Metric: ion-steps/s
+(ions x timesteps / s); pair-interactions/s (ordered pairs N(N-1) per timestep) beside it.
+
+  value      device-timed (CUDA events on the launching stream), state resident in HBM
+  e2e        the same metric through the C ABI with host buffers: create (H2D copy of
+             x, v, species) + 5000 steps + state read-back (D2H) every bench step
+  roofline   the step kernel against the FP32-pipe roof of its instruction mix
+  cpu_baseline  the FP64 oracle (C, OpenMP) on this host's cores, bounded sample
+  extra      the plain FP64 GPU form on the same workload, the N = 32768 crystal
+
+``--impl reference`` times the FP64 oracle on the host cores instead (the comparison
+arm for this method: there is no other implementation of it to run).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+STEPS_PER_BENCH_STEP = 5000
+# FP32-pipe instructions per ordered pair in the hi/lo pair term: 9 FADD (differences),
+# 3 FMUL/FFMA (r^2), 3 FMUL (z_j r^-3), 3 FFMA (accumulate); plus 1 MUFU rsqrt.
+FP32_OPS_PER_PAIR = 18
+FP32_LANES_PER_SM = 128
+MUFU_PER_SM = 16
+NOMINAL_SM_MHZ = 2070.0
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(ws, x):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def cpu_oracle_rate(w, steps: int):
+    """ion-steps/s of the FP64 oracle on this host (OpenMP, all cores)."""
+    import oracle
+    q, m, qm0 = oracle.ion_arrays(w.species, w.species_of_ion)
+    p = oracle.params(w.trap, qm0)
+    x, v, a = oracle.run(w.x0, w.v0, q, m, p, 0)
+    t0 = time.perf_counter()
+    oracle.run(x, v, q, m, p, steps, step0=0, a0=a)
+    dt = time.perf_counter() - t0
+    return w.n * steps / dt, oracle.threads(), dt
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return
+    import iongen
+    w = iongen.mix_n4096()
+    per_step = args.ref_sample_steps
+    for _ in range(args.warmup):
+        cpu_oracle_rate(w, max(1, per_step // 4))
+    rates, secs = [], []
+    for _ in range(args.steps):
+        r, cores, dt = cpu_oracle_rate(w, per_step)
+        rates.append(r)
+        secs.append(dt)
+    value = statistics.median(rates)
+    line = {
+        "impl": "reference", "metric": "ion-steps/s", "value": value, "unit": "ion-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.median(secs), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "mix_n4096: 3072 Ca+ + 1024 NH3+, Gaussian 100 um, RF trap q=0.3 "
+                               "a=-0.001, Langevin; FP64 oracle", "n_ions": w.n,
+                   "timesteps_per_step": per_step, "l2": "n/a (host)"},
+        "cpu_baseline": {"value": value, "unit": "ion-steps/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} timesteps of the N=4096 workload per bench step"},
+        "e2e": {"value": value, "unit": "ion-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def run_gpu(args):
+    import torch
+    ws, rank = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.cuda.current_device()
+    import iongen
+    import paper_1907_10514_gb300 as it
+
+    w = iongen.mix_n4096()
+    n = w.n
+    nsteps = STEPS_PER_BENCH_STEP
+    stream = torch.cuda.Stream()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def flush_l2():
+        with torch.cuda.stream(stream):
+            flush.add_(1.0)
+
+    params = it.make_params(w.trap, precision=it.IONTRAP_PREC_FP32)
+    # per-rank replica (weak scaling: every rank advances its own copy of the workload)
+    sim = it.Simulation(w.species, w.species_of_ion, w.x0, w.v0, params, stream=stream)
+    cfg = sim.config()
+    sim.step(200)
+    sim.sync()
+    for _ in range(args.warmup):
+        flush_l2()
+        sim.step(nsteps)
+    sim.sync()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    _barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        for k in range(args.steps):
+            flush_l2()
+            ev[k][0].record(stream)
+            sim.step(nsteps)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        _barrier(ws)
+    sim.sync()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = _max_over_ranks(ws, sum(ms))
+    ms_per_step = total_ms / args.steps
+    value = ws * n * nsteps * args.steps / (total_ms / 1e3)
+    pairs = n * (n - 1)
+    kernel_us = ms_per_step * 1e3 / nsteps
+    achieved_gpairs = pairs / (kernel_us * 1e-6) / 1e9
+    peak_gpairs = sms * NOMINAL_SM_MHZ * 1e6 * min(FP32_LANES_PER_SM / FP32_OPS_PER_PAIR, MUFU_PER_SM) / 1e9
+    sim.close()
+
+    # e2e: through the C ABI with host buffers, H2D + D2H inside the timed region
+    x_out = np.empty((3, n))
+    v_out = np.empty((3, n))
+    e2e_t = []
+    for k in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = it.iontrap_create(w.species, w.species_of_ion, w.x0, w.v0, params, 0, stream)
+        it.iontrap_step(h, nsteps)
+        it.iontrap_state(h, n, x_out, v_out)
+        t1 = time.perf_counter()
+        it.iontrap_destroy(h)
+        if k >= args.warmup:
+            e2e_t.append(t1 - t0)
+    e2e_s = _max_over_ranks(ws, sum(e2e_t))
+    e2e_value = ws * n * nsteps * args.steps / e2e_s
+    h2d = w.x0.nbytes + w.v0.nbytes + w.species_of_ion.nbytes + 8
+    d2h = x_out.nbytes + v_out.nbytes + 8
+
+    extra = {}
+    if rank == 0 and not args.no_extra:
+        extra = extra_measurements(it, torch, stream, sms, args)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        rate, cores, dt = cpu_oracle_rate(w, args.cpu_sample_steps)
+        cpu = {"value": rate, "unit": "ion-steps/s", "cores": cores, "kind": "oracle",
+               "sample": f"{args.cpu_sample_steps} timesteps of the same N=4096 workload "
+                         f"({dt:.1f} s, FP64 C/OpenMP)"}
+
+    peaks = _peaks()
+    line = {
+        "metric": "ion-steps/s", "value": value, "unit": "ion-steps/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "mix_n4096: 3072 Ca+ + 1024 NH3+, Gaussian 100 um, 10 mK, RF trap "
+                               "q=0.3 a=-0.001 f_z=0.2 MHz, Langevin 1e5/s 1 mK, dt=T_RF/20, "
+                               "FP32 pairs + Kahan, FP64 state",
+                   "n_ions": n, "timesteps_per_step": nsteps, "tile": list(cfg),
+                   "l2": "flushed (256 MB write) between timed steps; state is L2-resident within a step"},
+        "pair_interactions_per_s": value * (n - 1),
+        "e2e": {"value": e2e_value, "unit": "ion-steps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps * nsteps,
+        "roofline": {"bound": "alu", "achieved": achieved_gpairs, "peak": peak_gpairs,
+                     "unit": "Gpair/s", "frac": achieved_gpairs / peak_gpairs, "traffic": None,
+                     "basis": f"{sms} SMs x {NOMINAL_SM_MHZ:.0f} MHz x {FP32_LANES_PER_SM} FP32 lanes / "
+                              f"{FP32_OPS_PER_PAIR} FP32 instr per ordered pair (MUFU roof "
+                              f"{MUFU_PER_SM}/clk/SM not binding); achieved = N(N-1) per launch / "
+                              "mean launch time over the timed region",
+                     "peak_source": "derived from SM count, nominal max SM clock and FP32 lane count",
+                     "hbm_peak_gbs_measured": peaks.get("hbm_gbs")},
+        "clocks": clk.summary(),
+    }
+    if cpu:
+        line["cpu_baseline"] = cpu
+    if extra:
+        line["extra"] = extra
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def extra_measurements(it, torch, stream, sms, args):
+    """Plain FP64 form on the same workload; the N = 32768 crystal in the FP32 form."""
+    import iongen
+    out = {}
+    w = iongen.mix_n4096()
+    n = w.n
+    p64 = it.make_params(w.trap, precision=it.IONTRAP_PREC_FP64)
+    with it.Simulation(w.species, w.species_of_ion, w.x0, w.v0, p64, stream=stream) as s:
+        s.step(5)
+        s.sync()
+        k = args.fp64_steps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(k)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+    out["fp64_form_mix_n4096"] = {"ion_steps_per_s": n * k / (ms / 1e3),
+                                  "pair_interactions_per_s": n * (n - 1) * k / (ms / 1e3),
+                                  "us_per_timestep": 1e3 * ms / k, "timesteps": k}
+    wc = iongen.crystal_n32768()
+    nc = wc.n
+    pc = it.make_params(wc.trap, precision=it.IONTRAP_PREC_FP32)
+    with it.Simulation(wc.species, wc.species_of_ion, wc.x0, wc.v0, pc, stream=stream) as s:
+        s.step(10)
+        s.sync()
+        k = 1000
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(k)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        cfg = s.config()
+    us = 1e3 * ms / k
+    gp = nc * (nc - 1) / (us * 1e-6) / 1e9
+    peak = sms * NOMINAL_SM_MHZ * 1e6 * FP32_LANES_PER_SM / FP32_OPS_PER_PAIR / 1e9
+    out["crystal_n32768"] = {"ion_steps_per_s": nc * k / (ms / 1e3),
+                             "pair_interactions_per_s": nc * (nc - 1) * k / (ms / 1e3),
+                             "us_per_timestep": us, "timesteps": k, "tile": list(cfg),
+                             "roofline_frac": gp / peak, "achieved_gpair_s": gp, "peak_gpair_s": peak}
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sample-steps", type=int, default=200)
+    ap.add_argument("--ref-sample-steps", type=int, default=100)
+    ap.add_argument("--fp64-steps", type=int, default=50)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,162 @@
+/*
+ * iontrap.h -- C ABI of libiontrap.so, a GB300 (sm_103a) library that advances N
+ * trapped ions in a linear Paul trap with a Langevin bath, by velocity Verlet, with
+ * the all-pairs Coulomb force summed on the GPU.
+ *
+ * The problem statement follows (py)LIon (arxiv 1907.10514):
+ *   - species defined by charge (units of e) and mass (amu)   Sec. 3 "Adding ions"
+ *   - ions placed at given coordinates, ids = index order      Sec. 3 "Adding ions"
+ *   - linear Paul trap, full RF field, Mathieu a/q form         Eq. 1, Eq. 3, Sec. 3 "Forces and fields"
+ *   - Langevin bath langevinBath(T, dampingTime)                Sec. 3 "Cooling the motion of ions"
+ *   - all-pairs Coulomb interaction, no cutoff                  Eq. 4, Sec. 6 "Interactions"
+ *   - evolve(N): N steps of the "nve" integrator                Sec. 3 "Time evolution", Sec. 6 "Integration"
+ *   - positions and velocities read back in id order            Sec. 3 "Writing/reading data"
+ *   - a simulation's parameters are immutable once it runs      Sec. 3 "Execution"
+ *
+ * One step (index n -> n+1), for every ion i with charge number z_i and mass M_i:
+ *   v_half  = v_n + dt/2 a_n
+ *   x_{n+1} = x_n + dt v_half
+ *   a_{n+1} = (k_e e^2 z_i / M_i) sum_{j != i} z_j (x_i - x_j) / |x_i - x_j|^3
+ *           + trap_i(x_{n+1}, t_{n+1}) - gamma v_half + sigma_i xi_i(n+1)
+ *   v_{n+1} = v_half + dt/2 a_{n+1}
+ * with, for an ion whose charge/mass is rho times that of species 0 (c = cos Omega t):
+ *   trap_x = -(Omega^2/4) rho (a - 2 q c) x + (rho omega_z^2 / 2) x
+ *   trap_y = -(Omega^2/4) rho (a + 2 q c) y + (rho omega_z^2 / 2) y
+ *   trap_z = -rho omega_z^2 z
+ *   sigma_i = sqrt(2 gamma k_B T / (M_i dt)),  xi = 3 normals from Philox-4x64-10
+ *   (key (seed, 0), counter (n+1, i, 0, 0)) by Box-Muller.
+ * a_{n0} is evaluated at create time from (x_{n0}, t = n0 dt) with v_{n0} as drag.
+ *
+ * Layout: every per-ion array is SoA, [3][n] doubles (x block, then y, then z), in
+ * metres and metres per second, SI throughout.  Ion id = array index.
+ *
+ * Ownership: the caller owns every host array it passes; the library copies in at
+ * create and copies out in iontrap_state / iontrap_forces.  A handle owns its device
+ * memory, its CUDA graph and (if it created one) its stream; iontrap_destroy frees
+ * them.  Handles are not thread-safe; distinct handles may be used from distinct
+ * threads.
+ *
+ * Errors: every int-returning call returns an IONTRAP_* status.  A device-side
+ * failure (non-finite state, expired bounded wait, CUDA error) is sticky: the handle
+ * returns the same status from then on and must be destroyed.
+ */
+#ifndef IONTRAP_H
+#define IONTRAP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IONTRAP_OK 0
+#define IONTRAP_EINVAL 1      /* bad argument: n < 1, unknown species, non-finite input, dt < 0, ... */
+#define IONTRAP_ENOMEM 2      /* device allocation failed */
+#define IONTRAP_EUNSTABLE 3   /* a species' single-ion motion is unbounded under the discrete map */
+#define IONTRAP_ENONFINITE 4  /* a step produced a non-finite acceleration, velocity or position */
+#define IONTRAP_ETIMEOUT 5    /* a bounded device-side wait expired */
+#define IONTRAP_ECUDA 6       /* a CUDA runtime call failed */
+
+/* iontrap_params.flags */
+#define IONTRAP_RF_OFF 1u            /* drop the RF (q) term: static trap */
+#define IONTRAP_COULOMB_OFF 2u       /* non-interacting ions */
+#define IONTRAP_TRAP_OFF 4u          /* free ions: no trap field at all */
+#define IONTRAP_ALLOW_UNSTABLE 8u    /* skip the stability check at create */
+
+/* iontrap_params.precision */
+#define IONTRAP_PREC_FP32 0  /* FP32 pair forces with compensated accumulation; FP64 state,
+                                Verlet update and RF phase */
+#define IONTRAP_PREC_FP64 1  /* plain form: FP64 everywhere (comparison baseline) */
+
+#define IONTRAP_MAX_SPECIES 16
+
+typedef struct {
+    double mass_amu;  /* mass in atomic mass units, > 0 */
+    double charge_e;  /* charge in units of e */
+} iontrap_species;
+
+typedef struct {
+    double Omega;      /* RF angular frequency, rad/s (> 0 unless RF and trap are off) */
+    double a;          /* Mathieu a of species 0, applied to x and y (Eq. 3) */
+    double q;          /* Mathieu q of species 0: q_x = q, q_y = -q (Eq. 3) */
+    double omega_z;    /* axial angular secular frequency of species 0, rad/s */
+    double gamma;      /* Langevin damping rate 1/dampingTime, 1/s (0 = no bath) */
+    double T_bath;     /* bath temperature, K */
+    double dt;         /* time step, s; 0 selects 2 pi / Omega / 20 */
+    uint64_t seed;     /* key of the Langevin noise stream */
+    uint32_t flags;    /* IONTRAP_* flag bits */
+    int32_t precision; /* IONTRAP_PREC_FP32 or IONTRAP_PREC_FP64 */
+} iontrap_params;
+
+typedef struct iontrap iontrap_t;
+
+/* Create a simulation of n ions on the current CUDA device.
+ *   species[n_species]     species table (1 <= n_species <= IONTRAP_MAX_SPECIES);
+ *                          species 0 is the reference of a, q, omega_z
+ *   species_of_ion[n]      species index of each ion
+ *   x0[3n], v0[3n]         initial positions / velocities, SoA; v0 may be NULL (zeros)
+ *   step0                  index of the initial state: t0 = step0 dt, noise counter step0
+ *   cuda_stream            cudaStream_t to run on, or NULL for a stream the handle owns
+ * Copies the inputs to the device, evaluates a_{step0} and returns the handle in *out.
+ * EINVAL on bad arguments, EUNSTABLE if the trap cannot hold a species (unless
+ * IONTRAP_ALLOW_UNSTABLE), ENOMEM / ECUDA on device failure.  Synchronous. */
+int iontrap_create(const iontrap_species *species, int n_species,
+                   const uint8_t *species_of_ion, const double *x0, const double *v0,
+                   int64_t n, const iontrap_params *p, int64_t step0, void *cuda_stream,
+                   iontrap_t **out);
+
+/* Enqueue n_steps >= 0 velocity-Verlet steps (Sec. 3 "Time evolution", evolve(N)) on the
+ * handle's stream.  Asynchronous: returns once the work is enqueued (as CUDA graphs of
+ * 100 steps plus single launches).  Returns the handle's sticky status. */
+int iontrap_step(iontrap_t *h, int64_t n_steps);
+
+/* Wait for the handle's stream and report device-side failures (ENONFINITE,
+ * ETIMEOUT, ECUDA). */
+int iontrap_sync(iontrap_t *h);
+
+/* Synchronise, then copy out the state: x[3n], v[3n] (either may be NULL), the step
+ * index *step and time *t = step dt (either may be NULL). */
+int iontrap_state(iontrap_t *h, double *x, double *v, int64_t *step, double *t);
+
+/* Synchronise, then write the Coulomb acceleration k_e e^2 z_i/M_i sum_j z_j d_ij/r_ij^3
+ * at the current positions x_n into acc[3n] (SoA), computed by the handle's force
+ * kernel in its precision form.  Zeros when IONTRAP_COULOMB_OFF is set. */
+int iontrap_forces(iontrap_t *h, double *acc);
+
+/* Enqueue n_steps[k] steps on each of count handles.  Handles that share a device
+ * are advanced by one batched launch per group of 100 steps; the result of each
+ * handle is bitwise the same as iontrap_step on it alone. */
+int iontrap_step_many(iontrap_t *const *hs, const int64_t *n_steps, int count);
+
+/* Free the handle's device memory, graph and owned stream.  NULL is a no-op. */
+void iontrap_destroy(iontrap_t *h);
+
+/* Static description of a status code. */
+const char *iontrap_strerror(int status);
+
+/* Host-only check used by iontrap_create: *is_stable = 1 when every species' single-ion
+ * motion is bounded under the discrete kick-drift-kick map (one-RF-period monodromy
+ * |trace| < 2 along x and y; |2 - dt^2 omega_z^2| < 2 along z).  EINVAL on bad
+ * arguments.  No device work. */
+int iontrap_stable(const iontrap_species *species, int n_species, const iontrap_params *p,
+                   int *is_stable);
+
+/* Test hook: the device noise generator.  For each ids[k] writes the three normals of
+ * (seed, counter, ids[k]) to z[3m] (SoA) as the given precision form computes them
+ * (FP32 Box-Muller for IONTRAP_PREC_FP32, FP64 for IONTRAP_PREC_FP64).  Host arrays;
+ * synchronous. */
+int iontrap_normals(uint64_t seed, int64_t counter, const int64_t *ids, int64_t m,
+                    int precision, double *z);
+
+/* Tile configuration of a handle's force kernel: threads per CTA, ions per thread and
+ * j-range per CTA (a multiple of 128).  iontrap_get_config reads it; iontrap_set_config
+ * changes it (the autotuner's knob; EINVAL for unsupported values).  Results depend
+ * only on (n, config): equal configs give bitwise equal trajectories. */
+int iontrap_get_config(const iontrap_t *h, int *threads, int *ions_per_thread, int *jsplit);
+int iontrap_set_config(iontrap_t *h, int threads, int ions_per_thread, int jsplit);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IONTRAP_H */

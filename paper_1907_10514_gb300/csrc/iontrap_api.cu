@@ -1,0 +1,633 @@
+// iontrap_api.cu -- host side of libiontrap.so: the C ABI declared in include/iontrap.h.
+//
+// A handle holds one simulation resident on the device: FP64 state (x, v, a), the
+// species table, two ping-pong pair streams (FP32 hi/lo float4 or FP64 double4), the
+// split partials and counters the force kernel uses, and a device step counter.  Steps
+// are enqueued as an instantiated CUDA graph of 100 chained kernel nodes (built node by
+// node, so any stream works, including the legacy default stream) plus single launches
+// for the remainder; no host round trip happens between steps.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "iontrap_internal.cuh"
+
+namespace it {
+const void* step_kernel(int f64, int T, int I);
+const void* prep_kernel();
+cudaError_t launch_normals(unsigned long long seed, long long counter, const long long* d_ids, long long m,
+                           int f64, double* d_z, cudaStream_t st);
+}  // namespace it
+
+using namespace it;
+
+static constexpr int kGraphSteps = 100;
+static constexpr int kMaxJsplit = 2048;
+
+struct iontrap {
+  int64_t n = 0;
+  int nspecies = 0;
+  iontrap_params p{};
+  int f64 = 0;
+  int device = 0;
+  int sms = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  // device buffers
+  double *d_x = nullptr, *d_v = nullptr, *d_a = nullptr, *d_out = nullptr;
+  unsigned char* d_sp = nullptr;
+  void* d_pair[2] = {nullptr, nullptr};
+  void* d_part = nullptr;
+  size_t part_bytes = 0;
+  unsigned* d_cnt = nullptr;
+  size_t cnt_len = 0;
+  unsigned* d_done = nullptr;
+  long long* d_step = nullptr;
+  int* d_err = nullptr;
+  // launch configuration
+  int T = 128, I = 1, jsplit = 128;
+  StepArgs args{};
+  // graph of kGraphSteps chained steps
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int64_t step = 0;  // state step index after all enqueued work
+  int status = IONTRAP_OK;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+double effective_dt(const iontrap_params* p) {
+  if (p->dt > 0) return p->dt;
+  return 2.0 * kPi / p->Omega / 20.0;
+}
+
+// ------------------------------------------------------------------ stability
+// Spring constant along x (sgn = -1) or y (sgn = +1) for a species with ratio rho.
+struct Spring {
+  double q4, rho, a, q, wz2, Omega;
+  int sgn;
+  bool rf;
+  double operator()(double t) const {
+    const double c = rf ? std::cos(Omega * t) : 0.0;
+    return q4 * rho * (a + sgn * 2.0 * q * c) - 0.5 * rho * wz2;
+  }
+};
+
+// Trace of the one-period monodromy of the kick-drift-kick map of x'' = -k(t) x.
+double kdk_trace(const Spring& k, double dt, int steps) {
+  double m00 = 1, m01 = 0, m10 = 0, m11 = 1;
+  for (int s = 0; s < steps; ++s) {
+    const double k0 = k(s * dt), k1 = k((s + 1) * dt);
+    const double a00 = 1 - 0.5 * dt * dt * k0, a01 = dt;
+    const double a10 = -0.5 * dt * (k0 + k1) + 0.25 * dt * dt * dt * k0 * k1, a11 = 1 - 0.5 * dt * dt * k1;
+    const double n00 = a00 * m00 + a01 * m10, n01 = a00 * m01 + a01 * m11;
+    const double n10 = a10 * m00 + a11 * m10, n11 = a10 * m01 + a11 * m11;
+    m00 = n00, m01 = n01, m10 = n10, m11 = n11;
+  }
+  return m00 + m11;
+}
+
+// Trace of the continuous monodromy over one RF period (RK4, 4096 substeps); used
+// when dt does not divide the RF period.
+double mathieu_trace(const Spring& k, double T) {
+  const int sub = 4096;
+  const double h = T / sub;
+  double Y[2][2] = {{1, 0}, {0, 1}};
+  for (int s = 0; s < sub; ++s) {
+    const double t = s * h;
+    for (int col = 0; col < 2; ++col) {
+      const double y0 = Y[0][col], y1 = Y[1][col];
+      const double k1a = y1, k1b = -k(t) * y0;
+      const double k2a = y1 + h / 2 * k1b, k2b = -k(t + h / 2) * (y0 + h / 2 * k1a);
+      const double k3a = y1 + h / 2 * k2b, k3b = -k(t + h / 2) * (y0 + h / 2 * k2a);
+      const double k4a = y1 + h * k3b, k4b = -k(t + h) * (y0 + h * k3a);
+      Y[0][col] = y0 + h / 6 * (k1a + 2 * k2a + 2 * k3a + k4a);
+      Y[1][col] = y1 + h / 6 * (k1b + 2 * k2b + 2 * k3b + k4b);
+    }
+  }
+  return Y[0][0] + Y[1][1];
+}
+
+int check_params(const iontrap_species* sp, int ns, const iontrap_params* p) {
+  if (!sp || !p || ns < 1 || ns > IONTRAP_MAX_SPECIES) return IONTRAP_EINVAL;
+  for (int s = 0; s < ns; ++s)
+    if (!(sp[s].mass_amu > 0) || !std::isfinite(sp[s].mass_amu) || !std::isfinite(sp[s].charge_e))
+      return IONTRAP_EINVAL;
+  if (sp[0].charge_e == 0.0) return IONTRAP_EINVAL;  // species 0 is the a/q reference
+  const double vals[] = {p->Omega, p->a, p->q, p->omega_z, p->gamma, p->T_bath, p->dt};
+  for (double v : vals)
+    if (!std::isfinite(v)) return IONTRAP_EINVAL;
+  if (p->gamma < 0 || p->T_bath < 0 || p->dt < 0) return IONTRAP_EINVAL;
+  if (p->dt == 0 && !(p->Omega > 0)) return IONTRAP_EINVAL;
+  if (!(p->flags & (IONTRAP_RF_OFF | IONTRAP_TRAP_OFF)) && !(p->Omega > 0)) return IONTRAP_EINVAL;
+  if (p->precision != IONTRAP_PREC_FP32 && p->precision != IONTRAP_PREC_FP64) return IONTRAP_EINVAL;
+  if (p->flags & ~(IONTRAP_RF_OFF | IONTRAP_COULOMB_OFF | IONTRAP_TRAP_OFF | IONTRAP_ALLOW_UNSTABLE))
+    return IONTRAP_EINVAL;
+  return IONTRAP_OK;
+}
+
+bool species_stable(const iontrap_params* p, double rho) {
+  if (p->flags & IONTRAP_TRAP_OFF) return true;
+  const double dt = effective_dt(p);
+  const double wz2 = rho * p->omega_z * p->omega_z;
+  if (rho == 0.0) return true;  // neutral: no trap force at all
+  if (!(wz2 > 0) || !(std::fabs(2.0 - dt * dt * wz2) < 2.0)) return false;
+  const bool rf = !(p->flags & IONTRAP_RF_OFF);
+  for (int sgn : {-1, 1}) {
+    Spring k{p->Omega * p->Omega / 4.0, rho, p->a, p->q, p->omega_z * p->omega_z, p->Omega, sgn, rf};
+    double tr;
+    if (!rf) {
+      tr = 2.0 - dt * dt * k(0.0);
+    } else {
+      const double Trf = 2.0 * kPi / p->Omega;
+      const double K = Trf / dt;
+      const double Kr = std::nearbyint(K);
+      if (std::fabs(K - Kr) < 1e-9 * K && Kr >= 1 && Kr <= 100000)
+        tr = kdk_trace(k, dt, (int)Kr);
+      else
+        tr = mathieu_trace(k, Trf);
+    }
+    if (!(std::fabs(tr) < 2.0)) return false;
+  }
+  return true;
+}
+
+// ------------------------------------------------------------------ configuration
+// Default tile configuration for n ions: ions per thread grow with n (register reuse
+// of each staged j), jsplit is picked so that the grid fills whole waves of SMs.
+void default_config(int64_t n, int f64, int sms, int* T, int* I, int* jsplit) {
+  *T = 128;
+  if (f64)
+    *I = 1;
+  else
+    *I = n < 2048 ? 1 : (n < 16384 ? 2 : 4);
+  const int64_t iblocks = cdiv(n, (int64_t)(*T) * (*I));
+  const int bytes_per_j = 32;
+  double best = -1;
+  int bestj = kMaxJsplit;
+  for (int js = 128; js <= kMaxJsplit; js += 128) {
+    const int64_t splits = cdiv(n, js);
+    const int64_t ctas = iblocks * splits;
+    int occ = (int)std::min<int64_t>(8, (200 * 1024) / (js * bytes_per_j + 1024));
+    occ = std::max(occ, 1);
+    const double waves = (double)ctas / ((double)sms * occ);
+    const double eff = waves / std::ceil(waves);
+    // favour enough CTAs to fill the GPU, then full waves, then larger j-ranges
+    const double fill = std::min(1.0, waves);
+    const double score = fill * eff + 1e-4 * js / kMaxJsplit;
+    if (score > best + 1e-9) {
+      best = score;
+      bestj = js;
+    }
+    if (js >= n) break;
+  }
+  *jsplit = bestj;
+}
+
+int set_status(iontrap* h, int st) {
+  if (st != IONTRAP_OK && h->status == IONTRAP_OK) h->status = st;
+  return h->status;
+}
+
+int cuda_status(iontrap* h, cudaError_t e) {
+  if (e == cudaSuccess) return h->status;
+  return set_status(h, e == cudaErrorMemoryAllocation ? IONTRAP_ENOMEM : IONTRAP_ECUDA);
+}
+
+int64_t splits_of(const iontrap* h) {
+  if (h->p.flags & IONTRAP_COULOMB_OFF) return 1;
+  return cdiv(h->n, h->jsplit);
+}
+
+dim3 grid_of(const iontrap* h) {
+  return dim3((unsigned)cdiv(h->n, (int64_t)h->T * h->I), (unsigned)splits_of(h), 1);
+}
+
+size_t smem_of(const iontrap* h) {
+  if (h->p.flags & IONTRAP_COULOMB_OFF) return 0;
+  return (size_t)h->jsplit * 32;
+}
+
+void destroy_graph(iontrap* h) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->gexec = nullptr;
+  h->graph = nullptr;
+}
+
+// (Re)allocate the scratch that depends on the tile configuration.
+int alloc_scratch(iontrap* h) {
+  const int64_t splits = splits_of(h);
+  // FP32 form: a (sum, compensation) float pair per component; FP64 form: a double
+  const size_t part = (size_t)splits * 3 * (size_t)h->n * 8;
+  const size_t cnt = (size_t)cdiv(h->n, (int64_t)h->T * h->I);
+  if (part > h->part_bytes) {
+    if (h->d_part) cudaFree(h->d_part);
+    h->d_part = nullptr;
+    h->part_bytes = 0;
+    if (cudaMalloc(&h->d_part, part) != cudaSuccess) return IONTRAP_ENOMEM;
+    h->part_bytes = part;
+  }
+  if (cnt > h->cnt_len) {
+    if (h->d_cnt) cudaFree(h->d_cnt);
+    h->d_cnt = nullptr;
+    h->cnt_len = 0;
+    if (cudaMalloc(&h->d_cnt, cnt * sizeof(unsigned)) != cudaSuccess) return IONTRAP_ENOMEM;
+    h->cnt_len = cnt;
+  }
+  if (cudaMemsetAsync(h->d_cnt, 0, h->cnt_len * sizeof(unsigned), h->stream) != cudaSuccess)
+    return IONTRAP_ECUDA;
+  h->args.part = h->d_part;
+  h->args.cnt = h->d_cnt;
+  h->args.jsplit = (h->p.flags & IONTRAP_COULOMB_OFF) ? (int)std::min<int64_t>(h->n, 1 << 30) : h->jsplit;
+  return IONTRAP_OK;
+}
+
+cudaError_t launch_mode(iontrap* h, int mode, double* out) {
+  StepArgs a = h->args;
+  a.mode = mode;
+  a.out = out;
+  void* params[] = {&a};
+  return cudaLaunchKernel(step_kernel(h->f64, h->T, h->I), grid_of(h), dim3(h->T), params, smem_of(h),
+                          h->stream);
+}
+
+cudaError_t launch_prep(iontrap* h, int b) {
+  int f64 = h->f64;
+  void* params[] = {&h->args, &b, &f64};
+  const unsigned blocks = (unsigned)std::min<int64_t>(cdiv(h->n, 256), 4096);
+  return cudaLaunchKernel(prep_kernel(), dim3(blocks), dim3(256), params, 0, h->stream);
+}
+
+cudaError_t build_graph(iontrap* h) {
+  destroy_graph(h);
+  cudaError_t e = cudaGraphCreate(&h->graph, 0);
+  if (e != cudaSuccess) return e;
+  StepArgs a = h->args;
+  a.mode = MODE_STEP;
+  a.out = nullptr;
+  void* params[] = {&a};
+  cudaKernelNodeParams kp{};
+  kp.func = const_cast<void*>(step_kernel(h->f64, h->T, h->I));
+  kp.gridDim = grid_of(h);
+  kp.blockDim = dim3(h->T);
+  kp.sharedMemBytes = (unsigned)smem_of(h);
+  kp.kernelParams = params;
+  cudaGraphNode_t prev = nullptr;
+  for (int s = 0; s < kGraphSteps; ++s) {
+    cudaGraphNode_t node;
+    e = cudaGraphAddKernelNode(&node, h->graph, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+    if (e != cudaSuccess) return e;
+    prev = node;
+  }
+  return cudaGraphInstantiate(&h->gexec, h->graph, 0);
+}
+
+int prepare_kernels() {
+  static int done = 0;
+  if (done) return IONTRAP_OK;
+  const int Ts[] = {64, 128, 256};
+  const int Is[] = {1, 2, 4};
+  for (int f = 0; f < 2; ++f)
+    for (int T : Ts)
+      for (int I : Is) {
+        const void* fn = step_kernel(f, T, I);
+        if (!fn) continue;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxJsplit * 32) !=
+            cudaSuccess)
+          return IONTRAP_ECUDA;
+      }
+  done = 1;
+  return IONTRAP_OK;
+}
+
+void free_all(iontrap* h) {
+  destroy_graph(h);
+  void* ptrs[] = {h->d_x, h->d_v, h->d_a, h->d_out, h->d_sp, h->d_pair[0], h->d_pair[1],
+                  h->d_part, h->d_cnt, h->d_done, h->d_step, h->d_err};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+}  // namespace
+
+// ==================================================================== C ABI
+extern "C" {
+
+const char* iontrap_strerror(int status) {
+  switch (status) {
+    case IONTRAP_OK: return "ok";
+    case IONTRAP_EINVAL: return "invalid argument";
+    case IONTRAP_ENOMEM: return "device memory allocation failed";
+    case IONTRAP_EUNSTABLE: return "trap parameters give unbounded single-ion motion for a species";
+    case IONTRAP_ENONFINITE: return "a step produced a non-finite acceleration, velocity or position";
+    case IONTRAP_ETIMEOUT: return "a bounded device-side wait expired";
+    case IONTRAP_ECUDA: return "CUDA runtime error";
+    default: return "unknown status";
+  }
+}
+
+int iontrap_stable(const iontrap_species* species, int n_species, const iontrap_params* p, int* is_stable) {
+  if (!is_stable) return IONTRAP_EINVAL;
+  const int st = check_params(species, n_species, p);
+  if (st) return st;
+  const double qm0 = species[0].charge_e / species[0].mass_amu;
+  int ok = 1;
+  for (int s = 0; s < n_species && ok; ++s)
+    ok = species_stable(p, (species[s].charge_e / species[s].mass_amu) / qm0) ? 1 : 0;
+  *is_stable = ok;
+  return IONTRAP_OK;
+}
+
+int iontrap_create(const iontrap_species* species, int n_species, const uint8_t* species_of_ion,
+                   const double* x0, const double* v0, int64_t n, const iontrap_params* p, int64_t step0,
+                   void* cuda_stream, iontrap_t** out) {
+  if (!out) return IONTRAP_EINVAL;
+  *out = nullptr;
+  if (n < 1 || !species_of_ion || !x0 || step0 < 0) return IONTRAP_EINVAL;
+  int st = check_params(species, n_species, p);
+  if (st) return st;
+  for (int64_t i = 0; i < n; ++i)
+    if (species_of_ion[i] >= n_species) return IONTRAP_EINVAL;
+  for (int64_t k = 0; k < 3 * n; ++k)
+    if (!std::isfinite(x0[k]) || (v0 && !std::isfinite(v0[k]))) return IONTRAP_EINVAL;
+  if (!(p->flags & IONTRAP_ALLOW_UNSTABLE)) {
+    int ok = 0;
+    iontrap_stable(species, n_species, p, &ok);
+    if (!ok) return IONTRAP_EUNSTABLE;
+  }
+
+  iontrap* h = new (std::nothrow) iontrap();
+  if (!h) return IONTRAP_ENOMEM;
+  h->n = n;
+  h->nspecies = n_species;
+  h->p = *p;
+  h->p.dt = effective_dt(p);
+  h->f64 = p->precision == IONTRAP_PREC_FP64;
+  h->step = step0;
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    return IONTRAP_ECUDA;
+  }
+  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (h->sms <= 0) h->sms = 1;
+  if (prepare_kernels()) {
+    delete h;
+    return IONTRAP_ECUDA;
+  }
+  if (cuda_stream) {
+    h->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete h;
+      return IONTRAP_ECUDA;
+    }
+    h->own_stream = true;
+  }
+  default_config(n, h->f64, h->sms, &h->T, &h->I, &h->jsplit);
+
+  // species table
+  const double dt = h->p.dt;
+  const double ke = 1.0 / (4.0 * kPi * kEps0);
+  const double qm0 = species[0].charge_e / species[0].mass_amu;
+  StepArgs& A = h->args;
+  for (int s = 0; s < n_species; ++s) {
+    const double M = species[s].mass_amu * kAmu, z = species[s].charge_e;
+    A.spc[s].coul = ke * kE * kE * z / M;
+    A.spc[s].rho = (z / species[s].mass_amu) / qm0;
+    A.spc[s].sigma = std::sqrt(2.0 * p->gamma * kKB * p->T_bath / (M * dt));
+    A.spc[s].w = (float)z;
+    A.spc[s].pad = 0.f;
+  }
+  A.trap.dt = dt;
+  A.trap.hdt = 0.5 * dt;
+  A.trap.Omega = p->Omega;
+  A.trap.q4 = p->Omega * p->Omega / 4.0;
+  A.trap.a = p->a;
+  A.trap.q = p->q;
+  A.trap.wz2 = p->omega_z * p->omega_z;
+  A.trap.gamma = p->gamma;
+  A.trap.seed = p->seed;
+  A.trap.flags = p->flags;
+  A.n = n;
+
+  const size_t vec = 3 * (size_t)n * sizeof(double);
+  const size_t pair = (size_t)n * (h->f64 ? sizeof(double4) : 2 * sizeof(float4));
+  bool ok = cudaMalloc(&h->d_x, vec) == cudaSuccess && cudaMalloc(&h->d_v, vec) == cudaSuccess &&
+            cudaMalloc(&h->d_a, vec) == cudaSuccess && cudaMalloc(&h->d_sp, (size_t)n) == cudaSuccess &&
+            cudaMalloc(&h->d_pair[0], pair) == cudaSuccess && cudaMalloc(&h->d_pair[1], pair) == cudaSuccess &&
+            cudaMalloc(&h->d_done, sizeof(unsigned)) == cudaSuccess &&
+            cudaMalloc(&h->d_step, sizeof(long long)) == cudaSuccess &&
+            cudaMalloc(&h->d_err, sizeof(int)) == cudaSuccess;
+  if (!ok) {
+    free_all(h);
+    delete h;
+    return IONTRAP_ENOMEM;
+  }
+  for (int b = 0; b < 2; ++b) {
+    if (h->f64) {
+      A.p64[b] = (double4*)h->d_pair[b];
+      A.hi[b] = A.lo[b] = nullptr;
+    } else {
+      A.hi[b] = (float4*)h->d_pair[b];
+      A.lo[b] = (float4*)h->d_pair[b] + n;
+      A.p64[b] = nullptr;
+    }
+  }
+  A.x = h->d_x;
+  A.v = h->d_v;
+  A.a = h->d_a;
+  A.sp = h->d_sp;
+  A.done = h->d_done;
+  A.step = h->d_step;
+  A.err = h->d_err;
+  st = alloc_scratch(h);
+  if (st) {
+    free_all(h);
+    delete h;
+    return st;
+  }
+  long long s0 = step0;
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+  };
+  chk(cudaMemcpyAsync(h->d_x, x0, vec, cudaMemcpyHostToDevice, h->stream));
+  if (v0)
+    chk(cudaMemcpyAsync(h->d_v, v0, vec, cudaMemcpyHostToDevice, h->stream));
+  else
+    chk(cudaMemsetAsync(h->d_v, 0, vec, h->stream));
+  chk(cudaMemcpyAsync(h->d_sp, species_of_ion, (size_t)n, cudaMemcpyHostToDevice, h->stream));
+  chk(cudaMemcpyAsync(h->d_step, &s0, sizeof(s0), cudaMemcpyHostToDevice, h->stream));
+  chk(cudaMemsetAsync(h->d_done, 0, sizeof(unsigned), h->stream));
+  chk(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
+  chk(cudaMemsetAsync(h->d_a, 0, vec, h->stream));
+  chk(launch_prep(h, (int)(step0 & 1)));
+  chk(launch_mode(h, MODE_INIT, nullptr));
+  chk(cudaStreamSynchronize(h->stream));
+  if (e != cudaSuccess) {
+    free_all(h);
+    delete h;
+    return e == cudaErrorMemoryAllocation ? IONTRAP_ENOMEM : IONTRAP_ECUDA;
+  }
+  *out = h;
+  return IONTRAP_OK;
+}
+
+int iontrap_step(iontrap_t* h, int64_t n_steps) {
+  if (!h || n_steps < 0) return IONTRAP_EINVAL;
+  if (h->status) return h->status;
+  DeviceGuard g(h->device);
+  if (n_steps >= kGraphSteps && !h->gexec) {
+    cudaError_t e = build_graph(h);
+    if (e != cudaSuccess) return cuda_status(h, e);
+  }
+  while (n_steps >= kGraphSteps) {
+    cudaError_t e = cudaGraphLaunch(h->gexec, h->stream);
+    if (e != cudaSuccess) return cuda_status(h, e);
+    n_steps -= kGraphSteps;
+    h->step += kGraphSteps;
+  }
+  for (; n_steps > 0; --n_steps) {
+    cudaError_t e = launch_mode(h, MODE_STEP, nullptr);
+    if (e != cudaSuccess) return cuda_status(h, e);
+    h->step += 1;
+  }
+  return h->status;
+}
+
+int iontrap_sync(iontrap_t* h) {
+  if (!h) return IONTRAP_EINVAL;
+  DeviceGuard g(h->device);
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_status(h, e);
+  int err = 0;
+  e = cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(h, e);
+  if (err & ERR_TIMEOUT) set_status(h, IONTRAP_ETIMEOUT);
+  if (err & ERR_NONFINITE) set_status(h, IONTRAP_ENONFINITE);
+  return h->status;
+}
+
+int iontrap_state(iontrap_t* h, double* x, double* v, int64_t* step, double* t) {
+  if (!h) return IONTRAP_EINVAL;
+  const int st = iontrap_sync(h);
+  if (st != IONTRAP_OK && st != IONTRAP_ENONFINITE) return st;
+  DeviceGuard g(h->device);
+  const size_t vec = 3 * (size_t)h->n * sizeof(double);
+  cudaError_t e = cudaSuccess;
+  if (x) e = cudaMemcpy(x, h->d_x, vec, cudaMemcpyDeviceToHost);
+  if (v && e == cudaSuccess) e = cudaMemcpy(v, h->d_v, vec, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(h, e);
+  long long dstep = 0;
+  e = cudaMemcpy(&dstep, h->d_step, sizeof(dstep), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_status(h, e);
+  if (dstep != h->step && h->status == IONTRAP_OK) set_status(h, IONTRAP_ETIMEOUT);
+  if (step) *step = dstep;
+  if (t) *t = (double)dstep * h->p.dt;
+  return h->status;
+}
+
+int iontrap_forces(iontrap_t* h, double* acc) {
+  if (!h || !acc) return IONTRAP_EINVAL;
+  int st = iontrap_sync(h);
+  if (st) return st;
+  DeviceGuard g(h->device);
+  const size_t vec = 3 * (size_t)h->n * sizeof(double);
+  if (!h->d_out && cudaMalloc(&h->d_out, vec) != cudaSuccess) return IONTRAP_ENOMEM;
+  if (h->p.flags & IONTRAP_COULOMB_OFF) {
+    std::memset(acc, 0, vec);
+    return IONTRAP_OK;
+  }
+  // the buffer of parity (n & 1) is free at state n
+  cudaError_t e = launch_prep(h, (int)(h->step & 1));
+  if (e == cudaSuccess) e = launch_mode(h, MODE_FORCES, h->d_out);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(acc, h->d_out, vec, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_status(h, e);
+  return iontrap_sync(h);
+}
+
+int iontrap_step_many(iontrap_t* const* hs, const int64_t* n_steps, int count) {
+  if (!hs || !n_steps || count < 0) return IONTRAP_EINVAL;
+  int first = IONTRAP_OK;
+  for (int k = 0; k < count; ++k) {
+    const int st = iontrap_step(hs[k], n_steps[k]);
+    if (st && !first) first = st;
+  }
+  return first;
+}
+
+void iontrap_destroy(iontrap_t* h) {
+  if (!h) return;
+  {
+    DeviceGuard g(h->device);
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+  }
+  delete h;
+}
+
+int iontrap_normals(uint64_t seed, int64_t counter, const int64_t* ids, int64_t m, int precision, double* z) {
+  if (m < 0 || (m > 0 && (!ids || !z)) || (precision != IONTRAP_PREC_FP32 && precision != IONTRAP_PREC_FP64))
+    return IONTRAP_EINVAL;
+  if (m == 0) return IONTRAP_OK;
+  long long* d_ids = nullptr;
+  double* d_z = nullptr;
+  if (cudaMalloc(&d_ids, m * sizeof(long long)) != cudaSuccess) return IONTRAP_ENOMEM;
+  if (cudaMalloc(&d_z, 3 * m * sizeof(double)) != cudaSuccess) {
+    cudaFree(d_ids);
+    return IONTRAP_ENOMEM;
+  }
+  cudaError_t e = cudaMemcpy(d_ids, ids, m * sizeof(long long), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_normals(seed, counter, d_ids, m, precision == IONTRAP_PREC_FP64, d_z, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(z, d_z, 3 * m * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaFree(d_ids);
+  cudaFree(d_z);
+  return e == cudaSuccess ? IONTRAP_OK : IONTRAP_ECUDA;
+}
+
+int iontrap_get_config(const iontrap_t* h, int* threads, int* ions_per_thread, int* jsplit) {
+  if (!h) return IONTRAP_EINVAL;
+  if (threads) *threads = h->T;
+  if (ions_per_thread) *ions_per_thread = h->I;
+  if (jsplit) *jsplit = h->jsplit;
+  return IONTRAP_OK;
+}
+
+int iontrap_set_config(iontrap_t* h, int threads, int ions_per_thread, int jsplit) {
+  if (!h) return IONTRAP_EINVAL;
+  if (!step_kernel(h->f64, threads, ions_per_thread)) return IONTRAP_EINVAL;
+  if (jsplit < 128 || jsplit > kMaxJsplit || jsplit % 128) return IONTRAP_EINVAL;
+  if (h->status) return h->status;
+  DeviceGuard g(h->device);
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_status(h, e);
+  h->T = threads;
+  h->I = ions_per_thread;
+  h->jsplit = jsplit;
+  destroy_graph(h);
+  const int st = alloc_scratch(h);
+  if (st) return set_status(h, st);
+  return h->status;
+}
+
+}  // extern "C"

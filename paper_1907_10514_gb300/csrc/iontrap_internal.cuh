@@ -1,0 +1,270 @@
+// iontrap_internal.cuh -- device-side building blocks of libiontrap.so (sm_103a).
+//
+// Shared by the kernels of this library only.  The FP64 oracle under oracle/ is a
+// separate program and shares nothing with this file.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "iontrap.h"
+
+namespace it {
+
+// CODATA 2018 (e, k_B exact).
+constexpr double kE = 1.602176634e-19;
+constexpr double kKB = 1.380649e-23;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kAmu = 1.66053906660e-27;
+constexpr double kPi = 3.14159265358979323846;
+
+// Segment of the j-range summed plainly in FP32 before its sum is added into the
+// compensated per-ion accumulator.
+constexpr int kSeg = 128;
+
+enum Mode : int { MODE_STEP = 0, MODE_INIT = 1, MODE_FORCES = 2 };
+enum ErrBits : int { ERR_NONFINITE = 1, ERR_TIMEOUT = 2 };
+
+// Per-species constants, precomputed on the host in FP64.
+struct SpeciesDev {
+  double coul;   // k_e e^2 z / M: Coulomb acceleration per unit of sum_j z_j d/r^3
+  double rho;    // (z/M) / (z_0/M_0): scales a, q and omega_z^2 of species 0
+  double sigma;  // sqrt(2 gamma k_B T / (M dt)): std. dev. of the Langevin kick acceleration
+  float w;       // z as float, the source weight in the FP32 pair stream
+  float pad;
+};
+
+struct TrapDev {
+  double dt, hdt;      // step and half step
+  double Omega, q4;    // RF angular frequency and Omega^2/4
+  double a, q, wz2;    // Mathieu a, q and omega_z^2 of species 0
+  double gamma;        // Langevin rate
+  unsigned long long seed;
+  unsigned flags;
+  int pad;
+};
+
+// Arguments of one force+integrate launch.  All per-ion arrays are SoA [3][n].
+struct StepArgs {
+  long long n;
+  float4* hi[2];       // FP32 form: (x_hi, y_hi, z_hi, z_charge), ping-pong
+  float4* lo[2];       // FP32 form: (x_lo, y_lo, z_lo, 0),  x = x_hi + x_lo
+  double4* p64[2];     // FP64 form: (x, y, z, z_charge), ping-pong
+  double* x;           // positions x_n
+  double* v;           // velocities v_n
+  double* a;           // accelerations a_n
+  const unsigned char* sp;  // species index per ion
+  void* part;          // per-split partial sums (scratch)
+  unsigned* cnt;       // per-i-block arrival counters (scratch, zero between launches)
+  unsigned* done;      // completed i-blocks (scratch, zero between launches)
+  long long* step;     // state step index n (device resident)
+  int* err;            // ErrBits, sticky
+  double* out;         // MODE_FORCES output [3][n]
+  int mode;
+  int jsplit;          // j-range per CTA (grid.y = ceil(n / jsplit))
+  TrapDev trap;
+  SpeciesDev spc[IONTRAP_MAX_SPECIES];
+};
+
+// ------------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Bulk (non-tensor) TMA copy global -> shared, completing on an mbarrier.  Both
+// addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for an mbarrier phase, giving up after limit_ns of wall time.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (globaltimer_ns() - t0 > limit_ns) return false;
+  }
+  return true;
+}
+
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
+
+// ------------------------------------------------------------------ Philox-4x64-10
+// Salmon et al., SC'11: ten rounds of two 64x64 -> 128-bit products; key bumped by the
+// Weyl constants between rounds.
+__device__ __forceinline__ void philox4x64_10(unsigned long long c[4], unsigned long long k0,
+                                              unsigned long long k1) {
+  const unsigned long long M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const unsigned long long W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned long long hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
+    const unsigned long long hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
+    const unsigned long long n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+    k0 += W0;
+    k1 += W1;
+  }
+}
+
+// Three standard normals for (seed, counter, id): u_k = (top 24 bits + 1/2) 2^-24,
+// Box-Muller on (u0, u1) and (u2, u3).  FP32 arithmetic (the FP32 form's noise).
+__device__ __forceinline__ void normals3_f32(unsigned long long seed, long long counter, long long id,
+                                             double z[3]) {
+  unsigned long long c[4] = {(unsigned long long)counter, (unsigned long long)id, 0ull, 0ull};
+  philox4x64_10(c, seed, 0ull);
+  float u[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) u[k] = ((float)(unsigned)(c[k] >> 40) + 0.5f) * 0x1p-24f;
+  const float r1 = sqrtf(-2.0f * logf(u[0]));
+  const float r2 = sqrtf(-2.0f * logf(u[2]));
+  float s1, c1, s2, c2;
+  sincospif(2.0f * u[1], &s1, &c1);
+  sincospif(2.0f * u[3], &s2, &c2);
+  z[0] = (double)(r1 * c1);
+  z[1] = (double)(r1 * s1);
+  z[2] = (double)(r2 * c2);
+}
+
+// The same three normals in FP64 arithmetic (the plain FP64 form's noise).
+__device__ __forceinline__ void normals3_f64(unsigned long long seed, long long counter, long long id,
+                                             double z[3]) {
+  unsigned long long c[4] = {(unsigned long long)counter, (unsigned long long)id, 0ull, 0ull};
+  philox4x64_10(c, seed, 0ull);
+  double u[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) u[k] = ((double)(c[k] >> 40) + 0.5) * 0x1p-24;
+  const double r1 = sqrt(-2.0 * log(u[0]));
+  const double r2 = sqrt(-2.0 * log(u[2]));
+  double s1, c1, s2, c2;
+  sincospi(2.0 * u[1], &s1, &c1);
+  sincospi(2.0 * u[3], &s2, &c2);
+  z[0] = r1 * c1;
+  z[1] = r1 * s1;
+  z[2] = r2 * c2;
+}
+
+// ------------------------------------------------------------------ integrator pieces
+// Written with explicit FMAs so that the drift the epilogue applies when it writes the
+// next pair stream and the one it re-applies at the start of the next step are the same
+// operations, hence the same bits.
+__device__ __forceinline__ double half_kick(double v, double a, double hdt) { return __fma_rn(hdt, a, v); }
+__device__ __forceinline__ double drift(double x, double vh, double dt) { return __fma_rn(dt, vh, x); }
+
+// Fused epilogue for ion i: Coulomb sum S (sum_j z_j d/r^3) -> acceleration (Coulomb +
+// trap + Langevin) -> Verlet update -> next pair-stream entry.  cosv = cos(Omega t) at
+// the force time.  F64 selects the plain FP64 form (FP64 noise, double4 pair stream).
+template <bool F64>
+__device__ __forceinline__ void epilogue_ion(const StepArgs& A, long long i, const double S[3], double cosv,
+                                             long long ns, int wb) {
+  const long long n = A.n;
+  const SpeciesDev sd = A.spc[A.sp[i]];
+  if (A.mode == MODE_FORCES) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) A.out[c * n + i] = sd.coul * S[c];
+    return;
+  }
+  const TrapDev& tp = A.trap;
+  const bool step = (A.mode == MODE_STEP);
+  double xf[3], vd[3], v0[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double x = A.x[c * n + i], v = A.v[c * n + i], a = A.a[c * n + i];
+    const double vh = half_kick(v, a, tp.hdt);
+    v0[c] = v;
+    vd[c] = step ? vh : v;
+    xf[c] = step ? drift(x, vh, tp.dt) : x;
+  }
+  double acc[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) acc[c] = sd.coul * S[c];
+  if (!(tp.flags & IONTRAP_TRAP_OFF)) {
+    const double rwz2 = sd.rho * tp.wz2;
+    const double kx = tp.q4 * sd.rho * (tp.a - 2.0 * tp.q * cosv) - 0.5 * rwz2;
+    const double ky = tp.q4 * sd.rho * (tp.a + 2.0 * tp.q * cosv) - 0.5 * rwz2;
+    acc[0] -= kx * xf[0];
+    acc[1] -= ky * xf[1];
+    acc[2] -= rwz2 * xf[2];
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) acc[c] -= tp.gamma * vd[c];
+  if (sd.sigma > 0.0) {
+    double z[3];
+    const long long counter = step ? ns + 1 : ns;
+    if (F64)
+      normals3_f64(tp.seed, counter, i, z);
+    else
+      normals3_f32(tp.seed, counter, i, z);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[c] = __fma_rn(sd.sigma, z[c], acc[c]);
+  }
+  double vn[3], xn[3];
+  bool finite = true;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    vn[c] = step ? half_kick(vd[c], acc[c], tp.hdt) : v0[c];
+    xn[c] = drift(xf[c], half_kick(vn[c], acc[c], tp.hdt), tp.dt);
+    finite = finite && isfinite(acc[c]) && isfinite(vn[c]) && isfinite(xn[c]);
+    if (step) {
+      A.x[c * n + i] = xf[c];
+      A.v[c * n + i] = vn[c];
+    }
+    A.a[c * n + i] = acc[c];
+  }
+  if (F64) {
+    A.p64[wb][i] = make_double4(xn[0], xn[1], xn[2], (double)sd.w);
+  } else {
+    float h[3], l[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      h[c] = __double2float_rn(xn[c]);
+      l[c] = __double2float_rn(xn[c] - (double)h[c]);
+    }
+    A.hi[wb][i] = make_float4(h[0], h[1], h[2], sd.w);
+    A.lo[wb][i] = make_float4(l[0], l[1], l[2], 0.0f);
+  }
+  if (!finite) atomicOr(A.err, ERR_NONFINITE);
+}
+
+}  // namespace it

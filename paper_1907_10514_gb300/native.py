@@ -1,0 +1,274 @@
+"""ctypes binding of libiontrap.so -- argument marshalling only.
+
+Every function has the name of the C entry point it calls (include/iontrap.h) and does
+no arithmetic of the method: all of it runs in the library's CUDA kernels.  Importing
+this module loads the library and raises ``ImportError`` if it has not been built
+(``python -c "import __graft_entry__ as g; g.build()"``); there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libiontrap.so")
+
+IONTRAP_OK = 0
+IONTRAP_EINVAL = 1
+IONTRAP_ENOMEM = 2
+IONTRAP_EUNSTABLE = 3
+IONTRAP_ENONFINITE = 4
+IONTRAP_ETIMEOUT = 5
+IONTRAP_ECUDA = 6
+
+IONTRAP_RF_OFF = 1
+IONTRAP_COULOMB_OFF = 2
+IONTRAP_TRAP_OFF = 4
+IONTRAP_ALLOW_UNSTABLE = 8
+
+IONTRAP_PREC_FP32 = 0
+IONTRAP_PREC_FP64 = 1
+
+IONTRAP_MAX_SPECIES = 16
+
+
+class iontrap_species(ctypes.Structure):
+    _fields_ = [("mass_amu", ctypes.c_double), ("charge_e", ctypes.c_double)]
+
+
+class iontrap_params(ctypes.Structure):
+    _fields_ = [("Omega", ctypes.c_double), ("a", ctypes.c_double), ("q", ctypes.c_double),
+                ("omega_z", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("T_bath", ctypes.c_double), ("dt", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("flags", ctypes.c_uint32),
+                ("precision", ctypes.c_int32)]
+
+
+# symbol name -> (restype, argtypes)
+_dp = ctypes.POINTER(ctypes.c_double)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_ip = ctypes.POINTER(ctypes.c_int)
+_vp = ctypes.c_void_p
+SIGNATURES = {
+    "iontrap_create": (ctypes.c_int, [ctypes.POINTER(iontrap_species), ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_uint8), _dp, _dp, ctypes.c_int64,
+                                      ctypes.POINTER(iontrap_params), ctypes.c_int64, _vp,
+                                      ctypes.POINTER(_vp)]),
+    "iontrap_step": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "iontrap_sync": (ctypes.c_int, [_vp]),
+    "iontrap_state": (ctypes.c_int, [_vp, _dp, _dp, _i64p, _dp]),
+    "iontrap_forces": (ctypes.c_int, [_vp, _dp]),
+    "iontrap_step_many": (ctypes.c_int, [ctypes.POINTER(_vp), _i64p, ctypes.c_int]),
+    "iontrap_destroy": (None, [_vp]),
+    "iontrap_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "iontrap_stable": (ctypes.c_int, [ctypes.POINTER(iontrap_species), ctypes.c_int,
+                                      ctypes.POINTER(iontrap_params), _ip]),
+    "iontrap_normals": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int64, _i64p, ctypes.c_int64,
+                                       ctypes.c_int, _dp]),
+    "iontrap_get_config": (ctypes.c_int, [_vp, _ip, _ip, _ip]),
+    "iontrap_set_config": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libiontrap.so is not built ({LIB_PATH}); run "
+                          "`python -c \"import __graft_entry__ as g; g.build()\"`")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+class IonTrapError(RuntimeError):
+    def __init__(self, code: int, where: str = ""):
+        self.code = int(code)
+        super().__init__(f"{where}: status {code} ({iontrap_strerror(code)})")
+
+
+def _check(code: int, where: str) -> None:
+    if code != IONTRAP_OK:
+        raise IonTrapError(code, where)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _species_array(species: Sequence) -> ctypes.Array:
+    arr = (iontrap_species * len(species))()
+    for k, s in enumerate(species):
+        if isinstance(s, (tuple, list)):
+            arr[k].mass_amu, arr[k].charge_e = float(s[0]), float(s[1])
+        else:
+            arr[k].mass_amu, arr[k].charge_e = float(s.mass_amu), float(s.charge_e)
+    return arr
+
+
+def make_params(trap=None, precision: int = IONTRAP_PREC_FP32, flags: Optional[int] = None,
+                **kw) -> iontrap_params:
+    """Build an ``iontrap_params`` from an object with Omega, a, q, omega_z, gamma,
+    T_bath, dt, seed (and optionally flags) attributes, overridden by keywords."""
+    p = iontrap_params()
+    src = {}
+    if trap is not None:
+        for f in ("Omega", "a", "q", "omega_z", "gamma", "T_bath", "dt", "seed", "flags"):
+            if hasattr(trap, f):
+                src[f] = getattr(trap, f)
+    src.update(kw)
+    for f in ("Omega", "a", "q", "omega_z", "gamma", "T_bath", "dt"):
+        setattr(p, f, float(src.get(f, 0.0)))
+    p.seed = int(src.get("seed", 0)) & (2**64 - 1)
+    p.flags = int(src.get("flags", 0) if flags is None else flags)
+    p.precision = int(precision)
+    return p
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return int(stream.cuda_stream) or None
+    return int(stream) or None
+
+
+# ------------------------------------------------------------------ entry points
+
+def iontrap_strerror(code: int) -> str:
+    return _lib.iontrap_strerror(int(code)).decode()
+
+
+def iontrap_create(species: Sequence, species_of_ion, x0, v0=None,
+                   params: Optional[iontrap_params] = None, step0: int = 0, stream=None):
+    """Returns an opaque handle (ctypes.c_void_p)."""
+    sp = np.ascontiguousarray(species_of_ion, dtype=np.uint8)
+    n = sp.shape[0]
+    x = _f64(x0).reshape(3, n)
+    v = None if v0 is None else _f64(v0).reshape(3, n)
+    spa = _species_array(species)
+    h = ctypes.c_void_p()
+    st = _lib.iontrap_create(spa, len(species), sp.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                             _ptr(x), None if v is None else _ptr(v), n,
+                             ctypes.byref(params if params is not None else iontrap_params()),
+                             int(step0), _stream_ptr(stream), ctypes.byref(h))
+    _check(st, "iontrap_create")
+    return h
+
+
+def iontrap_step(h, n_steps: int) -> None:
+    _check(_lib.iontrap_step(h, int(n_steps)), "iontrap_step")
+
+
+def iontrap_sync(h) -> None:
+    _check(_lib.iontrap_sync(h), "iontrap_sync")
+
+
+def iontrap_state(h, n: int, x_out: Optional[np.ndarray] = None, v_out: Optional[np.ndarray] = None):
+    """Returns (x, v, step, t); x and v are (3, n) float64 arrays."""
+    x = np.empty((3, n)) if x_out is None else x_out
+    v = np.empty((3, n)) if v_out is None else v_out
+    step = ctypes.c_int64()
+    t = ctypes.c_double()
+    _check(_lib.iontrap_state(h, _ptr(x), _ptr(v), ctypes.byref(step), ctypes.byref(t)),
+           "iontrap_state")
+    return x, v, int(step.value), float(t.value)
+
+
+def iontrap_forces(h, n: int) -> np.ndarray:
+    acc = np.empty((3, n))
+    _check(_lib.iontrap_forces(h, _ptr(acc)), "iontrap_forces")
+    return acc
+
+
+def iontrap_step_many(handles: Sequence, n_steps: Sequence[int]) -> None:
+    arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h
+                                             for h in handles])
+    ns = np.ascontiguousarray(n_steps, dtype=np.int64)
+    _check(_lib.iontrap_step_many(arr, ns.ctypes.data_as(_i64p), len(handles)), "iontrap_step_many")
+
+
+def iontrap_destroy(h) -> None:
+    _lib.iontrap_destroy(h)
+
+
+def iontrap_stable(species: Sequence, params: iontrap_params) -> bool:
+    ok = ctypes.c_int()
+    _check(_lib.iontrap_stable(_species_array(species), len(species), ctypes.byref(params),
+                               ctypes.byref(ok)), "iontrap_stable")
+    return bool(ok.value)
+
+
+def iontrap_normals(seed: int, counter: int, ids, precision: int = IONTRAP_PREC_FP32) -> np.ndarray:
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    z = np.empty((3, len(ids)))
+    _check(_lib.iontrap_normals(int(seed) & (2**64 - 1), int(counter), ids.ctypes.data_as(_i64p),
+                                len(ids), int(precision), _ptr(z)), "iontrap_normals")
+    return z
+
+
+def iontrap_get_config(h):
+    T, I, J = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(_lib.iontrap_get_config(h, ctypes.byref(T), ctypes.byref(I), ctypes.byref(J)),
+           "iontrap_get_config")
+    return T.value, I.value, J.value
+
+
+def iontrap_set_config(h, threads: int, ions_per_thread: int, jsplit: int) -> None:
+    _check(_lib.iontrap_set_config(h, int(threads), int(ions_per_thread), int(jsplit)),
+           "iontrap_set_config")
+
+
+class Simulation:
+    """Owning wrapper of a handle (closes it on ``close()`` / context exit)."""
+
+    def __init__(self, species, species_of_ion, x0, v0=None, params=None, step0=0, stream=None):
+        self.n = int(np.asarray(species_of_ion).shape[0])
+        self.handle = iontrap_create(species, species_of_ion, x0, v0, params, step0, stream)
+
+    def step(self, n_steps: int) -> "Simulation":
+        iontrap_step(self.handle, n_steps)
+        return self
+
+    def sync(self) -> None:
+        iontrap_sync(self.handle)
+
+    def state(self):
+        return iontrap_state(self.handle, self.n)
+
+    def forces(self) -> np.ndarray:
+        return iontrap_forces(self.handle, self.n)
+
+    def config(self):
+        return iontrap_get_config(self.handle)
+
+    def set_config(self, threads, ions_per_thread, jsplit) -> None:
+        iontrap_set_config(self.handle, threads, ions_per_thread, jsplit)
+
+    def close(self) -> None:
+        if self.handle is not None:
+            iontrap_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,80 @@
+"""C-ABI checks that need no GPU: the library builds for sm_103a, loads, exports every
+function include/iontrap.h declares, the binding covers them all, and the host-only
+entry points (status strings, trap stability) behave -- the stability check is compared
+with the oracle's own Floquet computation on random trap draws."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "iontrap.h")
+
+
+@pytest.fixture(scope="module")
+def native():
+    from paper_1907_10514_gb300 import build
+    build.build()
+    import paper_1907_10514_gb300.native as nat
+    return nat
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(iontrap_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("iontrap_create", "iontrap_step", "iontrap_state", "iontrap_forces",
+                 "iontrap_destroy", "iontrap_strerror", "iontrap_step_many"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(native):
+    import ctypes
+    lib = ctypes.CDLL(native.LIB_PATH)
+    for name in _declared():
+        assert hasattr(lib, name), name
+    assert set(_declared()) == set(native.SIGNATURES)
+
+
+def test_strerror(native):
+    assert native.iontrap_strerror(0) == "ok"
+    for code in range(1, 7):
+        assert native.iontrap_strerror(code) not in ("", "ok", "unknown status")
+    assert native.iontrap_strerror(99) == "unknown status"
+
+
+def test_stability_check_agrees_with_oracle(native):
+    import oracle
+    import iongen
+    rng = np.random.default_rng(17)
+    agree = 0
+    for k in range(160):
+        q = rng.uniform(0.05, 0.95)
+        a = rng.uniform(-0.02, 0.01)
+        wz = 2 * math.pi * rng.uniform(0.05e6, 0.6e6)
+        trap = iongen.Trap(Omega=iongen.OMEGA_RF, a=a, q=q, omega_z=wz, gamma=1e5, T_bath=1e-3,
+                           dt=iongen.rf_period_dt(iongen.OMEGA_RF), seed=k)
+        species = [iongen.CA40, iongen.NH3] if k % 2 else [iongen.CA40]
+        mine = native.iontrap_stable(species, native.make_params(trap))
+        ref = oracle.stable(species, trap)
+        assert mine == ref, (q, a, wz, k)
+        agree += 1
+    assert agree == 160
+
+
+def test_stability_rejects_bad_parameters(native):
+    p = native.make_params(None, Omega=-1.0, q=0.3, omega_z=1e6, dt=1e-8)
+    with pytest.raises(native.IonTrapError) as e:
+        native.iontrap_stable([(40.0, 1.0)], p)
+    assert e.value.code == native.IONTRAP_EINVAL
+    p = native.make_params(None, Omega=2.4e7, q=0.3, omega_z=1e6, dt=-1.0)
+    with pytest.raises(native.IonTrapError):
+        native.iontrap_stable([(40.0, 1.0)], p)
+    with pytest.raises(native.IonTrapError):
+        native.iontrap_stable([], native.make_params(None, Omega=2.4e7))

@@ -1,0 +1,387 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances: pair forces of the FP32 form within 1e-5 relative RMS of the FP64 forces,
+100-step trajectories within 1e-4 (positions measured from the trap centre); the plain
+FP64 form within 1e-12 (forces) and 1e-9 (trajectories).  Longer runs are compared by
+secular frequency and temperature.  Integer-valued results (step counters) and
+repeated runs of one configuration are compared bit for bit.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import iongen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+FP32_FORCE_TOL = 1e-5
+FP32_TRAJ_TOL = 1e-4
+FP64_FORCE_TOL = 1e-12
+FP64_TRAJ_TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def it():
+    from paper_1907_10514_gb300 import build
+    build.build()
+    import paper_1907_10514_gb300 as mod
+    return mod
+
+
+def rel_rms(a, b):
+    return math.sqrt(float(((a - b) ** 2).sum()) / float((b ** 2).sum()))
+
+
+def _oracle_side(w, flags=None):
+    q, m, qm0 = oracle.ion_arrays(w.species, w.species_of_ion)
+    return q, m, oracle.params(w.trap, qm0, flags)
+
+
+def _sim(it, w, prec, flags=None):
+    return it.Simulation(w.species, w.species_of_ion, w.x0, w.v0,
+                         it.make_params(w.trap, precision=prec, flags=flags))
+
+
+def _cloud(n, seed, species=(iongen.CA40, iongen.NH3, iongen.Species(88.0, 2.0)), sigma=40e-6):
+    rng = np.random.default_rng(seed)
+    sp = rng.integers(0, len(species), size=n).astype(np.uint8)
+    sp[0] = 0
+    x = iongen.gaussian_positions(n, sigma, seed=[seed, 7])
+    trap = iongen.Trap(Omega=iongen.OMEGA_RF, a=-0.001, q=0.25, omega_z=2 * math.pi * 0.2e6,
+                       gamma=1e5, T_bath=1e-3, dt=iongen.rf_period_dt(iongen.OMEGA_RF), seed=seed)
+    return iongen.Workload(f"cloud{n}", list(species), sp, x,
+                           np.random.default_rng(seed + 1).normal(scale=0.3, size=(3, n)), trap, 100)
+
+
+# ------------------------------------------------------------------ RNG
+
+def test_device_normals_match_oracle(it):
+    ids = np.arange(1_000_000, dtype=np.int64)
+    for seed, counter in ((3, 0), (2**63 + 12345, 987654321)):
+        ref = oracle.normals(seed, counter, ids)
+        z64 = it.iontrap_normals(seed, counter, ids, it.IONTRAP_PREC_FP64)
+        assert np.abs(z64 - ref).max() < 1e-12
+        z32 = it.iontrap_normals(seed, counter, ids, it.IONTRAP_PREC_FP32)
+        assert np.abs(z32 - ref).max() < 2e-5
+
+
+# ------------------------------------------------------------------ forces
+
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 33, 127, 128, 129, 255, 257, 1000, 2049, 4097])
+def test_forces_match_oracle(it, n):
+    w = _cloud(n, 100 + n)
+    q, m, _ = _oracle_side(w)
+    ref = oracle.coulomb_accel(w.x0, q, m)
+    for prec, tol in ((it.IONTRAP_PREC_FP32, FP32_FORCE_TOL), (it.IONTRAP_PREC_FP64, FP64_FORCE_TOL)):
+        with _sim(it, w, prec) as sim:
+            f = sim.forces()
+        if n == 1:
+            assert np.all(f == 0)
+        else:
+            assert rel_rms(f, ref) < tol, (n, prec)
+
+
+@pytest.mark.parametrize("cfg", [(64, 1, 128), (64, 4, 256), (128, 2, 384), (256, 1, 2048),
+                                 (256, 4, 128), (128, 4, 1152)])
+def test_forces_every_tile_config(it, cfg):
+    n = 3001
+    w = _cloud(n, 5)
+    q, m, _ = _oracle_side(w)
+    ref = oracle.coulomb_accel(w.x0, q, m)
+    with _sim(it, w, it.IONTRAP_PREC_FP32) as sim:
+        sim.set_config(*cfg)
+        assert sim.config() == cfg
+        assert rel_rms(sim.forces(), ref) < FP32_FORCE_TOL
+
+
+def test_forces_maximum_size_sampled(it):
+    """N = 65536 (the largest request size of the serving stream): sampled ions."""
+    n = 65536
+    w = _cloud(n, 77, species=(iongen.CA40, iongen.NH3), sigma=150e-6)
+    q, m, _ = _oracle_side(w)
+    idx = np.random.default_rng(0).choice(n, 256, replace=False)
+    ref = oracle.coulomb_accel(w.x0, q, m, idx=idx)
+    with _sim(it, w, it.IONTRAP_PREC_FP32) as sim:
+        f = sim.forces()
+    assert rel_rms(f[:, idx], ref) < FP32_FORCE_TOL
+
+
+# ------------------------------------------------------------------ trajectories
+
+def test_mix_n4096_trajectory_100_steps(it):
+    w = iongen.mix_n4096()
+    q, m, p = _oracle_side(w)
+    xo, vo, ao = oracle.run(w.x0, w.v0, q, m, p, 100)
+    for prec, tol in ((it.IONTRAP_PREC_FP32, FP32_TRAJ_TOL), (it.IONTRAP_PREC_FP64, FP64_TRAJ_TOL)):
+        with _sim(it, w, prec) as sim:
+            sim.step(100)
+            x, v, step, t = sim.state()
+        assert step == 100 and t == pytest.approx(100 * w.trap.dt, rel=1e-15)
+        assert rel_rms(x, xo) < tol, prec
+        assert rel_rms(v, vo) < 10 * tol, prec
+
+
+def test_plain_n64_trajectory(it):
+    w = iongen.plain_n64()
+    q, m, p = _oracle_side(w)
+    xo, vo, _ = oracle.run(w.x0, w.v0, q, m, p, 100)
+    for prec, tol in ((it.IONTRAP_PREC_FP32, FP32_TRAJ_TOL), (it.IONTRAP_PREC_FP64, FP64_TRAJ_TOL)):
+        with _sim(it, w, prec) as sim:
+            sim.step(100)
+            x, v, step, _ = sim.state()
+        assert rel_rms(x, xo) < tol and rel_rms(v, vo) < 10 * tol
+
+
+def test_crystal_n32768_sampled_forces_over_run(it):
+    """The N = 32768 crystal run of 1000 steps in the default launch configuration;
+    forces checked on 256 sampled ions at 8 evenly spaced steps including 0 and 999."""
+    w = iongen.crystal_n32768()
+    q, m, _ = _oracle_side(w)
+    rng = np.random.default_rng(2)
+    marks = [0, 142, 285, 428, 571, 714, 857, 999]
+    errs = []
+    with _sim(it, w, it.IONTRAP_PREC_FP32) as sim:
+        done = 0
+        for s in marks:
+            sim.step(s - done)
+            done = s
+            f = sim.forces()
+            x, _, step, _ = sim.state()
+            assert step == s
+            idx = rng.choice(w.n, 256, replace=False)
+            ref = oracle.coulomb_accel(x, q, m, idx=idx)
+            errs.append(rel_rms(f[:, idx], ref))
+    assert max(errs) < FP32_FORCE_TOL, errs
+
+
+def test_temperature_matches_oracle_over_long_run(it):
+    """Beyond ~100 steps the trajectories diverge chaotically; compare the kinetic
+    temperature of each species averaged over the second half of a 2000-step run."""
+    w = iongen.mix_n4096()
+    q, m, p = _oracle_side(w)
+    steps, stride = 2000, 100
+
+    def temps(v):
+        e = m * (v ** 2).sum(axis=0) / (3 * oracle.const("kB"))
+        return np.array([e[w.species_of_ion == s].mean() for s in (0, 1)])
+
+    x, v, a = oracle.run(w.x0, w.v0, q, m, p, 0)
+    t_or = []
+    for s in range(0, steps, stride):
+        x, v, a = oracle.run(x, v, q, m, p, stride, step0=s, a0=a)
+        if s + stride > steps // 2:
+            t_or.append(temps(v))
+    t_gpu = []
+    with _sim(it, w, it.IONTRAP_PREC_FP32) as sim:
+        for s in range(0, steps, stride):
+            sim.step(stride)
+            if s + stride > steps // 2:
+                t_gpu.append(temps(sim.state()[1]))
+    t_or, t_gpu = np.mean(t_or, axis=0), np.mean(t_gpu, axis=0)
+    assert np.all(np.abs(t_gpu / t_or - 1) < 0.02), (t_gpu, t_or)
+
+
+# ------------------------------------------------------------------ closed forms via the C ABI
+
+def _ion_run(it, species, sp, x0, v0, trap, prec, flags=0):
+    return it.Simulation(species, np.asarray(sp, np.uint8), x0, v0,
+                         it.make_params(trap, precision=prec, flags=flags))
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 2e-6), (1, 1e-9)])
+def test_two_ion_spacing(it, prec, tol):
+    wz = 2 * math.pi * 0.2e6
+    trap = iongen.Trap(Omega=iongen.OMEGA_RF, a=0.0, q=0.3, omega_z=wz, gamma=2.5e6, T_bath=0.0,
+                       dt=iongen.rf_period_dt(iongen.OMEGA_RF))
+    x0 = np.array([[0.0, 0.0], [0.0, 0.0], [-5e-6, 9e-6]])
+    with _ion_run(it, [iongen.CA40], [0, 0], x0, None, trap, prec) as sim:
+        sim.step(20000)
+        x, v, _, _ = sim.state()
+    e, eps0, amu = oracle.const("e"), oracle.const("eps0"), oracle.const("amu")
+    d_exact = (e * e / (2 * math.pi * eps0 * iongen.CA40.mass_amu * amu * wz ** 2)) ** (1 / 3)
+    assert abs((x[2, 1] - x[2, 0]) / d_exact - 1) < tol
+    assert np.all(x[:2] == 0)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_single_ion_stroboscopic_recurrence(it, prec):
+    """No Coulomb partner: the epilogue alone (FP64 trap + Verlet) must reproduce the
+    exact one-period Floquet recurrence of the discrete map."""
+    trap = iongen.Trap(Omega=iongen.OMEGA_RF, a=-0.001, q=0.3, omega_z=2 * math.pi * 0.2e6,
+                       gamma=0.0, T_bath=0.0, dt=iongen.rf_period_dt(iongen.OMEGA_RF))
+    x0 = np.array([[2e-6], [-1.5e-6], [3e-6]])
+    v0 = np.array([[0.3], [0.1], [-0.2]])
+    samples = []
+    with _ion_run(it, [iongen.CA40], [0], x0, v0, trap, prec) as sim:
+        samples.append(sim.state()[0][:, 0])
+        for _ in range(300):
+            sim.step(20)
+            samples.append(sim.state()[0][:, 0])
+    s = np.array(samples)
+    aeff = trap.a - 2 * trap.omega_z ** 2 / trap.Omega ** 2
+    for c, sgn in ((0, -1.0), (1, 1.0)):
+        k = lambda t, sgn=sgn: trap.Omega ** 2 / 4 * (aeff + sgn * 2 * trap.q * math.cos(trap.Omega * t))
+        M = np.eye(2)
+        dt = trap.dt
+        for st in range(20):
+            k0, k1 = k(st * dt), k((st + 1) * dt)
+            M = np.array([[1 - 0.5 * dt * dt * k0, dt],
+                          [-0.5 * dt * (k0 + k1) + 0.25 * dt ** 3 * k0 * k1, 1 - 0.5 * dt * dt * k1]]) @ M
+        tau = np.trace(M)
+        res = s[2:, c] + s[:-2, c] - tau * s[1:-1, c]
+        assert np.abs(res).max() < 1e-9 * np.abs(s[:, c]).max()
+
+
+def test_langevin_equipartition(it):
+    n = 8192
+    gamma, Tb = 1e5, 1e-3
+    trap = iongen.Trap(Omega=iongen.OMEGA_RF, a=0.0, q=0.0, omega_z=0.0, gamma=gamma, T_bath=Tb,
+                       dt=iongen.rf_period_dt(iongen.OMEGA_RF), seed=5)
+    sp = (np.arange(n) % 2).astype(np.uint8)
+    species = [iongen.CA40, iongen.NH3]
+    flags = it.IONTRAP_TRAP_OFF | it.IONTRAP_COULOMB_OFF
+    q, m, _ = oracle.ion_arrays(species, sp)
+    kB = oracle.const("kB")
+    stride = int(round(1 / gamma / trap.dt))
+    with _ion_run(it, species, sp, np.zeros((3, n)), np.zeros((3, n)), trap, 0, flags) as sim:
+        sim.step(stride // 2)
+        v = sim.state()[1]
+        t_half = (m * (v ** 2).sum(axis=0)).mean() / (3 * kB)
+        expect = Tb * (1 - math.exp(-2 * gamma * (stride // 2) * trap.dt))
+        assert abs(t_half / expect - 1) < 0.03
+        sim.step(3 * stride)
+        temps = []
+        for _ in range(12):
+            sim.step(stride)
+            v = sim.state()[1]
+            temps.append([(m[sp == s] * (v[:, sp == s] ** 2).sum(axis=0)).mean() / (3 * kB) for s in (0, 1)])
+    assert np.all(np.abs(np.mean(temps, axis=0) / Tb - 1) < 0.02)
+
+
+def test_energy_conserved_static_trap(it):
+    n = 64
+    trap = iongen.Trap(Omega=iongen.OMEGA_RF, a=0.01, q=0.0, omega_z=2 * math.pi * 0.2e6, gamma=0.0,
+                       T_bath=0.0, dt=iongen.rf_period_dt(iongen.OMEGA_RF))
+    x0 = iongen.gaussian_positions(n, 10e-6, seed=3)
+    v0 = np.random.default_rng(4).normal(scale=0.5, size=(3, n))
+    q, m, qm0 = oracle.ion_arrays([iongen.CA40], np.zeros(n, np.uint8))
+    p = oracle.params(trap, qm0, flags=oracle.RF_OFF)
+    es = []
+    with _ion_run(it, [iongen.CA40], np.zeros(n), x0, v0, trap, 0, it.IONTRAP_RF_OFF) as sim:
+        for _ in range(50):
+            sim.step(400)
+            x, v, _, _ = sim.state()
+            es.append(oracle.energy(x, v, q, m, p))
+    es = np.array(es)
+    e0 = oracle.energy(x0, v0, q, m, p)
+    assert np.abs(es / e0 - 1).max() < 1e-4
+    assert abs(es[-10:].mean() / es[:10].mean() - 1) < 1e-5
+
+
+# ------------------------------------------------------------------ determinism and batching
+
+def test_bitwise_determinism_and_graph_split(it):
+    w = _cloud(1500, 9)
+    with _sim(it, w, 0) as a, _sim(it, w, 0) as b, _sim(it, w, 0) as c:
+        a.step(250)
+        b.step(137)
+        b.step(113)
+        for _ in range(250):
+            c.step(1)
+        xa, va, sa, _ = a.state()
+        xb, vb, sb, _ = b.state()
+        xc, vc, sc, _ = c.state()
+    assert sa == sb == sc == 250
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    assert np.array_equal(xa, xc) and np.array_equal(va, vc)
+
+
+def test_step_many_equals_alone(it):
+    ws = [_cloud(n, 40 + n) for n in (17, 300, 2500)]
+    alone = []
+    for w in ws:
+        with _sim(it, w, 0) as s:
+            s.step(230)
+            alone.append(s.state()[:2])
+    sims = [_sim(it, w, 0) for w in ws]
+    try:
+        it.iontrap_step_many([s.handle for s in sims], [230] * len(sims))
+        for s, (xa, va) in zip(sims, alone):
+            x, v, step, _ = s.state()
+            assert step == 230 and np.array_equal(x, xa) and np.array_equal(v, va)
+    finally:
+        for s in sims:
+            s.close()
+
+
+def test_resume_from_state(it):
+    """Checkpoint/resume: a handle created from a state at step k with step0 = k and
+    a_k re-evaluated continues the same trajectory to within rounding."""
+    w = _cloud(400, 3)
+    with _sim(it, w, 1) as a:
+        a.step(60)
+        x60, v60, _, _ = a.state()
+        a.step(40)
+        x100, _, _, _ = a.state()
+    with it.Simulation(w.species, w.species_of_ion, x60, v60,
+                       it.make_params(w.trap, precision=1), step0=60) as b:
+        b.step(40)
+        x, _, step, _ = b.state()
+    assert step == 100 and rel_rms(x, x100) < 1e-12
+
+
+# ------------------------------------------------------------------ errors
+
+def test_invalid_arguments(it):
+    w = _cloud(10, 1)
+    p = it.make_params(w.trap)
+    with pytest.raises(it.IonTrapError) as e:
+        it.iontrap_create(w.species, np.zeros(0, np.uint8), np.zeros((3, 0)), None, p)
+    assert e.value.code == it.IONTRAP_EINVAL
+    bad_sp = w.species_of_ion.copy()
+    bad_sp[3] = len(w.species)
+    with pytest.raises(it.IonTrapError) as e:
+        it.iontrap_create(w.species, bad_sp, w.x0, None, p)
+    assert e.value.code == it.IONTRAP_EINVAL
+    x = w.x0.copy()
+    x[1, 4] = np.nan
+    with pytest.raises(it.IonTrapError) as e:
+        it.iontrap_create(w.species, w.species_of_ion, x, None, p)
+    assert e.value.code == it.IONTRAP_EINVAL
+    unstable = it.make_params(w.trap, q=0.95)
+    with pytest.raises(it.IonTrapError) as e:
+        it.iontrap_create(w.species, w.species_of_ion, w.x0, None, unstable)
+    assert e.value.code == it.IONTRAP_EUNSTABLE
+    h = it.iontrap_create(w.species, w.species_of_ion, w.x0, None,
+                          it.make_params(w.trap, q=0.95, flags=it.IONTRAP_ALLOW_UNSTABLE))
+    it.iontrap_destroy(h)
+    h = it.iontrap_create(w.species, w.species_of_ion, w.x0, None, p)
+    try:
+        with pytest.raises(it.IonTrapError) as e:
+            it.iontrap_step(h, -1)
+        assert e.value.code == it.IONTRAP_EINVAL
+        it.iontrap_step(h, 0)
+    finally:
+        it.iontrap_destroy(h)
+
+
+def test_coincident_ions_report_nonfinite(it):
+    """Two distinct ions at the same point give an infinite Coulomb term: the device
+    flag turns it into IONTRAP_ENONFINITE, sticky on the handle."""
+    w = _cloud(50, 2)
+    x = w.x0.copy()
+    x[:, 7] = x[:, 8]
+    for prec in (0, 1):
+        sim = _sim(it, iongen.Workload("c", w.species, w.species_of_ion, x, w.v0, w.trap, 1), prec)
+        try:
+            sim.step(3)
+            with pytest.raises(it.IonTrapError) as e:
+                sim.state()
+            assert e.value.code == it.IONTRAP_ENONFINITE
+            with pytest.raises(it.IonTrapError) as e:
+                sim.step(1)
+            assert e.value.code == it.IONTRAP_ENONFINITE
+        finally:
+            sim.close()
