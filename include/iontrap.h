@@ -24,7 +24,8 @@
  *   trap_y = -(Omega^2/4) rho (a + 2 q c) y + (rho omega_z^2 / 2) y
  *   trap_z = -rho omega_z^2 z
  *   sigma_i = sqrt(2 gamma k_B T / (M_i dt)),  xi = 3 normals from Philox-4x64-10
- *   (key (seed, 0), counter (n+1, i, 0, 0)) by Box-Muller.
+ *   (key (seed, 0), counter (n+1, i, 0, 0)) by Box-Muller on the uniforms
+ *   (top 23 bits of each 64-bit word + 1/2) 2^-23.
  * a_{n0} is evaluated at create time from (x_{n0}, t = n0 dt) with v_{n0} as drag.
  *
  * Layout: every per-ion array is SoA, [3][n] doubles (x block, then y, then z), in
@@ -122,6 +123,18 @@ int iontrap_state(iontrap_t *h, double *x, double *v, int64_t *step, double *t);
  * at the current positions x_n into acc[3n] (SoA), computed by the handle's force
  * kernel in its precision form.  Zeros when IONTRAP_COULOMB_OFF is set. */
 int iontrap_forces(iontrap_t *h, double *acc);
+
+/* Checkpoint: synchronise, then copy out the full state x_n[3n], v_n[3n], a_n[3n]
+ * (any may be NULL) and the step index.  Together with iontrap_restore it resumes a run
+ * bit for bit (the paper only dumps x and v, Sec. 3 "Writing/reading data"; a_n is
+ * needed too because the Langevin drag of a_n used v_{n-1/2}, not v_n). */
+int iontrap_checkpoint(iontrap_t *h, double *x, double *v, double *a, int64_t *step);
+
+/* Restore: overwrite the state of a handle with a checkpoint (x, v, a: 3n each, all
+ * required; step >= 0) taken from a simulation with the same ions and parameters.
+ * Synchronous.  EINVAL on NULL or non-finite input; the handle's sticky status
+ * otherwise. */
+int iontrap_restore(iontrap_t *h, const double *x, const double *v, const double *a, int64_t step);
 
 /* Enqueue n_steps[k] steps on each of count handles.  Handles that share a device
  * are advanced by one batched launch per group of 100 steps; the result of each

@@ -24,7 +24,7 @@
  *
  *   sigma_i = sqrt(2 gamma k_B T / (M_i dt)); xi = three standard normals drawn by
  *   Box-Muller from Philox-4x64-10 (Salmon et al., SC'11) with key (seed, 0) and
- *   counter (n, i, 0, 0).
+ *   counter (n, i, 0, 0), on the uniforms (top 23 bits + 1/2) 2^-23.
  *
  *   one step, velocity Verlet ("nve", Sec. 6 "Integration"), kick-drift-kick:
  *     v_half = v_n + dt/2 a_n
@@ -129,9 +129,10 @@ void oracle_philox4x64_10(const uint64_t ctr_in[4], const uint64_t key_in[2], ui
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* Three standard normals for (seed, counter, ion id): the top 24 bits of each of the
- * four 64-bit Philox words give u_k = (m_k + 1/2) 2^-24 in (0, 1); Box-Muller turns
- * (u0, u1) into two normals and (u2, u3) into the third. */
+/* Three standard normals for (seed, counter, ion id): the top 23 bits of each of the
+ * four 64-bit Philox words give u_k = (m_k + 1/2) 2^-23 in (0, 1) (exact in FP32 as
+ * well as FP64); Box-Muller turns (u0, u1) into two normals and (u2, u3) into the
+ * third. */
 void oracle_normals(uint64_t seed, int64_t counter, int64_t id, double z[3])
 {
     uint64_t ctr[4] = {(uint64_t)counter, (uint64_t)id, 0u, 0u};
@@ -139,7 +140,7 @@ void oracle_normals(uint64_t seed, int64_t counter, int64_t id, double z[3])
     uint64_t r[4];
     double u[4];
     oracle_philox4x64_10(ctr, key, r);
-    for (int k = 0; k < 4; ++k) u[k] = ((double)(r[k] >> 40) + 0.5) * 0x1p-24;
+    for (int k = 0; k < 4; ++k) u[k] = ((double)(r[k] >> 41) + 0.5) * 0x1p-23;
     double R1 = sqrt(-2.0 * log(u[0]));
     double R2 = sqrt(-2.0 * log(u[2]));
     z[0] = R1 * cos(2.0 * ORC_PI * u[1]);

@@ -18,6 +18,7 @@
 namespace it {
 const void* step_kernel(int f64, int T, int I);
 const void* prep_kernel();
+const void* restore_kernel();
 cudaError_t launch_normals(unsigned long long seed, long long counter, const long long* d_ids, long long m,
                            int f64, double* d_z, cudaStream_t st);
 }  // namespace it
@@ -274,6 +275,13 @@ cudaError_t launch_prep(iontrap* h, int b) {
   void* params[] = {&h->args, &b, &f64};
   const unsigned blocks = (unsigned)std::min<int64_t>(cdiv(h->n, 256), 4096);
   return cudaLaunchKernel(prep_kernel(), dim3(blocks), dim3(256), params, 0, h->stream);
+}
+
+cudaError_t launch_restore(iontrap* h, int b) {
+  int f64 = h->f64;
+  void* params[] = {&h->args, &b, &f64};
+  const unsigned blocks = (unsigned)std::min<int64_t>(cdiv(h->n, 256), 4096);
+  return cudaLaunchKernel(restore_kernel(), dim3(blocks), dim3(256), params, 0, h->stream);
 }
 
 cudaError_t build_graph(iontrap* h) {
@@ -564,6 +572,38 @@ int iontrap_forces(iontrap_t* h, double* acc) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_status(h, e);
   return iontrap_sync(h);
+}
+
+int iontrap_checkpoint(iontrap_t* h, double* x, double* v, double* a, int64_t* step) {
+  if (!h) return IONTRAP_EINVAL;
+  int st = iontrap_state(h, x, v, step, nullptr);
+  if (st) return st;
+  DeviceGuard g(h->device);
+  if (a) {
+    cudaError_t e = cudaMemcpy(a, h->d_a, 3 * (size_t)h->n * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(h, e);
+  }
+  return h->status;
+}
+
+int iontrap_restore(iontrap_t* h, const double* x, const double* v, const double* a, int64_t step) {
+  if (!h || !x || !v || !a || step < 0) return IONTRAP_EINVAL;
+  for (int64_t k = 0; k < 3 * h->n; ++k)
+    if (!std::isfinite(x[k]) || !std::isfinite(v[k]) || !std::isfinite(a[k])) return IONTRAP_EINVAL;
+  int st = iontrap_sync(h);
+  if (st) return st;
+  DeviceGuard g(h->device);
+  const size_t vec = 3 * (size_t)h->n * sizeof(double);
+  long long s = step;
+  cudaError_t e = cudaMemcpyAsync(h->d_x, x, vec, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_v, v, vec, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_a, a, vec, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_step, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = launch_restore(h, (int)((step + 1) & 1));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_status(h, e);
+  h->step = step;
+  return h->status;
 }
 
 int iontrap_step_many(iontrap_t* const* hs, const int64_t* n_steps, int count) {

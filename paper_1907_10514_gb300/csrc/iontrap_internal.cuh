@@ -148,15 +148,15 @@ __device__ __forceinline__ void philox4x64_10(unsigned long long c[4], unsigned 
   }
 }
 
-// Three standard normals for (seed, counter, id): u_k = (top 24 bits + 1/2) 2^-24,
-// Box-Muller on (u0, u1) and (u2, u3).  FP32 arithmetic (the FP32 form's noise).
+// Three standard normals for (seed, counter, id): u_k = (top 23 bits + 1/2) 2^-23 (exact
+// in FP32), Box-Muller on (u0, u1) and (u2, u3).  FP32 arithmetic (the FP32 form's noise).
 __device__ __forceinline__ void normals3_f32(unsigned long long seed, long long counter, long long id,
                                              double z[3]) {
   unsigned long long c[4] = {(unsigned long long)counter, (unsigned long long)id, 0ull, 0ull};
   philox4x64_10(c, seed, 0ull);
   float u[4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) u[k] = ((float)(unsigned)(c[k] >> 40) + 0.5f) * 0x1p-24f;
+  for (int k = 0; k < 4; ++k) u[k] = ((float)(unsigned)(c[k] >> 41) + 0.5f) * 0x1p-23f;
   const float r1 = sqrtf(-2.0f * logf(u[0]));
   const float r2 = sqrtf(-2.0f * logf(u[2]));
   float s1, c1, s2, c2;
@@ -174,7 +174,7 @@ __device__ __forceinline__ void normals3_f64(unsigned long long seed, long long 
   philox4x64_10(c, seed, 0ull);
   double u[4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) u[k] = ((double)(c[k] >> 40) + 0.5) * 0x1p-24;
+  for (int k = 0; k < 4; ++k) u[k] = ((double)(c[k] >> 41) + 0.5) * 0x1p-23;
   const double r1 = sqrt(-2.0 * log(u[0]));
   const double r2 = sqrt(-2.0 * log(u[2]));
   double s1, c1, s2, c2;
@@ -191,6 +191,24 @@ __device__ __forceinline__ void normals3_f64(unsigned long long seed, long long 
 // operations, hence the same bits.
 __device__ __forceinline__ double half_kick(double v, double a, double hdt) { return __fma_rn(hdt, a, v); }
 __device__ __forceinline__ double drift(double x, double vh, double dt) { return __fma_rn(dt, vh, x); }
+
+// Entry i of pair stream b for the next positions xn (FP64 form: double4; FP32 form:
+// hi = fl(xn), lo = fl(xn - hi)).
+template <bool F64>
+__device__ __forceinline__ void write_pair(const StepArgs& A, int b, long long i, const double xn[3], float w) {
+  if (F64) {
+    A.p64[b][i] = make_double4(xn[0], xn[1], xn[2], (double)w);
+  } else {
+    float h[3], l[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      h[c] = __double2float_rn(xn[c]);
+      l[c] = __double2float_rn(xn[c] - (double)h[c]);
+    }
+    A.hi[b][i] = make_float4(h[0], h[1], h[2], w);
+    A.lo[b][i] = make_float4(l[0], l[1], l[2], 0.0f);
+  }
+}
 
 // Fused epilogue for ion i: Coulomb sum S (sum_j z_j d/r^3) -> acceleration (Coulomb +
 // trap + Langevin) -> Verlet update -> next pair-stream entry.  cosv = cos(Omega t) at
@@ -252,18 +270,7 @@ __device__ __forceinline__ void epilogue_ion(const StepArgs& A, long long i, con
     }
     A.a[c * n + i] = acc[c];
   }
-  if (F64) {
-    A.p64[wb][i] = make_double4(xn[0], xn[1], xn[2], (double)sd.w);
-  } else {
-    float h[3], l[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      h[c] = __double2float_rn(xn[c]);
-      l[c] = __double2float_rn(xn[c] - (double)h[c]);
-    }
-    A.hi[wb][i] = make_float4(h[0], h[1], h[2], sd.w);
-    A.lo[wb][i] = make_float4(l[0], l[1], l[2], 0.0f);
-  }
+  write_pair<F64>(A, wb, i, xn, sd.w);
   if (!finite) atomicOr(A.err, ERR_NONFINITE);
 }
 

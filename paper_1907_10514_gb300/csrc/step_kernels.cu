@@ -318,20 +318,33 @@ __global__ void __launch_bounds__(T) k_step_f64(const __grid_constant__ StepArgs
 }
 
 // ------------------------------------------------------------------ helpers
-// Write the pair stream of buffer b from the FP64 positions x_n (both forms).
+// Write pair stream b from the FP64 positions x_n (create and force evaluation).
 __global__ void k_prep(const __grid_constant__ StepArgs A, int b, int f64) {
   const long long n = A.n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const double x = A.x[i], y = A.x[n + i], z = A.x[2 * n + i];
+    const double xn[3] = {A.x[i], A.x[n + i], A.x[2 * n + i]};
     const float w = A.spc[A.sp[i]].w;
-    if (f64) {
-      A.p64[b][i] = make_double4(x, y, z, (double)w);
-    } else {
-      const float hx = __double2float_rn(x), hy = __double2float_rn(y), hz = __double2float_rn(z);
-      A.hi[b][i] = make_float4(hx, hy, hz, w);
-      A.lo[b][i] = make_float4(__double2float_rn(x - (double)hx), __double2float_rn(y - (double)hy),
-                               __double2float_rn(z - (double)hz), 0.0f);
-    }
+    if (f64)
+      write_pair<true>(A, b, i, xn, w);
+    else
+      write_pair<false>(A, b, i, xn, w);
+  }
+}
+
+// Write pair stream b from a full state (x_n, v_n, a_n): the drifted positions
+// x_{n+1} = x_n + dt (v_n + dt/2 a_n), by the same operations the epilogue uses.
+__global__ void k_restore(const __grid_constant__ StepArgs A, int b, int f64) {
+  const long long n = A.n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double xn[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      xn[c] = drift(A.x[c * n + i], half_kick(A.v[c * n + i], A.a[c * n + i], A.trap.hdt), A.trap.dt);
+    const float w = A.spc[A.sp[i]].w;
+    if (f64)
+      write_pair<true>(A, b, i, xn, w);
+    else
+      write_pair<false>(A, b, i, xn, w);
   }
 }
 
@@ -372,6 +385,7 @@ const void* step_kernel(int f64, int T, int I) {
 }
 
 const void* prep_kernel() { return (const void*)k_prep; }
+const void* restore_kernel() { return (const void*)k_restore; }
 
 cudaError_t launch_normals(unsigned long long seed, long long counter, const long long* d_ids, long long m,
                            int f64, double* d_z, cudaStream_t st) {

@@ -61,6 +61,8 @@ SIGNATURES = {
     "iontrap_sync": (ctypes.c_int, [_vp]),
     "iontrap_state": (ctypes.c_int, [_vp, _dp, _dp, _i64p, _dp]),
     "iontrap_forces": (ctypes.c_int, [_vp, _dp]),
+    "iontrap_checkpoint": (ctypes.c_int, [_vp, _dp, _dp, _dp, _i64p]),
+    "iontrap_restore": (ctypes.c_int, [_vp, _dp, _dp, _dp, ctypes.c_int64]),
     "iontrap_step_many": (ctypes.c_int, [ctypes.POINTER(_vp), _i64p, ctypes.c_int]),
     "iontrap_destroy": (None, [_vp]),
     "iontrap_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -192,6 +194,19 @@ def iontrap_forces(h, n: int) -> np.ndarray:
     return acc
 
 
+def iontrap_checkpoint(h, n: int):
+    """Returns (x, v, a, step) of the current state."""
+    x, v, a = np.empty((3, n)), np.empty((3, n)), np.empty((3, n))
+    step = ctypes.c_int64()
+    _check(_lib.iontrap_checkpoint(h, _ptr(x), _ptr(v), _ptr(a), ctypes.byref(step)), "iontrap_checkpoint")
+    return x, v, a, int(step.value)
+
+
+def iontrap_restore(h, x, v, a, step: int) -> None:
+    x, v, a = _f64(x), _f64(v), _f64(a)
+    _check(_lib.iontrap_restore(h, _ptr(x), _ptr(v), _ptr(a), int(step)), "iontrap_restore")
+
+
 def iontrap_step_many(handles: Sequence, n_steps: Sequence[int]) -> None:
     arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h
                                              for h in handles])
@@ -249,6 +264,12 @@ class Simulation:
 
     def forces(self) -> np.ndarray:
         return iontrap_forces(self.handle, self.n)
+
+    def checkpoint(self):
+        return iontrap_checkpoint(self.handle, self.n)
+
+    def restore(self, x, v, a, step: int) -> None:
+        iontrap_restore(self.handle, x, v, a, step)
 
     def config(self):
         return iontrap_get_config(self.handle)
