@@ -161,12 +161,21 @@ int iontrap_stable(const iontrap_species *species, int n_species, const iontrap_
 int iontrap_normals(uint64_t seed, int64_t counter, const int64_t *ids, int64_t m,
                     int precision, double *z);
 
-/* Tile configuration of a handle's force kernel: threads per CTA, ions per thread and
- * j-range per CTA (a multiple of 128).  iontrap_get_config reads it; iontrap_set_config
- * changes it (the autotuner's knob; EINVAL for unsupported values).  Results depend
- * only on (n, config): equal configs give bitwise equal trajectories. */
-int iontrap_get_config(const iontrap_t *h, int *threads, int *ions_per_thread, int *jsplit);
-int iontrap_set_config(iontrap_t *h, int threads, int ions_per_thread, int jsplit);
+/* Tile configuration of a handle's force kernel: threads per CTA, ions per thread,
+ * packed (1 = the FP32 pair arithmetic runs on packed FP32x2 instructions, two ions per
+ * instruction; bitwise identical to 0) and the j-range per CTA (grid.y = ceil(n/jsplit)).
+ * iontrap_get_config reads it; iontrap_set_config changes it (the autotuner's knob;
+ * EINVAL for a combination without a compiled kernel, jsplit < 1 or > n, or > 2048 in
+ * the FP64 form).  Results depend only on (n, threads*ions_per_thread, jsplit) and the
+ * parameters: equal configurations give bitwise equal trajectories. */
+int iontrap_get_config(const iontrap_t *h, int *threads, int *ions_per_thread, int *packed, int *jsplit);
+int iontrap_set_config(iontrap_t *h, int threads, int ions_per_thread, int packed, int jsplit);
+
+/* Microbenchmark of the pipes the step kernels use (not part of the method): runs
+ * independent dependency chains of one instruction kind on every SM of the current
+ * device and reports lane operations per SM clock and the SM clock seen.
+ * kind: 0 FFMA, 1 packed FFMA2 (2 lanes each), 2 MUFU rsqrt, 3 DFMA, 4 packed FADD2. */
+int iontrap_alu_probe(int kind, long long iters, double *lane_ops_per_clk_per_sm, double *sm_mhz);
 
 #ifdef __cplusplus
 }

@@ -1,7 +1,7 @@
 // iontrap_api.cu -- host side of libiontrap.so: the C ABI declared in include/iontrap.h.
 //
 // A handle holds one simulation resident on the device: FP64 state (x, v, a), the
-// species table, two ping-pong pair streams (FP32 hi/lo float4 or FP64 double4), the
+// species table, two ping-pong pair streams (FP32 hi/lo float4 or FP64 double4_32a), the
 // split partials and counters the force kernel uses, and a device step counter.  Steps
 // are enqueued as an instantiated CUDA graph of 100 chained kernel nodes (built node by
 // node, so any stream works, including the legacy default stream) plus single launches
@@ -16,7 +16,7 @@
 #include "iontrap_internal.cuh"
 
 namespace it {
-const void* step_kernel(int f64, int T, int I);
+const void* step_kernel(int f64, int T, int I, int packed);
 const void* prep_kernel();
 const void* restore_kernel();
 cudaError_t launch_normals(unsigned long long seed, long long counter, const long long* d_ids, long long m,
@@ -26,7 +26,7 @@ cudaError_t launch_normals(unsigned long long seed, long long counter, const lon
 using namespace it;
 
 static constexpr int kGraphSteps = 100;
-static constexpr int kMaxJsplit = 2048;
+static constexpr int kMaxJsplitF64 = 2048;  // FP64 form stages its whole j-range
 
 struct iontrap {
   int64_t n = 0;
@@ -37,6 +37,7 @@ struct iontrap {
   int sms = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  cudaStream_t cap = nullptr;  // private stream used only to capture the step graph
   // device buffers
   double *d_x = nullptr, *d_v = nullptr, *d_a = nullptr, *d_out = nullptr;
   unsigned char* d_sp = nullptr;
@@ -49,7 +50,7 @@ struct iontrap {
   long long* d_step = nullptr;
   int* d_err = nullptr;
   // launch configuration
-  int T = 128, I = 1, jsplit = 128;
+  int T = 128, I = 1, packed = 0, jsplit = 128;
   StepArgs args{};
   // graph of kGraphSteps chained steps
   cudaGraph_t graph = nullptr;
@@ -171,35 +172,43 @@ bool species_stable(const iontrap_params* p, double rho) {
 }
 
 // ------------------------------------------------------------------ configuration
-// Default tile configuration for n ions: ions per thread grow with n (register reuse
-// of each staged j), jsplit is picked so that the grid fills whole waves of SMs.
-void default_config(int64_t n, int f64, int sms, int* T, int* I, int* jsplit) {
-  *T = 128;
-  if (f64)
-    *I = 1;
-  else
-    *I = n < 2048 ? 1 : (n < 16384 ? 2 : 4);
-  const int64_t iblocks = cdiv(n, (int64_t)(*T) * (*I));
-  const int bytes_per_j = 32;
-  double best = -1;
-  int bestj = kMaxJsplit;
-  for (int js = 128; js <= kMaxJsplit; js += 128) {
-    const int64_t splits = cdiv(n, js);
-    const int64_t ctas = iblocks * splits;
-    int occ = (int)std::min<int64_t>(8, (200 * 1024) / (js * bytes_per_j + 1024));
-    occ = std::max(occ, 1);
-    const double waves = (double)ctas / ((double)sms * occ);
-    const double eff = waves / std::ceil(waves);
-    // favour enough CTAs to fill the GPU, then full waves, then larger j-ranges
-    const double fill = std::min(1.0, waves);
-    const double score = fill * eff + 1e-4 * js / kMaxJsplit;
-    if (score > best + 1e-9) {
-      best = score;
-      bestj = js;
-    }
-    if (js >= n) break;
+int64_t gcd64(int64_t a, int64_t b) {
+  while (b) {
+    const int64_t t = a % b;
+    a = b;
+    b = t;
   }
-  *jsplit = bestj;
+  return a;
+}
+
+// Default tile configuration for n ions.  The i-block (T*I ions) grows with n: small
+// blocks keep the FP64 epilogue of the last CTA short, large ones reuse each staged j
+// over more ions.  The number of j-splits S makes the grid a multiple of the SM count
+// (equal work per SM) with at least two CTAs per SM where n allows.
+void default_config(int64_t n, int f64, int sms, int* T, int* I, int* packed, int* jsplit) {
+  if (f64) {
+    *T = 128;
+    *I = 1;
+    *packed = 0;
+  } else if (n <= 2048) {
+    *T = 64, *I = 1, *packed = 0;
+  } else if (n <= 8192) {
+    *T = 64, *I = 2, *packed = 1;
+  } else if (n <= 32768) {
+    *T = 128, *I = 4, *packed = 1;
+  } else {
+    *T = 128, *I = 4, *packed = 1;
+  }
+  const int64_t iblocks = cdiv(n, (int64_t)(*T) * (*I));
+  const int64_t step = sms / gcd64(iblocks, sms);  // S multiple of this => grid multiple of sms
+  const int64_t min_j = f64 ? 32 : 32;
+  const int64_t s_max = std::max<int64_t>(1, n / min_j);
+  int64_t S = step;
+  while (S * iblocks < 2 * (int64_t)sms && S + step <= s_max) S += step;
+  if (S > s_max) S = std::max<int64_t>(1, std::min(s_max, cdiv(2 * (int64_t)sms, iblocks)));
+  int64_t js = cdiv(n, S);
+  if (f64) js = std::min<int64_t>(js, kMaxJsplitF64);
+  *jsplit = (int)js;
 }
 
 int set_status(iontrap* h, int st) {
@@ -222,7 +231,7 @@ dim3 grid_of(const iontrap* h) {
 }
 
 size_t smem_of(const iontrap* h) {
-  if (h->p.flags & IONTRAP_COULOMB_OFF) return 0;
+  if (!h->f64 || (h->p.flags & IONTRAP_COULOMB_OFF)) return 0;  // FP32 form: static chunk buffers
   return (size_t)h->jsplit * 32;
 }
 
@@ -261,13 +270,29 @@ int alloc_scratch(iontrap* h) {
   return IONTRAP_OK;
 }
 
+// Launch one step kernel with programmatic dependent launch, so that consecutive steps
+// overlap one grid's launch with the previous grid's tail.
+cudaError_t launch_step_on(iontrap* h, StepArgs& a, cudaStream_t st) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid_of(h);
+  cfg.blockDim = dim3(h->T);
+  cfg.dynamicSmemBytes = smem_of(h);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  void* params[] = {&a};
+  return cudaLaunchKernelExC(&cfg, step_kernel(h->f64, h->T, h->I, h->packed), params);
+}
+
 cudaError_t launch_mode(iontrap* h, int mode, double* out) {
   StepArgs a = h->args;
   a.mode = mode;
   a.out = out;
   void* params[] = {&a};
-  return cudaLaunchKernel(step_kernel(h->f64, h->T, h->I), grid_of(h), dim3(h->T), params, smem_of(h),
-                          h->stream);
+  return launch_step_on(h, a, h->stream);
 }
 
 cudaError_t launch_prep(iontrap* h, int b) {
@@ -284,27 +309,28 @@ cudaError_t launch_restore(iontrap* h, int b) {
   return cudaLaunchKernel(restore_kernel(), dim3(blocks), dim3(256), params, 0, h->stream);
 }
 
+// Capture kGraphSteps chained PDL step launches on the private capture stream; the
+// instantiated graph is then launched on the handle's stream (any stream works).
 cudaError_t build_graph(iontrap* h) {
   destroy_graph(h);
-  cudaError_t e = cudaGraphCreate(&h->graph, 0);
-  if (e != cudaSuccess) return e;
+  if (!h->cap) {
+    cudaError_t e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+  }
   StepArgs a = h->args;
   a.mode = MODE_STEP;
   a.out = nullptr;
-  void* params[] = {&a};
-  cudaKernelNodeParams kp{};
-  kp.func = const_cast<void*>(step_kernel(h->f64, h->T, h->I));
-  kp.gridDim = grid_of(h);
-  kp.blockDim = dim3(h->T);
-  kp.sharedMemBytes = (unsigned)smem_of(h);
-  kp.kernelParams = params;
-  cudaGraphNode_t prev = nullptr;
-  for (int s = 0; s < kGraphSteps; ++s) {
-    cudaGraphNode_t node;
-    e = cudaGraphAddKernelNode(&node, h->graph, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
-    if (e != cudaSuccess) return e;
-    prev = node;
+  cudaError_t e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  for (int s = 0; s < kGraphSteps && e == cudaSuccess; ++s) e = launch_step_on(h, a, h->cap);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return e;
   }
+  h->graph = g;
   return cudaGraphInstantiate(&h->gexec, h->graph, 0);
 }
 
@@ -313,15 +339,13 @@ int prepare_kernels() {
   if (done) return IONTRAP_OK;
   const int Ts[] = {64, 128, 256};
   const int Is[] = {1, 2, 4};
-  for (int f = 0; f < 2; ++f)
-    for (int T : Ts)
-      for (int I : Is) {
-        const void* fn = step_kernel(f, T, I);
-        if (!fn) continue;
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxJsplit * 32) !=
-            cudaSuccess)
-          return IONTRAP_ECUDA;
-      }
+  for (int T : Ts)
+    for (int I : Is) {
+      const void* fn = step_kernel(1, T, I, 0);
+      if (fn && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxJsplitF64 * 32) !=
+                    cudaSuccess)
+        return IONTRAP_ECUDA;
+    }
   done = 1;
   return IONTRAP_OK;
 }
@@ -333,6 +357,7 @@ void free_all(iontrap* h) {
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  if (h->cap) cudaStreamDestroy(h->cap);
 }
 
 }  // namespace
@@ -410,7 +435,7 @@ int iontrap_create(const iontrap_species* species, int n_species, const uint8_t*
     }
     h->own_stream = true;
   }
-  default_config(n, h->f64, h->sms, &h->T, &h->I, &h->jsplit);
+  default_config(n, h->f64, h->sms, &h->T, &h->I, &h->packed, &h->jsplit);
 
   // species table
   const double dt = h->p.dt;
@@ -438,7 +463,7 @@ int iontrap_create(const iontrap_species* species, int n_species, const uint8_t*
   A.n = n;
 
   const size_t vec = 3 * (size_t)n * sizeof(double);
-  const size_t pair = (size_t)n * (h->f64 ? sizeof(double4) : 2 * sizeof(float4));
+  const size_t pair = (size_t)n * (h->f64 ? sizeof(double4_32a) : 2 * sizeof(float4));
   bool ok = cudaMalloc(&h->d_x, vec) == cudaSuccess && cudaMalloc(&h->d_v, vec) == cudaSuccess &&
             cudaMalloc(&h->d_a, vec) == cudaSuccess && cudaMalloc(&h->d_sp, (size_t)n) == cudaSuccess &&
             cudaMalloc(&h->d_pair[0], pair) == cudaSuccess && cudaMalloc(&h->d_pair[1], pair) == cudaSuccess &&
@@ -452,7 +477,7 @@ int iontrap_create(const iontrap_species* species, int n_species, const uint8_t*
   }
   for (int b = 0; b < 2; ++b) {
     if (h->f64) {
-      A.p64[b] = (double4*)h->d_pair[b];
+      A.p64[b] = (double4_32a*)h->d_pair[b];
       A.hi[b] = A.lo[b] = nullptr;
     } else {
       A.hi[b] = (float4*)h->d_pair[b];
@@ -645,24 +670,26 @@ int iontrap_normals(uint64_t seed, int64_t counter, const int64_t* ids, int64_t 
   return e == cudaSuccess ? IONTRAP_OK : IONTRAP_ECUDA;
 }
 
-int iontrap_get_config(const iontrap_t* h, int* threads, int* ions_per_thread, int* jsplit) {
+int iontrap_get_config(const iontrap_t* h, int* threads, int* ions_per_thread, int* packed, int* jsplit) {
   if (!h) return IONTRAP_EINVAL;
   if (threads) *threads = h->T;
   if (ions_per_thread) *ions_per_thread = h->I;
+  if (packed) *packed = h->packed;
   if (jsplit) *jsplit = h->jsplit;
   return IONTRAP_OK;
 }
 
-int iontrap_set_config(iontrap_t* h, int threads, int ions_per_thread, int jsplit) {
+int iontrap_set_config(iontrap_t* h, int threads, int ions_per_thread, int packed, int jsplit) {
   if (!h) return IONTRAP_EINVAL;
-  if (!step_kernel(h->f64, threads, ions_per_thread)) return IONTRAP_EINVAL;
-  if (jsplit < 128 || jsplit > kMaxJsplit || jsplit % 128) return IONTRAP_EINVAL;
+  if (!step_kernel(h->f64, threads, ions_per_thread, packed)) return IONTRAP_EINVAL;
+  if (jsplit < 1 || jsplit > h->n || (h->f64 && jsplit > kMaxJsplitF64)) return IONTRAP_EINVAL;
   if (h->status) return h->status;
   DeviceGuard g(h->device);
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_status(h, e);
   h->T = threads;
   h->I = ions_per_thread;
+  h->packed = packed;
   h->jsplit = jsplit;
   destroy_graph(h);
   const int st = alloc_scratch(h);

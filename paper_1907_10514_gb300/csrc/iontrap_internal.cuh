@@ -49,7 +49,7 @@ struct StepArgs {
   long long n;
   float4* hi[2];       // FP32 form: (x_hi, y_hi, z_hi, z_charge), ping-pong
   float4* lo[2];       // FP32 form: (x_lo, y_lo, z_lo, 0),  x = x_hi + x_lo
-  double4* p64[2];     // FP64 form: (x, y, z, z_charge), ping-pong
+  double4_32a* p64[2];     // FP64 form: (x, y, z, z_charge), ping-pong
   double* x;           // positions x_n
   double* v;           // velocities v_n
   double* a;           // accelerations a_n
@@ -192,12 +192,12 @@ __device__ __forceinline__ void normals3_f64(unsigned long long seed, long long 
 __device__ __forceinline__ double half_kick(double v, double a, double hdt) { return __fma_rn(hdt, a, v); }
 __device__ __forceinline__ double drift(double x, double vh, double dt) { return __fma_rn(dt, vh, x); }
 
-// Entry i of pair stream b for the next positions xn (FP64 form: double4; FP32 form:
+// Entry i of pair stream b for the next positions xn (FP64 form: double4_32a; FP32 form:
 // hi = fl(xn), lo = fl(xn - hi)).
 template <bool F64>
 __device__ __forceinline__ void write_pair(const StepArgs& A, int b, long long i, const double xn[3], float w) {
   if (F64) {
-    A.p64[b][i] = make_double4(xn[0], xn[1], xn[2], (double)w);
+    A.p64[b][i] = make_double4_32a(xn[0], xn[1], xn[2], (double)w);
   } else {
     float h[3], l[3];
 #pragma unroll
@@ -212,7 +212,7 @@ __device__ __forceinline__ void write_pair(const StepArgs& A, int b, long long i
 
 // Fused epilogue for ion i: Coulomb sum S (sum_j z_j d/r^3) -> acceleration (Coulomb +
 // trap + Langevin) -> Verlet update -> next pair-stream entry.  cosv = cos(Omega t) at
-// the force time.  F64 selects the plain FP64 form (FP64 noise, double4 pair stream).
+// the force time.  F64 selects the plain FP64 form (FP64 noise, double4_32a pair stream).
 template <bool F64>
 __device__ __forceinline__ void epilogue_ion(const StepArgs& A, long long i, const double S[3], double cosv,
                                              long long ns, int wb) {

@@ -21,22 +21,23 @@
 namespace it {
 
 // ------------------------------------------------------------------ FP32 pair terms
-// d = x_i - x_j from hi/lo pairs: (x_i,hi - x_j,hi) is exact for close pairs (Sterbenz)
-// and the lo difference restores the bits FP32 rounding dropped from both positions.
+// d = x_j - x_i from hi/lo pairs, with the i side held negated in registers:
+// (x_j,hi - x_i,hi) is exact for close pairs (Sterbenz) and the lo difference restores
+// the bits FP32 rounding dropped from both positions.  The accumulators therefore hold
+// -sum_j z_j (x_i - x_j)/r^3; the epilogue flips the sign.
 template <int I, bool DIAG>
-__device__ __forceinline__ void segment_f32(const float4* __restrict__ sh, const float4* __restrict__ sl, int g0,
-                                            int g1, long long jbase, const float (&xh)[I][3],
-                                            const float (&xl)[I][3], const long long (&ii)[I],
-                                            float (&acc)[I][3]) {
+__device__ __forceinline__ void segment_f32(const float4* __restrict__ sh, const float4* __restrict__ sl, int jn,
+                                            long long jbase, const float (&nxh)[I][3], const float (&nxl)[I][3],
+                                            const long long (&ii)[I], float (&acc)[I][3]) {
 #pragma unroll 4
-  for (int j = g0; j < g1; ++j) {
+  for (int j = 0; j < jn; ++j) {
     const float4 ph = sh[j];
     const float4 pl = sl[j];
 #pragma unroll
     for (int k = 0; k < I; ++k) {
-      const float dx = (xh[k][0] - ph.x) + (xl[k][0] - pl.x);
-      const float dy = (xh[k][1] - ph.y) + (xl[k][1] - pl.y);
-      const float dz = (xh[k][2] - ph.z) + (xl[k][2] - pl.z);
+      const float dx = (ph.x + nxh[k][0]) + (pl.x + nxl[k][0]);
+      const float dy = (ph.y + nxh[k][1]) + (pl.y + nxl[k][1]);
+      const float dz = (ph.z + nxh[k][2]) + (pl.z + nxl[k][2]);
       const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
       float ri = rsqrt_approx(r2);
       if (DIAG) ri = (jbase + j == ii[k]) ? 0.0f : ri;
@@ -49,30 +50,48 @@ __device__ __forceinline__ void segment_f32(const float4* __restrict__ sh, const
   }
 }
 
+// The same arithmetic on two ions per instruction (packed FP32x2 FADD/FMUL/FFMA of
+// sm_100+); each lane rounds exactly as the scalar loop does, so both loops give the
+// same bits.
 template <int I, bool DIAG>
-__device__ __forceinline__ void segment_f64(const double4* __restrict__ sp, int g0, int g1, long long jbase,
-                                            const double (&xi)[I][3], const long long (&ii)[I],
-                                            double (&acc)[I][3]) {
-#pragma unroll 2
-  for (int j = g0; j < g1; ++j) {
-    const double4 p = sp[j];
+__device__ __forceinline__ void segment_f32x2(const float4* __restrict__ sh, const float4* __restrict__ sl, int jn,
+                                              long long jbase, const float2 (&nxh)[I / 2][3],
+                                              const float2 (&nxl)[I / 2][3], const long long (&ii)[I],
+                                              float2 (&acc)[I / 2][3]) {
+#pragma unroll 4
+  for (int j = 0; j < jn; ++j) {
+    const float4 ph = sh[j];
+    const float4 pl = sl[j];
+    const float2 hx = make_float2(ph.x, ph.x), hy = make_float2(ph.y, ph.y), hz = make_float2(ph.z, ph.z);
+    const float2 lx = make_float2(pl.x, pl.x), ly = make_float2(pl.y, pl.y), lz = make_float2(pl.z, pl.z);
+    const float2 w = make_float2(ph.w, ph.w);
 #pragma unroll
-    for (int k = 0; k < I; ++k) {
-      const double dx = xi[k][0] - p.x;
-      const double dy = xi[k][1] - p.y;
-      const double dz = xi[k][2] - p.z;
-      const double r2 = dx * dx + dy * dy + dz * dz;
-      double ri = rsqrt(r2);
-      if (DIAG) ri = (jbase + j == ii[k]) ? 0.0 : ri;
-      const double s = p.w * ri * ri * ri;
-      acc[k][0] += s * dx;
-      acc[k][1] += s * dy;
-      acc[k][2] += s * dz;
+    for (int k = 0; k < I / 2; ++k) {
+      const float2 dx = __fadd2_rn(__fadd2_rn(hx, nxh[k][0]), __fadd2_rn(lx, nxl[k][0]));
+      const float2 dy = __fadd2_rn(__fadd2_rn(hy, nxh[k][1]), __fadd2_rn(ly, nxl[k][1]));
+      const float2 dz = __fadd2_rn(__fadd2_rn(hz, nxh[k][2]), __fadd2_rn(lz, nxl[k][2]));
+      const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+      float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+      if (DIAG) {
+        ri.x = (jbase + j == ii[2 * k]) ? 0.0f : ri.x;
+        ri.y = (jbase + j == ii[2 * k + 1]) ? 0.0f : ri.y;
+      }
+      const float2 ri2 = __fmul2_rn(ri, ri);
+      const float2 s = __fmul2_rn(__fmul2_rn(w, ri), ri2);
+      acc[k][0] = __ffma2_rn(s, dx, acc[k][0]);
+      acc[k][1] = __ffma2_rn(s, dy, acc[k][1]);
+      acc[k][2] = __ffma2_rn(s, dz, acc[k][2]);
     }
   }
 }
 
-// Stage the CTA's j-range (bytes per stream) with bulk TMA; every thread waits with a
+// Programmatic dependent launch: let the next step's CTAs be scheduled as this grid's
+// CTAs retire, and wait for the previous step's grid (its memory included) before
+// touching any state.  Both are no-ops for a launch without the PDL attribute.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Stage a whole j-range (bytes per stream) with bulk TMA; every thread waits with a
 // time limit.  Returns false (error flag set, copies drained) if the wait expired.
 __device__ __forceinline__ bool stage_jrange(uint64_t* bar, void* d0, const void* s0, void* d1, const void* s1,
                                              uint32_t bytes, int* err) {
@@ -131,23 +150,29 @@ __device__ __forceinline__ double force_time_cos(const StepArgs& A, long long ns
 }
 
 // ------------------------------------------------------------------ FP32 form
-template <int T, int I>
+constexpr int kChunk = kSeg;  // j-chunk staged per TMA transaction = one Kahan segment
+
+template <int T, int I, bool PACK>
 __global__ void __launch_bounds__(T) k_step_f32(const __grid_constant__ StepArgs A) {
-  extern __shared__ __align__(128) unsigned char smraw[];
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(128) float4 sh[2][kChunk];
+  __shared__ __align__(128) float4 sl[2][kChunk];
+  __shared__ __align__(8) uint64_t bar[2];
   __shared__ int s_flag;
   __shared__ double s_cos;
-  float4* sh = reinterpret_cast<float4*>(smraw);
-  float4* sl = sh + A.jsplit;
 
+  pdl_trigger();
+  pdl_wait();
   const int tid = threadIdx.x;
   const long long n = A.n;
   const long long i0 = (long long)blockIdx.x * (T * I);
   const long long j0 = (long long)blockIdx.y * A.jsplit;
-  const int jn = (int)min((long long)A.jsplit, n - j0);
+  const long long j1 = min(j0 + (long long)A.jsplit, n);
+  const int nch = (int)((j1 - j0 + kChunk - 1) / kChunk);
   const long long ns = *A.step;
   const int rb = (A.mode == MODE_STEP) ? (int)((ns + 1) & 1) : (int)(ns & 1);
   const bool coulomb = !(A.trap.flags & IONTRAP_COULOMB_OFF);
+  const float4* __restrict__ ghi = A.hi[rb];
+  const float4* __restrict__ glo = A.lo[rb];
 
   float ks[I][3], kc[I][3];
 #pragma unroll
@@ -156,43 +181,98 @@ __global__ void __launch_bounds__(T) k_step_f32(const __grid_constant__ StepArgs
     for (int c = 0; c < 3; ++c) ks[k][c] = kc[k][c] = 0.0f;
 
   if (coulomb) {
-    if (!stage_jrange(&bar, sh, A.hi[rb] + j0, sl, A.lo[rb] + j0, (uint32_t)jn * 16u, A.err)) return;
-    float xh[I][3], xl[I][3];
+    auto issue = [&](int c) {
+      const long long jc = j0 + (long long)c * kChunk;
+      const uint32_t bytes = (uint32_t)min((long long)kChunk, j1 - jc) * 16u;
+      const int b = c & 1;
+      mbar_arrive_expect_tx(&bar[b], 2u * bytes);
+      tma_bulk_g2s(sh[b], ghi + jc, bytes, &bar[b]);
+      tma_bulk_g2s(sl[b], glo + jc, bytes, &bar[b]);
+    };
+    if (tid == 0) {
+      mbar_init(&bar[0], 1);
+      mbar_init(&bar[1], 1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      issue(0);
+      if (nch > 1) issue(1);
+    }
     long long ii[I];
+    float nxh[I][3], nxl[I][3];
 #pragma unroll
     for (int k = 0; k < I; ++k) {
       ii[k] = i0 + k * T + tid;
       float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
       if (ii[k] < n) {
-        h = A.hi[rb][ii[k]];
-        l = A.lo[rb][ii[k]];
+        h = ghi[ii[k]];
+        l = glo[ii[k]];
       }
-      xh[k][0] = h.x, xh[k][1] = h.y, xh[k][2] = h.z;
-      xl[k][0] = l.x, xl[k][1] = l.y, xl[k][2] = l.z;
+      nxh[k][0] = -h.x, nxh[k][1] = -h.y, nxh[k][2] = -h.z;
+      nxl[k][0] = -l.x, nxl[k][1] = -l.y, nxl[k][2] = -l.z;
     }
     const long long iend = i0 + T * I;
-    for (int g0 = 0; g0 < jn; g0 += kSeg) {
-      const int g1 = min(g0 + kSeg, jn);
+    for (int c = 0; c < nch; ++c) {
+      const int b = c & 1;
+      const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)((c >> 1) & 1), kWaitLimitNs);
+      const long long jc = j0 + (long long)c * kChunk;
+      const int jn = (int)min((long long)kChunk, j1 - jc);
+      const bool diag = (jc < iend) && (i0 < jc + jn);
       float acc[I][3];
+      if constexpr (PACK) {
+        float2 nxh2[I / 2][3], nxl2[I / 2][3], acc2[I / 2][3];
 #pragma unroll
-      for (int k = 0; k < I; ++k)
+        for (int k = 0; k < I / 2; ++k)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) acc[k][c] = 0.0f;
-      const bool diag = (j0 + g0 < iend) && (i0 < j0 + g1);
-      if (diag)
-        segment_f32<I, true>(sh, sl, g0, g1, j0, xh, xl, ii, acc);
-      else
-        segment_f32<I, false>(sh, sl, g0, g1, j0, xh, xl, ii, acc);
+          for (int d = 0; d < 3; ++d) {
+            nxh2[k][d] = make_float2(nxh[2 * k][d], nxh[2 * k + 1][d]);
+            nxl2[k][d] = make_float2(nxl[2 * k][d], nxl[2 * k + 1][d]);
+            acc2[k][d] = make_float2(0.0f, 0.0f);
+          }
+        if (diag)
+          segment_f32x2<I, true>(sh[b], sl[b], jn, jc, nxh2, nxl2, ii, acc2);
+        else
+          segment_f32x2<I, false>(sh[b], sl[b], jn, jc, nxh2, nxl2, ii, acc2);
+#pragma unroll
+        for (int k = 0; k < I / 2; ++k)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            acc[2 * k][d] = acc2[k][d].x;
+            acc[2 * k + 1][d] = acc2[k][d].y;
+          }
+      } else {
+#pragma unroll
+        for (int k = 0; k < I; ++k)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) acc[k][d] = 0.0f;
+        if (diag)
+          segment_f32<I, true>(sh[b], sl[b], jn, jc, nxh, nxl, ii, acc);
+        else
+          segment_f32<I, false>(sh[b], sl[b], jn, jc, nxh, nxl, ii, acc);
+      }
       // Kahan: value = ks - kc
 #pragma unroll
       for (int k = 0; k < I; ++k)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const float y = acc[k][c] - kc[k][c];
-          const float t = ks[k][c] + y;
-          kc[k][c] = (t - ks[k][c]) - y;
-          ks[k][c] = t;
+        for (int d = 0; d < 3; ++d) {
+          const float y = acc[k][d] - kc[k][d];
+          const float t = ks[k][d] + y;
+          kc[k][d] = (t - ks[k][d]) - y;
+          ks[k][d] = t;
         }
+      if (__syncthreads_or(!ok)) {  // a staged chunk never arrived: drain and give up
+        if (tid == 0) {
+          atomicOr(A.err, ERR_TIMEOUT);
+          for (int q = c; q < min(c + 2, nch); ++q)
+            mbar_wait_bounded(&bar[q & 1], (uint32_t)((q >> 1) & 1), kWaitLimitNs);
+        }
+        __syncthreads();
+        return;
+      }
+      if (tid == 0 && c + 2 < nch) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(c + 2);
+      }
     }
   }
 
@@ -216,6 +296,7 @@ __global__ void __launch_bounds__(T) k_step_f32(const __grid_constant__ StepArgs
   const double cosv = s_cos;
   const int wb = rb ^ 1;
   const int nsplit = gridDim.y;
+  constexpr int U = 8;
 #pragma unroll
   for (int k = 0; k < I; ++k) {
     const long long i = i0 + k * T + tid;
@@ -224,15 +305,27 @@ __global__ void __launch_bounds__(T) k_step_f32(const __grid_constant__ StepArgs
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       float s = 0.0f, cc = 0.0f;
-      for (int p = 0; p < nsplit; ++p) {
-        const float ps = __ldcg(part + ((p * 3ll + c) * 2 + 0) * n + i);
-        const float pc = __ldcg(part + ((p * 3ll + c) * 2 + 1) * n + i);
-        const float y = ps - cc;
-        const float t = s + y;
-        cc = ((t - s) - y) + pc;
-        s = t;
+      for (int p0 = 0; p0 < nsplit; p0 += U) {
+        float ps[U], pc[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          ps[u] = pc[u] = 0.0f;
+          if (p0 + u < nsplit) {
+            ps[u] = __ldcg(part + (((p0 + u) * 3ll + c) * 2 + 0) * n + i);
+            pc[u] = __ldcg(part + (((p0 + u) * 3ll + c) * 2 + 1) * n + i);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (p0 + u < nsplit) {
+            const float y = ps[u] - cc;
+            const float t = s + y;
+            cc = ((t - s) - y) + pc[u];
+            s = t;
+          }
+        }
       }
-      S[c] = (double)s - (double)cc;
+      S[c] = (double)cc - (double)s;  // the accumulators hold the negated sum
     }
     epilogue_ion<false>(A, i, S, cosv, ns, wb);
   }
@@ -240,14 +333,39 @@ __global__ void __launch_bounds__(T) k_step_f32(const __grid_constant__ StepArgs
 }
 
 // ------------------------------------------------------------------ FP64 plain form
+template <int I, bool DIAG>
+__device__ __forceinline__ void segment_f64(const double4_32a* __restrict__ sp, int g0, int g1, long long jbase,
+                                            const double (&xi)[I][3], const long long (&ii)[I],
+                                            double (&acc)[I][3]) {
+#pragma unroll 2
+  for (int j = g0; j < g1; ++j) {
+    const double4_32a p = sp[j];
+#pragma unroll
+    for (int k = 0; k < I; ++k) {
+      const double dx = xi[k][0] - p.x;
+      const double dy = xi[k][1] - p.y;
+      const double dz = xi[k][2] - p.z;
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      double ri = rsqrt(r2);
+      if (DIAG) ri = (jbase + j == ii[k]) ? 0.0 : ri;
+      const double s = p.w * ri * ri * ri;
+      acc[k][0] += s * dx;
+      acc[k][1] += s * dy;
+      acc[k][2] += s * dz;
+    }
+  }
+}
+
 template <int T, int I>
 __global__ void __launch_bounds__(T) k_step_f64(const __grid_constant__ StepArgs A) {
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ __align__(8) uint64_t bar;
   __shared__ int s_flag;
   __shared__ double s_cos;
-  double4* sp = reinterpret_cast<double4*>(smraw);
+  double4_32a* sp = reinterpret_cast<double4_32a*>(smraw);
 
+  pdl_trigger();
+  pdl_wait();
   const int tid = threadIdx.x;
   const long long n = A.n;
   const long long i0 = (long long)blockIdx.x * (T * I);
@@ -270,7 +388,7 @@ __global__ void __launch_bounds__(T) k_step_f64(const __grid_constant__ StepArgs
 #pragma unroll
     for (int k = 0; k < I; ++k) {
       ii[k] = i0 + k * T + tid;
-      double4 p = make_double4(0., 0., 0., 0.);
+      double4_32a p = make_double4_32a(0., 0., 0., 0.);
       if (ii[k] < n) p = A.p64[rb][ii[k]];
       xi[k][0] = p.x, xi[k][1] = p.y, xi[k][2] = p.z;
     }
@@ -364,23 +482,24 @@ __global__ void k_normals(unsigned long long seed, long long counter, const long
 
 // ------------------------------------------------------------------ registry
 struct KernelEntry {
-  int f64, T, I;
+  int f64, T, I, packed;
   const void* fn;
 };
 
 static const KernelEntry kKernels[] = {
-    {0, 64, 1, (const void*)k_step_f32<64, 1>},    {0, 64, 2, (const void*)k_step_f32<64, 2>},
-    {0, 64, 4, (const void*)k_step_f32<64, 4>},    {0, 128, 1, (const void*)k_step_f32<128, 1>},
-    {0, 128, 2, (const void*)k_step_f32<128, 2>},  {0, 128, 4, (const void*)k_step_f32<128, 4>},
-    {0, 256, 1, (const void*)k_step_f32<256, 1>},  {0, 256, 2, (const void*)k_step_f32<256, 2>},
-    {0, 256, 4, (const void*)k_step_f32<256, 4>},  {1, 64, 1, (const void*)k_step_f64<64, 1>},
-    {1, 128, 1, (const void*)k_step_f64<128, 1>},  {1, 128, 2, (const void*)k_step_f64<128, 2>},
-    {1, 256, 1, (const void*)k_step_f64<256, 1>},
+    {0, 64, 1, 0, (const void*)k_step_f32<64, 1, false>},    {0, 64, 2, 0, (const void*)k_step_f32<64, 2, false>},
+    {0, 64, 2, 1, (const void*)k_step_f32<64, 2, true>},     {0, 64, 4, 1, (const void*)k_step_f32<64, 4, true>},
+    {0, 128, 1, 0, (const void*)k_step_f32<128, 1, false>},  {0, 128, 2, 0, (const void*)k_step_f32<128, 2, false>},
+    {0, 128, 2, 1, (const void*)k_step_f32<128, 2, true>},   {0, 128, 4, 0, (const void*)k_step_f32<128, 4, false>},
+    {0, 128, 4, 1, (const void*)k_step_f32<128, 4, true>},   {0, 256, 2, 1, (const void*)k_step_f32<256, 2, true>},
+    {0, 256, 4, 1, (const void*)k_step_f32<256, 4, true>},   {0, 256, 4, 0, (const void*)k_step_f32<256, 4, false>},
+    {1, 64, 1, 0, (const void*)k_step_f64<64, 1>},           {1, 128, 1, 0, (const void*)k_step_f64<128, 1>},
+    {1, 128, 2, 0, (const void*)k_step_f64<128, 2>},         {1, 256, 1, 0, (const void*)k_step_f64<256, 1>},
 };
 
-const void* step_kernel(int f64, int T, int I) {
+const void* step_kernel(int f64, int T, int I, int packed) {
   for (const auto& e : kKernels)
-    if (e.f64 == f64 && e.T == T && e.I == I) return e.fn;
+    if (e.f64 == f64 && e.T == T && e.I == I && e.packed == packed) return e.fn;
   return nullptr;
 }
 

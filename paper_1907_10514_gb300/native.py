@@ -70,8 +70,9 @@ SIGNATURES = {
                                       ctypes.POINTER(iontrap_params), _ip]),
     "iontrap_normals": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int64, _i64p, ctypes.c_int64,
                                        ctypes.c_int, _dp]),
-    "iontrap_get_config": (ctypes.c_int, [_vp, _ip, _ip, _ip]),
-    "iontrap_set_config": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "iontrap_get_config": (ctypes.c_int, [_vp, _ip, _ip, _ip, _ip]),
+    "iontrap_set_config": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "iontrap_alu_probe": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_longlong, _dp, _dp]),
 }
 
 
@@ -234,15 +235,24 @@ def iontrap_normals(seed: int, counter: int, ids, precision: int = IONTRAP_PREC_
 
 
 def iontrap_get_config(h):
-    T, I, J = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    _check(_lib.iontrap_get_config(h, ctypes.byref(T), ctypes.byref(I), ctypes.byref(J)),
+    """Returns (threads, ions_per_thread, packed, jsplit)."""
+    T, I, P, J = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(_lib.iontrap_get_config(h, ctypes.byref(T), ctypes.byref(I), ctypes.byref(P), ctypes.byref(J)),
            "iontrap_get_config")
-    return T.value, I.value, J.value
+    return T.value, I.value, P.value, J.value
 
 
-def iontrap_set_config(h, threads: int, ions_per_thread: int, jsplit: int) -> None:
-    _check(_lib.iontrap_set_config(h, int(threads), int(ions_per_thread), int(jsplit)),
+def iontrap_set_config(h, threads: int, ions_per_thread: int, packed: int, jsplit: int) -> None:
+    _check(_lib.iontrap_set_config(h, int(threads), int(ions_per_thread), int(packed), int(jsplit)),
            "iontrap_set_config")
+
+
+def iontrap_alu_probe(kind: int, iters: int = 20000):
+    """Returns (lane operations per SM clock, SM MHz) for one instruction kind."""
+    ops, mhz = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.iontrap_alu_probe(int(kind), int(iters), ctypes.byref(ops), ctypes.byref(mhz)),
+           "iontrap_alu_probe")
+    return ops.value, mhz.value
 
 
 class Simulation:
@@ -274,8 +284,8 @@ class Simulation:
     def config(self):
         return iontrap_get_config(self.handle)
 
-    def set_config(self, threads, ions_per_thread, jsplit) -> None:
-        iontrap_set_config(self.handle, threads, ions_per_thread, jsplit)
+    def set_config(self, threads, ions_per_thread, packed, jsplit) -> None:
+        iontrap_set_config(self.handle, threads, ions_per_thread, packed, jsplit)
 
     def close(self) -> None:
         if self.handle is not None:
