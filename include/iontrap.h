@@ -161,15 +161,25 @@ int iontrap_stable(const iontrap_species *species, int n_species, const iontrap_
 int iontrap_normals(uint64_t seed, int64_t counter, const int64_t *ids, int64_t m,
                     int precision, double *z);
 
-/* Tile configuration of a handle's force kernel: threads per CTA, ions per thread,
- * packed (1 = the FP32 pair arithmetic runs on packed FP32x2 instructions, two ions per
- * instruction; bitwise identical to 0) and the j-range per CTA (grid.y = ceil(n/jsplit)).
- * iontrap_get_config reads it; iontrap_set_config changes it (the autotuner's knob;
- * EINVAL for a combination without a compiled kernel, jsplit < 1 or > n, or > 2048 in
- * the FP64 form).  Results depend only on (n, threads*ions_per_thread, jsplit) and the
- * parameters: equal configurations give bitwise equal trajectories. */
-int iontrap_get_config(const iontrap_t *h, int *threads, int *ions_per_thread, int *packed, int *jsplit);
-int iontrap_set_config(iontrap_t *h, int threads, int ions_per_thread, int packed, int jsplit);
+/* Launch configuration of a handle's step kernels. */
+typedef struct {
+    int32_t threads;          /* CTA size of the force kernel (64, 128, 256) */
+    int32_t ions_per_thread;  /* ions held in registers per thread (1, 2, 4) */
+    int32_t packed;           /* 1: the FP32 pair arithmetic runs on packed FP32x2 instructions,
+                                 two ions per instruction; bitwise identical to 0 */
+    int32_t jsplit;           /* j-range per CTA: grid.y = ceil(n / jsplit) */
+    int32_t fused;            /* 1: the last CTA of each i-block merges the split partials and
+                                 integrates; 0: a separate epilogue kernel does, one ion per
+                                 thread over all SMs.  The FP64 form supports 1 only. */
+} iontrap_config;
+
+/* iontrap_get_config reads a handle's configuration; iontrap_set_config changes it (the
+ * autotuner's knob).  EINVAL for a combination without a compiled kernel, jsplit < 1 or
+ * > n, or jsplit > 2048 in the FP64 form.  Results depend only on n, the product
+ * threads*ions_per_thread, jsplit and the parameters: configurations equal in those
+ * give bitwise equal trajectories. */
+int iontrap_get_config(const iontrap_t *h, iontrap_config *cfg);
+int iontrap_set_config(iontrap_t *h, const iontrap_config *cfg);
 
 /* Microbenchmark of the pipes the step kernels use (not part of the method): runs
  * independent dependency chains of one instruction kind on every SM of the current

@@ -16,7 +16,8 @@
 #include "iontrap_internal.cuh"
 
 namespace it {
-const void* step_kernel(int f64, int T, int I, int packed);
+const void* step_kernel(int f64, int T, int I, int packed, int fused);
+const void* epilogue_kernel(int f64);
 const void* prep_kernel();
 const void* restore_kernel();
 cudaError_t launch_normals(unsigned long long seed, long long counter, const long long* d_ids, long long m,
@@ -50,7 +51,7 @@ struct iontrap {
   long long* d_step = nullptr;
   int* d_err = nullptr;
   // launch configuration
-  int T = 128, I = 1, packed = 0, jsplit = 128;
+  int T = 128, I = 1, packed = 0, jsplit = 128, fused = 1;
   StepArgs args{};
   // graph of kGraphSteps chained steps
   cudaGraph_t graph = nullptr;
@@ -185,7 +186,8 @@ int64_t gcd64(int64_t a, int64_t b) {
 // blocks keep the FP64 epilogue of the last CTA short, large ones reuse each staged j
 // over more ions.  The number of j-splits S makes the grid a multiple of the SM count
 // (equal work per SM) with at least two CTAs per SM where n allows.
-void default_config(int64_t n, int f64, int sms, int* T, int* I, int* packed, int* jsplit) {
+void default_config(int64_t n, int f64, int sms, int* T, int* I, int* packed, int* jsplit, int* fused) {
+  *fused = (f64 || n > 16384) ? 1 : 0;
   if (f64) {
     *T = 128;
     *I = 1;
@@ -267,6 +269,7 @@ int alloc_scratch(iontrap* h) {
   h->args.part = h->d_part;
   h->args.cnt = h->d_cnt;
   h->args.jsplit = (h->p.flags & IONTRAP_COULOMB_OFF) ? (int)std::min<int64_t>(h->n, 1 << 30) : h->jsplit;
+  h->args.nsplit = (int)splits;
   return IONTRAP_OK;
 }
 
@@ -284,7 +287,12 @@ cudaError_t launch_step_on(iontrap* h, StepArgs& a, cudaStream_t st) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   void* params[] = {&a};
-  return cudaLaunchKernelExC(&cfg, step_kernel(h->f64, h->T, h->I, h->packed), params);
+  cudaError_t e = cudaLaunchKernelExC(&cfg, step_kernel(h->f64, h->T, h->I, h->packed, h->fused), params);
+  if (e != cudaSuccess || h->fused) return e;
+  cfg.gridDim = dim3((unsigned)cdiv(h->n, 32));
+  cfg.blockDim = dim3(32);
+  cfg.dynamicSmemBytes = 0;
+  return cudaLaunchKernelExC(&cfg, epilogue_kernel(h->f64), params);
 }
 
 cudaError_t launch_mode(iontrap* h, int mode, double* out) {
@@ -341,7 +349,7 @@ int prepare_kernels() {
   const int Is[] = {1, 2, 4};
   for (int T : Ts)
     for (int I : Is) {
-      const void* fn = step_kernel(1, T, I, 0);
+      const void* fn = step_kernel(1, T, I, 0, 1);
       if (fn && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxJsplitF64 * 32) !=
                     cudaSuccess)
         return IONTRAP_ECUDA;
@@ -435,7 +443,7 @@ int iontrap_create(const iontrap_species* species, int n_species, const uint8_t*
     }
     h->own_stream = true;
   }
-  default_config(n, h->f64, h->sms, &h->T, &h->I, &h->packed, &h->jsplit);
+  default_config(n, h->f64, h->sms, &h->T, &h->I, &h->packed, &h->jsplit, &h->fused);
 
   // species table
   const double dt = h->p.dt;
@@ -670,27 +678,29 @@ int iontrap_normals(uint64_t seed, int64_t counter, const int64_t* ids, int64_t 
   return e == cudaSuccess ? IONTRAP_OK : IONTRAP_ECUDA;
 }
 
-int iontrap_get_config(const iontrap_t* h, int* threads, int* ions_per_thread, int* packed, int* jsplit) {
-  if (!h) return IONTRAP_EINVAL;
-  if (threads) *threads = h->T;
-  if (ions_per_thread) *ions_per_thread = h->I;
-  if (packed) *packed = h->packed;
-  if (jsplit) *jsplit = h->jsplit;
+int iontrap_get_config(const iontrap_t* h, iontrap_config* c) {
+  if (!h || !c) return IONTRAP_EINVAL;
+  c->threads = h->T;
+  c->ions_per_thread = h->I;
+  c->packed = h->packed;
+  c->jsplit = h->jsplit;
+  c->fused = h->fused;
   return IONTRAP_OK;
 }
 
-int iontrap_set_config(iontrap_t* h, int threads, int ions_per_thread, int packed, int jsplit) {
-  if (!h) return IONTRAP_EINVAL;
-  if (!step_kernel(h->f64, threads, ions_per_thread, packed)) return IONTRAP_EINVAL;
-  if (jsplit < 1 || jsplit > h->n || (h->f64 && jsplit > kMaxJsplitF64)) return IONTRAP_EINVAL;
+int iontrap_set_config(iontrap_t* h, const iontrap_config* c) {
+  if (!h || !c) return IONTRAP_EINVAL;
+  if (!step_kernel(h->f64, c->threads, c->ions_per_thread, c->packed, c->fused)) return IONTRAP_EINVAL;
+  if (c->jsplit < 1 || c->jsplit > h->n || (h->f64 && c->jsplit > kMaxJsplitF64)) return IONTRAP_EINVAL;
   if (h->status) return h->status;
   DeviceGuard g(h->device);
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_status(h, e);
-  h->T = threads;
-  h->I = ions_per_thread;
-  h->packed = packed;
-  h->jsplit = jsplit;
+  h->T = c->threads;
+  h->I = c->ions_per_thread;
+  h->packed = c->packed;
+  h->jsplit = c->jsplit;
+  h->fused = c->fused;
   destroy_graph(h);
   const int st = alloc_scratch(h);
   if (st) return set_status(h, st);

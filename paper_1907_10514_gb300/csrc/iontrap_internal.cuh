@@ -62,6 +62,7 @@ struct StepArgs {
   double* out;         // MODE_FORCES output [3][n]
   int mode;
   int jsplit;          // j-range per CTA (grid.y = ceil(n / jsplit))
+  int nsplit;          // ceil(n / jsplit): partials per ion for the epilogue kernel
   TrapDev trap;
   SpeciesDev spc[IONTRAP_MAX_SPECIES];
 };
@@ -234,19 +235,23 @@ __device__ __forceinline__ void epilogue_ion(const StepArgs& A, long long i, con
     vd[c] = step ? vh : v;
     xf[c] = step ? drift(x, vh, tp.dt) : x;
   }
+  // Explicit roundings (no FMA contraction left to the compiler): every kernel that
+  // inlines this epilogue produces the same bits.
   double acc[3];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) acc[c] = sd.coul * S[c];
+  for (int c = 0; c < 3; ++c) acc[c] = __dmul_rn(sd.coul, S[c]);
   if (!(tp.flags & IONTRAP_TRAP_OFF)) {
-    const double rwz2 = sd.rho * tp.wz2;
-    const double kx = tp.q4 * sd.rho * (tp.a - 2.0 * tp.q * cosv) - 0.5 * rwz2;
-    const double ky = tp.q4 * sd.rho * (tp.a + 2.0 * tp.q * cosv) - 0.5 * rwz2;
-    acc[0] -= kx * xf[0];
-    acc[1] -= ky * xf[1];
-    acc[2] -= rwz2 * xf[2];
+    const double rwz2 = __dmul_rn(sd.rho, tp.wz2);
+    const double rq4 = __dmul_rn(tp.q4, sd.rho);
+    const double qc2 = __dmul_rn(2.0 * tp.q, cosv);
+    const double kx = __fma_rn(rq4, __dsub_rn(tp.a, qc2), -0.5 * rwz2);
+    const double ky = __fma_rn(rq4, __dadd_rn(tp.a, qc2), -0.5 * rwz2);
+    acc[0] = __fma_rn(-kx, xf[0], acc[0]);
+    acc[1] = __fma_rn(-ky, xf[1], acc[1]);
+    acc[2] = __fma_rn(-rwz2, xf[2], acc[2]);
   }
 #pragma unroll
-  for (int c = 0; c < 3; ++c) acc[c] -= tp.gamma * vd[c];
+  for (int c = 0; c < 3; ++c) acc[c] = __fma_rn(-tp.gamma, vd[c], acc[c]);
   if (sd.sigma > 0.0) {
     double z[3];
     const long long counter = step ? ns + 1 : ns;

@@ -149,10 +149,53 @@ __device__ __forceinline__ double force_time_cos(const StepArgs& A, long long ns
   return cos(A.trap.Omega * ((double)nf * A.trap.dt));
 }
 
+// Merge of the split partials of ion i, in split order.  FP32 form: compensated
+// (Kahan) addition of the per-split (sum, compensation) pairs; the accumulators hold
+// the negated sum, hence the sign.  FP64 form: plain FP64 sum.
+__device__ __forceinline__ void merge_f32(const float* __restrict__ part, long long n, long long i, int nsplit,
+                                          double S[3]) {
+  constexpr int U = 8;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float s = 0.0f, cc = 0.0f;
+    for (int p0 = 0; p0 < nsplit; p0 += U) {
+      float ps[U], pc[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        ps[u] = pc[u] = 0.0f;
+        if (p0 + u < nsplit) {
+          ps[u] = __ldcg(part + (((p0 + u) * 3ll + c) * 2 + 0) * n + i);
+          pc[u] = __ldcg(part + (((p0 + u) * 3ll + c) * 2 + 1) * n + i);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (p0 + u < nsplit) {
+          const float y = ps[u] - cc;
+          const float t = s + y;
+          cc = ((t - s) - y) + pc[u];
+          s = t;
+        }
+      }
+    }
+    S[c] = (double)cc - (double)s;
+  }
+}
+
+__device__ __forceinline__ void merge_f64(const double* __restrict__ part, long long n, long long i, int nsplit,
+                                          double S[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    double s = 0.0;
+    for (int p = 0; p < nsplit; ++p) s += __ldcg(part + (p * 3ll + c) * n + i);
+    S[c] = s;
+  }
+}
+
 // ------------------------------------------------------------------ FP32 form
 constexpr int kChunk = kSeg;  // j-chunk staged per TMA transaction = one Kahan segment
 
-template <int T, int I, bool PACK>
+template <int T, int I, bool PACK, bool FUSED>
 __global__ void __launch_bounds__(T) k_step_f32(const __grid_constant__ StepArgs A) {
   __shared__ __align__(128) float4 sh[2][kChunk];
   __shared__ __align__(128) float4 sl[2][kChunk];
@@ -289,47 +332,59 @@ __global__ void __launch_bounds__(T) k_step_f32(const __grid_constant__ StepArgs
       }
     }
   }
+  if constexpr (!FUSED) return;  // the epilogue kernel merges the partials
   if (!arrive_last(&A.cnt[blockIdx.x], gridDim.y, &s_flag)) return;
 
   if (tid == 0) s_cos = force_time_cos(A, ns);
   __syncthreads();
   const double cosv = s_cos;
   const int wb = rb ^ 1;
-  const int nsplit = gridDim.y;
-  constexpr int U = 8;
 #pragma unroll
   for (int k = 0; k < I; ++k) {
     const long long i = i0 + k * T + tid;
     if (i >= n) continue;
     double S[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      float s = 0.0f, cc = 0.0f;
-      for (int p0 = 0; p0 < nsplit; p0 += U) {
-        float ps[U], pc[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          ps[u] = pc[u] = 0.0f;
-          if (p0 + u < nsplit) {
-            ps[u] = __ldcg(part + (((p0 + u) * 3ll + c) * 2 + 0) * n + i);
-            pc[u] = __ldcg(part + (((p0 + u) * 3ll + c) * 2 + 1) * n + i);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          if (p0 + u < nsplit) {
-            const float y = ps[u] - cc;
-            const float t = s + y;
-            cc = ((t - s) - y) + pc[u];
-            s = t;
-          }
-        }
-      }
-      S[c] = (double)cc - (double)s;  // the accumulators hold the negated sum
-    }
+    merge_f32(part, n, i, (int)gridDim.y, S);
     epilogue_ion<false>(A, i, S, cosv, ns, wb);
   }
   finish_iblock(A, ns);
+}
+
+// Separate epilogue (one ion per thread over all SMs): merge the split partials of the
+// force kernel that just ran and integrate.  Used where the FP64 epilogue of a few
+// last CTAs would otherwise sit on the critical path.  The last CTA advances the step.
+template <bool F64>
+__global__ void __launch_bounds__(32) k_epilogue(const __grid_constant__ StepArgs A) {
+  __shared__ double s_cos;
+  __shared__ int s_last;
+  pdl_trigger();
+  pdl_wait();
+  const long long n = A.n;
+  const long long ns = *A.step;
+  const int rb = (A.mode == MODE_STEP) ? (int)((ns + 1) & 1) : (int)(ns & 1);
+  if (threadIdx.x == 0) s_cos = force_time_cos(A, ns);
+  __syncthreads();
+  const long long i = blockIdx.x * 32ll + threadIdx.x;
+  if (i < n) {
+    double S[3];
+    if (F64)
+      merge_f64(reinterpret_cast<const double*>(A.part), n, i, A.nsplit, S);
+    else
+      merge_f32(reinterpret_cast<const float*>(A.part), n, i, A.nsplit, S);
+    epilogue_ion<F64>(A, i, S, s_cos, ns, rb ^ 1);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(A.done, 1u);
+    s_last = (prev == gridDim.x - 1u);
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
+    *A.done = 0u;
+    if (A.mode == MODE_STEP) *A.step = ns + 1;
+    __threadfence();
+  }
 }
 
 // ------------------------------------------------------------------ FP64 plain form
@@ -370,7 +425,7 @@ __global__ void __launch_bounds__(T) k_step_f64(const __grid_constant__ StepArgs
   const long long n = A.n;
   const long long i0 = (long long)blockIdx.x * (T * I);
   const long long j0 = (long long)blockIdx.y * A.jsplit;
-  const int jn = (int)min((long long)A.jsplit, n - j0);
+  const int jn = (int)min((long long)A.jsplit, n - j0);  // FP64 form: whole j-range staged
   const long long ns = *A.step;
   const int rb = (A.mode == MODE_STEP) ? (int)((ns + 1) & 1) : (int)(ns & 1);
   const bool coulomb = !(A.trap.flags & IONTRAP_COULOMB_OFF);
@@ -424,12 +479,7 @@ __global__ void __launch_bounds__(T) k_step_f64(const __grid_constant__ StepArgs
     const long long i = i0 + k * T + tid;
     if (i >= n) continue;
     double S[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      double s = 0.0;
-      for (int p = 0; p < nsplit; ++p) s += __ldcg(part + (p * 3ll + c) * n + i);
-      S[c] = s;
-    }
+    merge_f64(part, n, i, nsplit, S);
     epilogue_ion<true>(A, i, S, cosv, ns, wb);
   }
   finish_iblock(A, ns);
@@ -482,26 +532,29 @@ __global__ void k_normals(unsigned long long seed, long long counter, const long
 
 // ------------------------------------------------------------------ registry
 struct KernelEntry {
-  int f64, T, I, packed;
+  int f64, T, I, packed, fused;
   const void* fn;
 };
 
+#define IT_F32(T, I, P) {0, T, I, P, 1, (const void*)k_step_f32<T, I, P, true>}, \
+                        {0, T, I, P, 0, (const void*)k_step_f32<T, I, P, false>}
 static const KernelEntry kKernels[] = {
-    {0, 64, 1, 0, (const void*)k_step_f32<64, 1, false>},    {0, 64, 2, 0, (const void*)k_step_f32<64, 2, false>},
-    {0, 64, 2, 1, (const void*)k_step_f32<64, 2, true>},     {0, 64, 4, 1, (const void*)k_step_f32<64, 4, true>},
-    {0, 128, 1, 0, (const void*)k_step_f32<128, 1, false>},  {0, 128, 2, 0, (const void*)k_step_f32<128, 2, false>},
-    {0, 128, 2, 1, (const void*)k_step_f32<128, 2, true>},   {0, 128, 4, 0, (const void*)k_step_f32<128, 4, false>},
-    {0, 128, 4, 1, (const void*)k_step_f32<128, 4, true>},   {0, 256, 2, 1, (const void*)k_step_f32<256, 2, true>},
-    {0, 256, 4, 1, (const void*)k_step_f32<256, 4, true>},   {0, 256, 4, 0, (const void*)k_step_f32<256, 4, false>},
-    {1, 64, 1, 0, (const void*)k_step_f64<64, 1>},           {1, 128, 1, 0, (const void*)k_step_f64<128, 1>},
-    {1, 128, 2, 0, (const void*)k_step_f64<128, 2>},         {1, 256, 1, 0, (const void*)k_step_f64<256, 1>},
+    IT_F32(64, 1, false),  IT_F32(64, 2, false),  IT_F32(64, 2, true),  IT_F32(64, 4, true),
+    IT_F32(128, 1, false), IT_F32(128, 2, false), IT_F32(128, 2, true), IT_F32(128, 4, false),
+    IT_F32(128, 4, true),  IT_F32(256, 1, false), IT_F32(256, 2, true), IT_F32(256, 4, true),
+    IT_F32(256, 4, false),
+    {1, 64, 1, 0, 1, (const void*)k_step_f64<64, 1>},   {1, 128, 1, 0, 1, (const void*)k_step_f64<128, 1>},
+    {1, 128, 2, 0, 1, (const void*)k_step_f64<128, 2>}, {1, 256, 1, 0, 1, (const void*)k_step_f64<256, 1>},
 };
+#undef IT_F32
 
-const void* step_kernel(int f64, int T, int I, int packed) {
+const void* step_kernel(int f64, int T, int I, int packed, int fused) {
   for (const auto& e : kKernels)
-    if (e.f64 == f64 && e.T == T && e.I == I && e.packed == packed) return e.fn;
+    if (e.f64 == f64 && e.T == T && e.I == I && e.packed == packed && e.fused == fused) return e.fn;
   return nullptr;
 }
+
+const void* epilogue_kernel(int f64) { return f64 ? (const void*)k_epilogue<true> : (const void*)k_epilogue<false>; }
 
 const void* prep_kernel() { return (const void*)k_prep; }
 const void* restore_kernel() { return (const void*)k_restore; }

@@ -47,6 +47,11 @@ class iontrap_params(ctypes.Structure):
                 ("precision", ctypes.c_int32)]
 
 
+class iontrap_config(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("ions_per_thread", ctypes.c_int32),
+                ("packed", ctypes.c_int32), ("jsplit", ctypes.c_int32), ("fused", ctypes.c_int32)]
+
+
 # symbol name -> (restype, argtypes)
 _dp = ctypes.POINTER(ctypes.c_double)
 _i64p = ctypes.POINTER(ctypes.c_int64)
@@ -70,8 +75,8 @@ SIGNATURES = {
                                       ctypes.POINTER(iontrap_params), _ip]),
     "iontrap_normals": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int64, _i64p, ctypes.c_int64,
                                        ctypes.c_int, _dp]),
-    "iontrap_get_config": (ctypes.c_int, [_vp, _ip, _ip, _ip, _ip]),
-    "iontrap_set_config": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "iontrap_get_config": (ctypes.c_int, [_vp, ctypes.POINTER(iontrap_config)]),
+    "iontrap_set_config": (ctypes.c_int, [_vp, ctypes.POINTER(iontrap_config)]),
     "iontrap_alu_probe": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_longlong, _dp, _dp]),
 }
 
@@ -235,16 +240,15 @@ def iontrap_normals(seed: int, counter: int, ids, precision: int = IONTRAP_PREC_
 
 
 def iontrap_get_config(h):
-    """Returns (threads, ions_per_thread, packed, jsplit)."""
-    T, I, P, J = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    _check(_lib.iontrap_get_config(h, ctypes.byref(T), ctypes.byref(I), ctypes.byref(P), ctypes.byref(J)),
-           "iontrap_get_config")
-    return T.value, I.value, P.value, J.value
+    """Returns (threads, ions_per_thread, packed, jsplit, fused)."""
+    c = iontrap_config()
+    _check(_lib.iontrap_get_config(h, ctypes.byref(c)), "iontrap_get_config")
+    return c.threads, c.ions_per_thread, c.packed, c.jsplit, c.fused
 
 
-def iontrap_set_config(h, threads: int, ions_per_thread: int, packed: int, jsplit: int) -> None:
-    _check(_lib.iontrap_set_config(h, int(threads), int(ions_per_thread), int(packed), int(jsplit)),
-           "iontrap_set_config")
+def iontrap_set_config(h, threads: int, ions_per_thread: int, packed: int, jsplit: int, fused: int = 1) -> None:
+    c = iontrap_config(int(threads), int(ions_per_thread), int(packed), int(jsplit), int(fused))
+    _check(_lib.iontrap_set_config(h, ctypes.byref(c)), "iontrap_set_config")
 
 
 def iontrap_alu_probe(kind: int, iters: int = 20000):
@@ -284,8 +288,8 @@ class Simulation:
     def config(self):
         return iontrap_get_config(self.handle)
 
-    def set_config(self, threads, ions_per_thread, packed, jsplit) -> None:
-        iontrap_set_config(self.handle, threads, ions_per_thread, packed, jsplit)
+    def set_config(self, threads, ions_per_thread, packed, jsplit, fused=1) -> None:
+        iontrap_set_config(self.handle, threads, ions_per_thread, packed, jsplit, fused)
 
     def close(self) -> None:
         if self.handle is not None:

@@ -83,8 +83,8 @@ def test_forces_match_oracle(it, n):
             assert rel_rms(f, ref) < tol, (n, prec)
 
 
-@pytest.mark.parametrize("cfg", [(64, 1, 0, 128), (64, 4, 1, 256), (128, 2, 1, 384), (256, 2, 1, 3001),
-                                 (256, 4, 0, 100), (128, 4, 1, 1152), (128, 1, 0, 7), (64, 2, 0, 1000)])
+@pytest.mark.parametrize("cfg", [(64, 1, 0, 128, 1), (64, 4, 1, 256, 0), (128, 2, 1, 384, 1), (256, 2, 1, 3001, 0),
+                                 (256, 4, 0, 100, 1), (128, 4, 1, 1152, 0), (128, 1, 0, 7, 1), (64, 2, 0, 1000, 0)])
 def test_forces_every_tile_config(it, cfg):
     n = 3001
     w = _cloud(n, 5)
@@ -312,17 +312,19 @@ def test_bitwise_determinism_and_graph_split(it):
     assert np.array_equal(xa, xc) and np.array_equal(va, vc)
 
 
-def test_packed_fp32x2_is_bitwise_scalar(it):
-    """The packed FP32x2 pair loop rounds lane by lane as the scalar loop does."""
+def test_packed_and_fused_variants_are_bitwise_equal(it):
+    """The packed FP32x2 pair loop rounds lane by lane as the scalar loop does, and the
+    separate epilogue kernel merges the partials exactly as the fused one does."""
     w = _cloud(2100, 12)
     outs = []
-    for packed in (0, 1):
+    for packed, fused in ((0, 1), (1, 1), (1, 0), (0, 0)):
         with _sim(it, w, 0) as sim:
-            sim.set_config(128, 2, packed, 700)
+            sim.set_config(128, 2, packed, 700, fused)
             f = sim.forces()
             sim.step(120)
             outs.append((f, sim.state()[0]))
-    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    for f, x in outs[1:]:
+        assert np.array_equal(outs[0][0], f) and np.array_equal(outs[0][1], x)
 
 
 def test_step_many_equals_alone(it):
