@@ -175,11 +175,19 @@ typedef struct {
 
 /* iontrap_get_config reads a handle's configuration; iontrap_set_config changes it (the
  * autotuner's knob).  EINVAL for a combination without a compiled kernel, jsplit < 1 or
- * > n, or jsplit > 2048 in the FP64 form.  Results depend only on n, the product
+ * > n, jsplit > 2048 in the FP64 form, or more than 64 splits when not fused.  Results depend only on n, the product
  * threads*ions_per_thread, jsplit and the parameters: configurations equal in those
  * give bitwise equal trajectories. */
 int iontrap_get_config(const iontrap_t *h, iontrap_config *cfg);
 int iontrap_set_config(iontrap_t *h, const iontrap_config *cfg);
+
+/* Profiling hook: run ONE step with per-CTA phase timestamps (%globaltimer, ns) and copy
+ * them to marks[cap].  Layout: 4 marks per force-kernel CTA, CTA id = y*grid.x + x
+ * (start after the grid dependency wait, end of the pair loop, start of the fused
+ * epilogue or 0, end of the fused epilogue or 0), then 2 per epilogue-kernel CTA (start,
+ * end) when the configuration is not fused.  *n_force and *n_epi receive the counts.
+ * Synchronous; EINVAL if cap is too small. */
+int iontrap_trace_step(iontrap_t *h, unsigned long long *marks, int64_t cap, int64_t *n_force, int64_t *n_epi);
 
 /* Microbenchmark of the pipes the step kernels use (not part of the method): runs
  * independent dependency chains of one instruction kind on every SM of the current

@@ -28,6 +28,7 @@ using namespace it;
 
 static constexpr int kGraphSteps = 100;
 static constexpr int kMaxJsplitF64 = 2048;  // FP64 form stages its whole j-range
+static constexpr int64_t kMaxSplitsUnfused = 64;   // records one epilogue lane group folds
 
 struct iontrap {
   int64_t n = 0;
@@ -187,7 +188,7 @@ int64_t gcd64(int64_t a, int64_t b) {
 // over more ions.  The number of j-splits S makes the grid a multiple of the SM count
 // (equal work per SM) with at least two CTAs per SM where n allows.
 void default_config(int64_t n, int f64, int sms, int* T, int* I, int* packed, int* jsplit, int* fused) {
-  *fused = (f64 || n > 16384) ? 1 : 0;
+  *fused = f64 ? 1 : 0;
   if (f64) {
     *T = 128;
     *I = 1;
@@ -210,6 +211,7 @@ void default_config(int64_t n, int f64, int sms, int* T, int* I, int* packed, in
   if (S > s_max) S = std::max<int64_t>(1, std::min(s_max, cdiv(2 * (int64_t)sms, iblocks)));
   int64_t js = cdiv(n, S);
   if (f64) js = std::min<int64_t>(js, kMaxJsplitF64);
+  if (!*fused && cdiv(n, js) > kMaxSplitsUnfused) js = cdiv(n, kMaxSplitsUnfused);
   *jsplit = (int)js;
 }
 
@@ -247,8 +249,8 @@ void destroy_graph(iontrap* h) {
 // (Re)allocate the scratch that depends on the tile configuration.
 int alloc_scratch(iontrap* h) {
   const int64_t splits = splits_of(h);
-  // FP32 form: a (sum, compensation) float pair per component; FP64 form: a double
-  const size_t part = (size_t)splits * 3 * (size_t)h->n * 8;
+  // one 32-byte record per (split, ion) in both forms
+  const size_t part = (size_t)splits * (size_t)h->n * 32;
   const size_t cnt = (size_t)cdiv(h->n, (int64_t)h->T * h->I);
   if (part > h->part_bytes) {
     if (h->d_part) cudaFree(h->d_part);
@@ -289,8 +291,8 @@ cudaError_t launch_step_on(iontrap* h, StepArgs& a, cudaStream_t st) {
   void* params[] = {&a};
   cudaError_t e = cudaLaunchKernelExC(&cfg, step_kernel(h->f64, h->T, h->I, h->packed, h->fused), params);
   if (e != cudaSuccess || h->fused) return e;
-  cfg.gridDim = dim3((unsigned)cdiv(h->n, 32));
-  cfg.blockDim = dim3(32);
+  cfg.gridDim = dim3((unsigned)cdiv(h->n, 32));  // 32 ions per epilogue CTA
+  cfg.blockDim = dim3(256);
   cfg.dynamicSmemBytes = 0;
   return cudaLaunchKernelExC(&cfg, epilogue_kernel(h->f64), params);
 }
@@ -639,6 +641,35 @@ int iontrap_restore(iontrap_t* h, const double* x, const double* v, const double
   return h->status;
 }
 
+int iontrap_trace_step(iontrap_t* h, unsigned long long* marks, int64_t cap, int64_t* n_force, int64_t* n_epi) {
+  if (!h || !marks || cap < 1) return IONTRAP_EINVAL;
+  int st = iontrap_sync(h);
+  if (st) return st;
+  DeviceGuard g(h->device);
+  const dim3 grid = grid_of(h);
+  const int64_t nf = 4 * (int64_t)grid.x * grid.y;
+  const int64_t ne = h->fused ? 0 : 2 * cdiv(h->n, 32);
+  if (nf + ne > cap) return IONTRAP_EINVAL;
+  unsigned long long* d = nullptr;
+  if (cudaMalloc(&d, (nf + ne) * sizeof(unsigned long long)) != cudaSuccess) return IONTRAP_ENOMEM;
+  cudaError_t e = cudaMemsetAsync(d, 0, (nf + ne) * sizeof(unsigned long long), h->stream);
+  StepArgs a = h->args;
+  a.mode = MODE_STEP;
+  a.out = nullptr;
+  a.trace = d;
+  a.trace_epi = nf;
+  if (e == cudaSuccess) e = launch_step_on(h, a, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(marks, d, (nf + ne) * sizeof(unsigned long long),
+                                            cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_status(h, e);
+  h->step += 1;
+  if (n_force) *n_force = nf;
+  if (n_epi) *n_epi = ne;
+  return iontrap_sync(h);
+}
+
 int iontrap_step_many(iontrap_t* const* hs, const int64_t* n_steps, int count) {
   if (!hs || !n_steps || count < 0) return IONTRAP_EINVAL;
   int first = IONTRAP_OK;
@@ -692,6 +723,7 @@ int iontrap_set_config(iontrap_t* h, const iontrap_config* c) {
   if (!h || !c) return IONTRAP_EINVAL;
   if (!step_kernel(h->f64, c->threads, c->ions_per_thread, c->packed, c->fused)) return IONTRAP_EINVAL;
   if (c->jsplit < 1 || c->jsplit > h->n || (h->f64 && c->jsplit > kMaxJsplitF64)) return IONTRAP_EINVAL;
+  if (!c->fused && cdiv(h->n, c->jsplit) > kMaxSplitsUnfused) return IONTRAP_EINVAL;
   if (h->status) return h->status;
   DeviceGuard g(h->device);
   cudaError_t e = cudaStreamSynchronize(h->stream);

@@ -60,6 +60,8 @@ struct StepArgs {
   long long* step;     // state step index n (device resident)
   int* err;            // ErrBits, sticky
   double* out;         // MODE_FORCES output [3][n]
+  unsigned long long* trace;  // optional per-CTA phase timestamps (globaltimer ns), or null
+  long long trace_epi;        // offset of the epilogue kernel's marks in trace
   int mode;
   int jsplit;          // j-range per CTA (grid.y = ceil(n / jsplit))
   int nsplit;          // ceil(n / jsplit): partials per ion for the epilogue kernel
@@ -127,6 +129,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 }
 
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
+
+// Phase timestamp of this CTA into the optional trace buffer (thread 0 only).
+__device__ __forceinline__ void trace_mark(unsigned long long* trace, long long slot) {
+  if (trace && threadIdx.x == 0) trace[slot] = globaltimer_ns();
+}
 
 // ------------------------------------------------------------------ Philox-4x64-10
 // Salmon et al., SC'11: ten rounds of two 64x64 -> 128-bit products; key bumped by the

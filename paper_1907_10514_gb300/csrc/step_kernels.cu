@@ -149,47 +149,54 @@ __device__ __forceinline__ double force_time_cos(const StepArgs& A, long long ns
   return cos(A.trap.Omega * ((double)nf * A.trap.dt));
 }
 
-// Merge of the split partials of ion i, in split order.  FP32 form: compensated
-// (Kahan) addition of the per-split (sum, compensation) pairs; the accumulators hold
-// the negated sum, hence the sign.  FP64 form: plain FP64 sum.
-__device__ __forceinline__ void merge_f32(const float* __restrict__ part, long long n, long long i, int nsplit,
-                                          double S[3]) {
-  constexpr int U = 8;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    float s = 0.0f, cc = 0.0f;
-    for (int p0 = 0; p0 < nsplit; p0 += U) {
-      float ps[U], pc[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        ps[u] = pc[u] = 0.0f;
-        if (p0 + u < nsplit) {
-          ps[u] = __ldcg(part + (((p0 + u) * 3ll + c) * 2 + 0) * n + i);
-          pc[u] = __ldcg(part + (((p0 + u) * 3ll + c) * 2 + 1) * n + i);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (p0 + u < nsplit) {
-          const float y = ps[u] - cc;
-          const float t = s + y;
-          cc = ((t - s) - y) + pc[u];
-          s = t;
-        }
-      }
-    }
-    S[c] = (double)cc - (double)s;
-  }
+// Split partials are stored as one 32-byte record per (split, ion):
+//   FP32 form: float[8] = (sum_x, sum_y, sum_z, 0, comp_x, comp_y, comp_z, 0)
+//   FP64 form: double[4] = (sum_x, sum_y, sum_z, 0)
+// at record index split * n + i.  The merge runs in split order: FP32 form by
+// compensated (Kahan) addition of the (sum, compensation) pairs -- the accumulators hold
+// the negated sum, hence the sign -- FP64 form by a plain FP64 sum.
+__device__ __forceinline__ void kahan_merge(float& s, float& cc, float ps, float pc) {
+  const float y = ps - cc;
+  const float t = s + y;
+  cc = ((t - s) - y) + pc;
+  s = t;
 }
 
-__device__ __forceinline__ void merge_f64(const double* __restrict__ part, long long n, long long i, int nsplit,
+__device__ __forceinline__ void merge_f32(const float4* __restrict__ part, long long n, long long i, int nsplit,
                                           double S[3]) {
+  float s[3] = {0.f, 0.f, 0.f}, cc[3] = {0.f, 0.f, 0.f};
+  constexpr int U = 4;
+  for (int p0 = 0; p0 < nsplit; p0 += U) {
+    float4 a[U], b[U];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    double s = 0.0;
-    for (int p = 0; p < nsplit; ++p) s += __ldcg(part + (p * 3ll + c) * n + i);
-    S[c] = s;
+    for (int u = 0; u < U; ++u)
+      if (p0 + u < nsplit) {
+        a[u] = __ldcg(part + 2 * ((p0 + u) * n + i));
+        b[u] = __ldcg(part + 2 * ((p0 + u) * n + i) + 1);
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (p0 + u < nsplit) {
+        kahan_merge(s[0], cc[0], a[u].x, b[u].x);
+        kahan_merge(s[1], cc[1], a[u].y, b[u].y);
+        kahan_merge(s[2], cc[2], a[u].z, b[u].z);
+      }
   }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) S[c] = (double)cc[c] - (double)s[c];
+}
+
+__device__ __forceinline__ void merge_f64(const double4_32a* __restrict__ part, long long n, long long i,
+                                          int nsplit, double S[3]) {
+  double s[3] = {0.0, 0.0, 0.0};
+  for (int p = 0; p < nsplit; ++p) {
+    const double2* r = reinterpret_cast<const double2*>(part + p * n + i);
+    const double2 xy = __ldcg(r), zw = __ldcg(r + 1);
+    s[0] += xy.x;
+    s[1] += xy.y;
+    s[2] += zw.x;
+  }
+  S[0] = s[0], S[1] = s[1], S[2] = s[2];
 }
 
 // ------------------------------------------------------------------ FP32 form
@@ -216,6 +223,8 @@ __global__ void __launch_bounds__(T) k_step_f32(const __grid_constant__ StepArgs
   const bool coulomb = !(A.trap.flags & IONTRAP_COULOMB_OFF);
   const float4* __restrict__ ghi = A.hi[rb];
   const float4* __restrict__ glo = A.lo[rb];
+  const long long tslot = 4ll * (blockIdx.y * (long long)gridDim.x + blockIdx.x);
+  trace_mark(A.trace, tslot + 0);
 
   float ks[I][3], kc[I][3];
 #pragma unroll
@@ -319,21 +328,20 @@ __global__ void __launch_bounds__(T) k_step_f32(const __grid_constant__ StepArgs
     }
   }
 
-  // partials: part[((split*3 + c)*2 + {0: sum, 1: compensation}) * n + i]
-  float* part = reinterpret_cast<float*>(A.part);
+  trace_mark(A.trace, tslot + 1);
+  float4* part = reinterpret_cast<float4*>(A.part);
 #pragma unroll
   for (int k = 0; k < I; ++k) {
     const long long i = i0 + k * T + tid;
     if (i < n) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        __stcg(part + ((blockIdx.y * 3ll + c) * 2 + 0) * n + i, ks[k][c]);
-        __stcg(part + ((blockIdx.y * 3ll + c) * 2 + 1) * n + i, kc[k][c]);
-      }
+      const long long r = 2 * (blockIdx.y * n + i);
+      __stcg(part + r, make_float4(ks[k][0], ks[k][1], ks[k][2], 0.0f));
+      __stcg(part + r + 1, make_float4(kc[k][0], kc[k][1], kc[k][2], 0.0f));
     }
   }
   if constexpr (!FUSED) return;  // the epilogue kernel merges the partials
   if (!arrive_last(&A.cnt[blockIdx.x], gridDim.y, &s_flag)) return;
+  trace_mark(A.trace, tslot + 2);
 
   if (tid == 0) s_cos = force_time_cos(A, ns);
   __syncthreads();
@@ -344,17 +352,24 @@ __global__ void __launch_bounds__(T) k_step_f32(const __grid_constant__ StepArgs
     const long long i = i0 + k * T + tid;
     if (i >= n) continue;
     double S[3];
-    merge_f32(part, n, i, (int)gridDim.y, S);
+    merge_f32(part, n, i, (int)gridDim.y, S);  // fused path: the last CTA of the i-block
     epilogue_ion<false>(A, i, S, cosv, ns, wb);
   }
   finish_iblock(A, ns);
+  trace_mark(A.trace, tslot + 3);
 }
 
-// Separate epilogue (one ion per thread over all SMs): merge the split partials of the
-// force kernel that just ran and integrate.  Used where the FP64 epilogue of a few
-// last CTAs would otherwise sit on the critical path.  The last CTA advances the step.
-template <bool F64>
-__global__ void __launch_bounds__(32) k_epilogue(const __grid_constant__ StepArgs A) {
+// Separate epilogue over all SMs.  A CTA of 256 threads serves 32 ions: 8 lanes per ion
+// fetch the ion's split records together (one memory round trip instead of one per
+// split), fold them in split order through warp shuffles, and leave the merged sum in
+// shared memory; then one warp integrates the 32 ions, one per lane.  The last CTA
+// advances the step counter.
+constexpr int kEpiIons = 32;
+constexpr int kEpiThreads = 256;
+constexpr int kEpiMaxRec = 8;  // records per lane: splits up to 8 * 8 = 64
+
+__global__ void __launch_bounds__(kEpiThreads) k_epilogue_f32(const __grid_constant__ StepArgs A) {
+  __shared__ double s_S[kEpiIons][3];
   __shared__ double s_cos;
   __shared__ int s_last;
   pdl_trigger();
@@ -362,16 +377,51 @@ __global__ void __launch_bounds__(32) k_epilogue(const __grid_constant__ StepArg
   const long long n = A.n;
   const long long ns = *A.step;
   const int rb = (A.mode == MODE_STEP) ? (int)((ns + 1) & 1) : (int)(ns & 1);
+  unsigned long long* et = A.trace ? A.trace + A.trace_epi : nullptr;
+  trace_mark(et, 2ll * blockIdx.x);
   if (threadIdx.x == 0) s_cos = force_time_cos(A, ns);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int sub = lane & 7;                       // lane within the ion's group of 8
+  const int slot = warp * 4 + (lane >> 3);        // ion slot in this CTA
+  const long long i = blockIdx.x * (long long)kEpiIons + slot;
+  const int nsplit = A.nsplit;
+  const float4* __restrict__ part = reinterpret_cast<const float4*>(A.part);
+  float4 ra[kEpiMaxRec], rc[kEpiMaxRec];
+#pragma unroll
+  for (int q = 0; q < kEpiMaxRec; ++q) {
+    const int p = q * 8 + sub;
+    ra[q] = rc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < n && p < nsplit) {
+      ra[q] = __ldcg(part + 2 * (p * n + i));
+      rc[q] = __ldcg(part + 2 * (p * n + i) + 1);
+    }
+  }
+  float s[3] = {0.f, 0.f, 0.f}, cc[3] = {0.f, 0.f, 0.f};
+  const int base = lane & ~7;
+#pragma unroll
+  for (int q = 0; q < kEpiMaxRec; ++q) {
+    if (q * 8 >= nsplit) break;
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {
+      const int p = q * 8 + l;  // uniform across the warp
+      const float ax = __shfl_sync(0xffffffffu, ra[q].x, base + l), ay = __shfl_sync(0xffffffffu, ra[q].y, base + l);
+      const float az = __shfl_sync(0xffffffffu, ra[q].z, base + l), cx = __shfl_sync(0xffffffffu, rc[q].x, base + l);
+      const float cy = __shfl_sync(0xffffffffu, rc[q].y, base + l), cz = __shfl_sync(0xffffffffu, rc[q].z, base + l);
+      if (p < nsplit) {
+        kahan_merge(s[0], cc[0], ax, cx);
+        kahan_merge(s[1], cc[1], ay, cy);
+        kahan_merge(s[2], cc[2], az, cz);
+      }
+    }
+  }
+  if (sub == 0) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) s_S[slot][c] = (double)cc[c] - (double)s[c];
+  }
   __syncthreads();
-  const long long i = blockIdx.x * 32ll + threadIdx.x;
-  if (i < n) {
-    double S[3];
-    if (F64)
-      merge_f64(reinterpret_cast<const double*>(A.part), n, i, A.nsplit, S);
-    else
-      merge_f32(reinterpret_cast<const float*>(A.part), n, i, A.nsplit, S);
-    epilogue_ion<F64>(A, i, S, s_cos, ns, rb ^ 1);
+  if (warp == 0) {
+    const long long ie = blockIdx.x * (long long)kEpiIons + lane;
+    if (ie < n) epilogue_ion<false>(A, ie, s_S[lane], s_cos, ns, rb ^ 1);
   }
   __threadfence();
   __syncthreads();
@@ -385,6 +435,7 @@ __global__ void __launch_bounds__(32) k_epilogue(const __grid_constant__ StepArg
     if (A.mode == MODE_STEP) *A.step = ns + 1;
     __threadfence();
   }
+  trace_mark(et, 2ll * blockIdx.x + 1);
 }
 
 // ------------------------------------------------------------------ FP64 plain form
@@ -458,13 +509,14 @@ __global__ void __launch_bounds__(T) k_step_f64(const __grid_constant__ StepArgs
     }
   }
 
-  double* part = reinterpret_cast<double*>(A.part);
+  double4_32a* part = reinterpret_cast<double4_32a*>(A.part);
 #pragma unroll
   for (int k = 0; k < I; ++k) {
     const long long i = i0 + k * T + tid;
     if (i < n) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) __stcg(part + (blockIdx.y * 3ll + c) * n + i, acc[k][c]);
+      double2* r = reinterpret_cast<double2*>(part + blockIdx.y * n + i);
+      __stcg(r, make_double2(acc[k][0], acc[k][1]));
+      __stcg(r + 1, make_double2(acc[k][2], 0.0));
     }
   }
   if (!arrive_last(&A.cnt[blockIdx.x], gridDim.y, &s_flag)) return;
@@ -554,7 +606,7 @@ const void* step_kernel(int f64, int T, int I, int packed, int fused) {
   return nullptr;
 }
 
-const void* epilogue_kernel(int f64) { return f64 ? (const void*)k_epilogue<true> : (const void*)k_epilogue<false>; }
+const void* epilogue_kernel(int f64) { return f64 ? nullptr : (const void*)k_epilogue_f32; }
 
 const void* prep_kernel() { return (const void*)k_prep; }
 const void* restore_kernel() { return (const void*)k_restore; }

@@ -77,6 +77,7 @@ SIGNATURES = {
                                        ctypes.c_int, _dp]),
     "iontrap_get_config": (ctypes.c_int, [_vp, ctypes.POINTER(iontrap_config)]),
     "iontrap_set_config": (ctypes.c_int, [_vp, ctypes.POINTER(iontrap_config)]),
+    "iontrap_trace_step": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int64, _i64p, _i64p]),
     "iontrap_alu_probe": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_longlong, _dp, _dp]),
 }
 
@@ -249,6 +250,15 @@ def iontrap_get_config(h):
 def iontrap_set_config(h, threads: int, ions_per_thread: int, packed: int, jsplit: int, fused: int = 1) -> None:
     c = iontrap_config(int(threads), int(ions_per_thread), int(packed), int(jsplit), int(fused))
     _check(_lib.iontrap_set_config(h, ctypes.byref(c)), "iontrap_set_config")
+
+
+def iontrap_trace_step(h, cap: int = 1 << 22):
+    """One traced step: returns (force_marks (k, 4), epilogue_marks (m, 2)) in ns."""
+    buf = np.zeros(cap, dtype=np.uint64)
+    nf, ne = ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.iontrap_trace_step(h, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_ulonglong)), cap,
+                                   ctypes.byref(nf), ctypes.byref(ne)), "iontrap_trace_step")
+    return buf[:nf.value].reshape(-1, 4), buf[nf.value:nf.value + ne.value].reshape(-1, 2)
 
 
 def iontrap_alu_probe(kind: int, iters: int = 20000):
