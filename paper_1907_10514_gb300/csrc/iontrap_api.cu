@@ -458,7 +458,13 @@ int iontrap_create(const iontrap_species* species, int n_species, const uint8_t*
     A.spc[s].rho = (z / species[s].mass_amu) / qm0;
     A.spc[s].sigma = std::sqrt(2.0 * p->gamma * kKB * p->T_bath / (M * dt));
     A.spc[s].w = (float)z;
-    A.spc[s].pad = 0.f;
+    const double rho = A.spc[s].rho, q4 = p->Omega * p->Omega / 4.0;
+    A.spc[s].coulf = (float)A.spc[s].coul;
+    A.spc[s].rakf = (float)(q4 * rho * p->a - 0.5 * rho * p->omega_z * p->omega_z);
+    A.spc[s].rq2f = (float)(q4 * rho * 2.0 * p->q);
+    A.spc[s].rwz2f = (float)(rho * p->omega_z * p->omega_z);
+    A.spc[s].gammaf = (float)p->gamma;
+    A.spc[s].sigmaf = (float)A.spc[s].sigma;
   }
   A.trap.dt = dt;
   A.trap.hdt = 0.5 * dt;

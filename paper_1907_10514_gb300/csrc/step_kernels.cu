@@ -210,7 +210,6 @@ __global__ void __launch_bounds__(T) k_step_f32(const __grid_constant__ StepArgs
   __shared__ int s_flag;
   __shared__ double s_cos;
 
-  pdl_trigger();
   pdl_wait();
   const int tid = threadIdx.x;
   const long long n = A.n;
@@ -329,6 +328,7 @@ __global__ void __launch_bounds__(T) k_step_f32(const __grid_constant__ StepArgs
   }
 
   trace_mark(A.trace, tslot + 1);
+  pdl_trigger();  // dependents launch as the last CTAs finish their pair loops
   float4* part = reinterpret_cast<float4*>(A.part);
 #pragma unroll
   for (int k = 0; k < I; ++k) {
@@ -369,10 +369,8 @@ constexpr int kEpiThreads = 256;
 constexpr int kEpiMaxRec = 8;  // records per lane: splits up to 8 * 8 = 64
 
 __global__ void __launch_bounds__(kEpiThreads) k_epilogue_f32(const __grid_constant__ StepArgs A) {
-  __shared__ double s_S[kEpiIons][3];
   __shared__ double s_cos;
   __shared__ int s_last;
-  pdl_trigger();
   pdl_wait();
   const long long n = A.n;
   const long long ns = *A.step;
@@ -414,14 +412,14 @@ __global__ void __launch_bounds__(kEpiThreads) k_epilogue_f32(const __grid_const
       }
     }
   }
-  if (sub == 0) {
+  pdl_trigger();
+  __syncthreads();  // s_cos
+  // one lane per ion integrates; the 32 ions are spread over the 8 warps (4 per warp)
+  if (sub == 0 && i < n) {
+    double S[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) s_S[slot][c] = (double)cc[c] - (double)s[c];
-  }
-  __syncthreads();
-  if (warp == 0) {
-    const long long ie = blockIdx.x * (long long)kEpiIons + lane;
-    if (ie < n) epilogue_ion<false>(A, ie, s_S[lane], s_cos, ns, rb ^ 1);
+    for (int c = 0; c < 3; ++c) S[c] = (double)cc[c] - (double)s[c];
+    epilogue_ion<false>(A, i, S, s_cos, ns, rb ^ 1);
   }
   __threadfence();
   __syncthreads();
@@ -470,7 +468,6 @@ __global__ void __launch_bounds__(T) k_step_f64(const __grid_constant__ StepArgs
   __shared__ double s_cos;
   double4_32a* sp = reinterpret_cast<double4_32a*>(smraw);
 
-  pdl_trigger();
   pdl_wait();
   const int tid = threadIdx.x;
   const long long n = A.n;
@@ -509,6 +506,7 @@ __global__ void __launch_bounds__(T) k_step_f64(const __grid_constant__ StepArgs
     }
   }
 
+  pdl_trigger();
   double4_32a* part = reinterpret_cast<double4_32a*>(A.part);
 #pragma unroll
   for (int k = 0; k < I; ++k) {
@@ -573,10 +571,13 @@ __global__ void k_normals(unsigned long long seed, long long counter, const long
   const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (k >= m) return;
   double t[3];
-  if (f64)
+  if (f64) {
     normals3_f64(seed, counter, ids[k], t);
-  else
-    normals3_f32(seed, counter, ids[k], t);
+  } else {
+    float tf[3];
+    normals3_f32(seed, counter, ids[k], tf);
+    t[0] = tf[0], t[1] = tf[1], t[2] = tf[2];
+  }
   z[k] = t[0];
   z[m + k] = t[1];
   z[2 * m + k] = t[2];

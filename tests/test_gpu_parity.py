@@ -219,10 +219,11 @@ def test_two_ion_spacing(it, prec, tol):
     assert np.all(x[:2] == 0)
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_single_ion_stroboscopic_recurrence(it, prec):
-    """No Coulomb partner: the epilogue alone (FP64 trap + Verlet) must reproduce the
-    exact one-period Floquet recurrence of the discrete map."""
+@pytest.mark.parametrize("prec,tol", [(0, 1e-6), (1, 1e-9)])
+def test_single_ion_stroboscopic_recurrence(it, prec, tol):
+    """No Coulomb partner: the epilogue alone (trap + Verlet) must reproduce the exact
+    one-period Floquet recurrence of the discrete map -- to rounding in the plain FP64
+    form, to FP32 rounding of the acceleration terms (FP64 Verlet) in the FP32 form."""
     trap = iongen.Trap(Omega=iongen.OMEGA_RF, a=-0.001, q=0.3, omega_z=2 * math.pi * 0.2e6,
                        gamma=0.0, T_bath=0.0, dt=iongen.rf_period_dt(iongen.OMEGA_RF))
     x0 = np.array([[2e-6], [-1.5e-6], [3e-6]])
@@ -245,7 +246,7 @@ def test_single_ion_stroboscopic_recurrence(it, prec):
                           [-0.5 * dt * (k0 + k1) + 0.25 * dt ** 3 * k0 * k1, 1 - 0.5 * dt * dt * k1]]) @ M
         tau = np.trace(M)
         res = s[2:, c] + s[:-2, c] - tau * s[1:-1, c]
-        assert np.abs(res).max() < 1e-9 * np.abs(s[:, c]).max()
+        assert np.abs(res).max() < tol * np.abs(s[:, c]).max()
 
 
 def test_langevin_equipartition(it):
