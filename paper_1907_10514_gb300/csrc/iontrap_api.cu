@@ -52,7 +52,7 @@ struct iontrap {
   long long* d_step = nullptr;
   int* d_err = nullptr;
   // launch configuration
-  int T = 128, I = 1, packed = 0, jsplit = 128, fused = 1;
+  int T = 128, I = 1, packed = 0, jsplit = 128, fused = 1, pdl = 1, use_graph = 1;
   StepArgs args{};
   // graph of kGraphSteps chained steps
   cudaGraph_t graph = nullptr;
@@ -287,7 +287,7 @@ cudaError_t launch_step_on(iontrap* h, StepArgs& a, cudaStream_t st) {
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = h->pdl ? 1 : 0;
   void* params[] = {&a};
   cudaError_t e = cudaLaunchKernelExC(&cfg, step_kernel(h->f64, h->T, h->I, h->packed, h->fused), params);
   if (e != cudaSuccess || h->fused) return e;
@@ -458,13 +458,7 @@ int iontrap_create(const iontrap_species* species, int n_species, const uint8_t*
     A.spc[s].rho = (z / species[s].mass_amu) / qm0;
     A.spc[s].sigma = std::sqrt(2.0 * p->gamma * kKB * p->T_bath / (M * dt));
     A.spc[s].w = (float)z;
-    const double rho = A.spc[s].rho, q4 = p->Omega * p->Omega / 4.0;
-    A.spc[s].coulf = (float)A.spc[s].coul;
-    A.spc[s].rakf = (float)(q4 * rho * p->a - 0.5 * rho * p->omega_z * p->omega_z);
-    A.spc[s].rq2f = (float)(q4 * rho * 2.0 * p->q);
-    A.spc[s].rwz2f = (float)(rho * p->omega_z * p->omega_z);
-    A.spc[s].gammaf = (float)p->gamma;
-    A.spc[s].sigmaf = (float)A.spc[s].sigma;
+    A.spc[s].pad = 0.f;
   }
   A.trap.dt = dt;
   A.trap.hdt = 0.5 * dt;
@@ -545,11 +539,11 @@ int iontrap_step(iontrap_t* h, int64_t n_steps) {
   if (!h || n_steps < 0) return IONTRAP_EINVAL;
   if (h->status) return h->status;
   DeviceGuard g(h->device);
-  if (n_steps >= kGraphSteps && !h->gexec) {
+  if (n_steps >= kGraphSteps && h->use_graph && !h->gexec) {
     cudaError_t e = build_graph(h);
     if (e != cudaSuccess) return cuda_status(h, e);
   }
-  while (n_steps >= kGraphSteps) {
+  while (h->use_graph && n_steps >= kGraphSteps) {
     cudaError_t e = cudaGraphLaunch(h->gexec, h->stream);
     if (e != cudaSuccess) return cuda_status(h, e);
     n_steps -= kGraphSteps;
@@ -722,6 +716,8 @@ int iontrap_get_config(const iontrap_t* h, iontrap_config* c) {
   c->packed = h->packed;
   c->jsplit = h->jsplit;
   c->fused = h->fused;
+  c->pdl = h->pdl;
+  c->graph = h->use_graph;
   return IONTRAP_OK;
 }
 
@@ -739,6 +735,8 @@ int iontrap_set_config(iontrap_t* h, const iontrap_config* c) {
   h->packed = c->packed;
   h->jsplit = c->jsplit;
   h->fused = c->fused;
+  h->pdl = c->pdl ? 1 : 0;
+  h->use_graph = c->graph ? 1 : 0;
   destroy_graph(h);
   const int st = alloc_scratch(h);
   if (st) return set_status(h, st);

@@ -31,13 +31,7 @@ struct SpeciesDev {
   double rho;    // (z/M) / (z_0/M_0): scales a, q and omega_z^2 of species 0
   double sigma;  // sqrt(2 gamma k_B T / (M dt)): std. dev. of the Langevin kick acceleration
   float w;       // z as float, the source weight in the FP32 pair stream
-  // FP32 form's acceleration constants (rounded once from FP64 on the host):
-  float coulf;   // coul
-  float rakf;    // (Omega^2/4) rho a - rho omega_z^2 / 2: static radial spring constant
-  float rq2f;    // (Omega^2/4) rho 2 q: RF spring amplitude, times cos(Omega t)
-  float rwz2f;   // rho omega_z^2
-  float gammaf;  // gamma
-  float sigmaf;  // sigma
+  float pad;
 };
 
 struct TrapDev {
@@ -248,56 +242,37 @@ __device__ __forceinline__ void epilogue_ion(const StepArgs& A, long long i, con
     vd[c] = step ? vh : v;
     xf[c] = step ? drift(x, vh, tp.dt) : x;
   }
-  // Acceleration.  Plain FP64 form: every term in FP64.  FP32 form: the terms (Coulomb
-  // sum, trap field, drag, kick) in FP32 -- the Coulomb sum is FP32-accurate already --
-  // from FP64 positions and velocities and the FP64 RF phase; the Verlet update below
-  // stays FP64.  Explicit roundings (no FMA contraction left to the compiler): every
-  // kernel that inlines this epilogue produces the same bits.
+  // Acceleration terms in FP64 in both forms: the trajectories of these clouds amplify
+  // FP32-sized perturbations of the RF trap term by ~1e4 within 100 steps.  Explicit
+  // roundings (no FMA contraction left to the compiler) make every kernel that inlines
+  // this epilogue produce the same bits.
   double acc[3];
-  if constexpr (F64) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) acc[c] = __dmul_rn(sd.coul, S[c]);
-    if (!(tp.flags & IONTRAP_TRAP_OFF)) {
-      const double rwz2 = __dmul_rn(sd.rho, tp.wz2);
-      const double rq4 = __dmul_rn(tp.q4, sd.rho);
-      const double qc2 = __dmul_rn(2.0 * tp.q, cosv);
-      const double kx = __fma_rn(rq4, __dsub_rn(tp.a, qc2), -0.5 * rwz2);
-      const double ky = __fma_rn(rq4, __dadd_rn(tp.a, qc2), -0.5 * rwz2);
-      acc[0] = __fma_rn(-kx, xf[0], acc[0]);
-      acc[1] = __fma_rn(-ky, xf[1], acc[1]);
-      acc[2] = __fma_rn(-rwz2, xf[2], acc[2]);
+  for (int c = 0; c < 3; ++c) acc[c] = __dmul_rn(sd.coul, S[c]);
+  if (!(tp.flags & IONTRAP_TRAP_OFF)) {
+    const double rwz2 = __dmul_rn(sd.rho, tp.wz2);
+    const double rq4 = __dmul_rn(tp.q4, sd.rho);
+    const double qc2 = __dmul_rn(2.0 * tp.q, cosv);
+    const double kx = __fma_rn(rq4, __dsub_rn(tp.a, qc2), -0.5 * rwz2);
+    const double ky = __fma_rn(rq4, __dadd_rn(tp.a, qc2), -0.5 * rwz2);
+    acc[0] = __fma_rn(-kx, xf[0], acc[0]);
+    acc[1] = __fma_rn(-ky, xf[1], acc[1]);
+    acc[2] = __fma_rn(-rwz2, xf[2], acc[2]);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) acc[c] = __fma_rn(-tp.gamma, vd[c], acc[c]);
+  if (sd.sigma > 0.0) {
+    double z[3];
+    const long long counter = step ? ns + 1 : ns;
+    if constexpr (F64) {
+      normals3_f64(tp.seed, counter, i, z);
+    } else {
+      float zf[3];
+      normals3_f32(tp.seed, counter, i, zf);
+      z[0] = zf[0], z[1] = zf[1], z[2] = zf[2];
     }
 #pragma unroll
-    for (int c = 0; c < 3; ++c) acc[c] = __fma_rn(-tp.gamma, vd[c], acc[c]);
-    if (sd.sigma > 0.0) {
-      double z[3];
-      normals3_f64(tp.seed, step ? ns + 1 : ns, i, z);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) acc[c] = __fma_rn(sd.sigma, z[c], acc[c]);
-    }
-  } else {
-    float af[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) af[c] = __fmul_rn(sd.coulf, (float)S[c]);
-    if (!(tp.flags & IONTRAP_TRAP_OFF)) {
-      const float rwz2 = sd.rwz2f;
-      const float qc2 = __fmul_rn(sd.rq2f, (float)cosv);
-      const float kx = __fsub_rn(sd.rakf, qc2);
-      const float ky = __fadd_rn(sd.rakf, qc2);
-      af[0] = __fmaf_rn(-kx, (float)xf[0], af[0]);
-      af[1] = __fmaf_rn(-ky, (float)xf[1], af[1]);
-      af[2] = __fmaf_rn(-rwz2, (float)xf[2], af[2]);
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) af[c] = __fmaf_rn(-sd.gammaf, (float)vd[c], af[c]);
-    if (sd.sigma > 0.0) {
-      float z[3];
-      normals3_f32(tp.seed, step ? ns + 1 : ns, i, z);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) af[c] = __fmaf_rn(sd.sigmaf, z[c], af[c]);
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) acc[c] = (double)af[c];
+    for (int c = 0; c < 3; ++c) acc[c] = __fma_rn(sd.sigma, z[c], acc[c]);
   }
   double vn[3], xn[3];
   bool finite = true;

@@ -49,7 +49,8 @@ class iontrap_params(ctypes.Structure):
 
 class iontrap_config(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("ions_per_thread", ctypes.c_int32),
-                ("packed", ctypes.c_int32), ("jsplit", ctypes.c_int32), ("fused", ctypes.c_int32)]
+                ("packed", ctypes.c_int32), ("jsplit", ctypes.c_int32), ("fused", ctypes.c_int32),
+                ("pdl", ctypes.c_int32), ("graph", ctypes.c_int32)]
 
 
 # symbol name -> (restype, argtypes)
@@ -241,14 +242,16 @@ def iontrap_normals(seed: int, counter: int, ids, precision: int = IONTRAP_PREC_
 
 
 def iontrap_get_config(h):
-    """Returns (threads, ions_per_thread, packed, jsplit, fused)."""
+    """Returns (threads, ions_per_thread, packed, jsplit, fused, pdl, graph)."""
     c = iontrap_config()
     _check(_lib.iontrap_get_config(h, ctypes.byref(c)), "iontrap_get_config")
-    return c.threads, c.ions_per_thread, c.packed, c.jsplit, c.fused
+    return c.threads, c.ions_per_thread, c.packed, c.jsplit, c.fused, c.pdl, c.graph
 
 
-def iontrap_set_config(h, threads: int, ions_per_thread: int, packed: int, jsplit: int, fused: int = 1) -> None:
-    c = iontrap_config(int(threads), int(ions_per_thread), int(packed), int(jsplit), int(fused))
+def iontrap_set_config(h, threads: int, ions_per_thread: int, packed: int, jsplit: int, fused: int = 1,
+                       pdl: int = 1, graph: int = 1) -> None:
+    c = iontrap_config(int(threads), int(ions_per_thread), int(packed), int(jsplit), int(fused), int(pdl),
+                       int(graph))
     _check(_lib.iontrap_set_config(h, ctypes.byref(c)), "iontrap_set_config")
 
 
@@ -298,8 +301,8 @@ class Simulation:
     def config(self):
         return iontrap_get_config(self.handle)
 
-    def set_config(self, threads, ions_per_thread, packed, jsplit, fused=1) -> None:
-        iontrap_set_config(self.handle, threads, ions_per_thread, packed, jsplit, fused)
+    def set_config(self, threads, ions_per_thread, packed, jsplit, fused=1, pdl=1, graph=1) -> None:
+        iontrap_set_config(self.handle, threads, ions_per_thread, packed, jsplit, fused, pdl, graph)
 
     def close(self) -> None:
         if self.handle is not None:

@@ -92,7 +92,7 @@ def test_forces_every_tile_config(it, cfg):
     ref = oracle.coulomb_accel(w.x0, q, m)
     with _sim(it, w, it.IONTRAP_PREC_FP32) as sim:
         sim.set_config(*cfg)
-        assert sim.config() == cfg
+        assert sim.config()[:5] == cfg
         assert rel_rms(sim.forces(), ref) < FP32_FORCE_TOL
 
 
@@ -219,11 +219,10 @@ def test_two_ion_spacing(it, prec, tol):
     assert np.all(x[:2] == 0)
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-6), (1, 1e-9)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 1e-9)])
 def test_single_ion_stroboscopic_recurrence(it, prec, tol):
-    """No Coulomb partner: the epilogue alone (trap + Verlet) must reproduce the exact
-    one-period Floquet recurrence of the discrete map -- to rounding in the plain FP64
-    form, to FP32 rounding of the acceleration terms (FP64 Verlet) in the FP32 form."""
+    """No Coulomb partner: the epilogue alone (FP64 trap + Verlet) must reproduce the
+    exact one-period Floquet recurrence of the discrete map."""
     trap = iongen.Trap(Omega=iongen.OMEGA_RF, a=-0.001, q=0.3, omega_z=2 * math.pi * 0.2e6,
                        gamma=0.0, T_bath=0.0, dt=iongen.rf_period_dt(iongen.OMEGA_RF))
     x0 = np.array([[2e-6], [-1.5e-6], [3e-6]])
