@@ -171,7 +171,8 @@ typedef struct {
     int32_t fused;            /* 1: the last CTA of each i-block merges the split partials and
                                  integrates; 0: a separate epilogue kernel does, one ion per
                                  thread over all SMs.  The FP64 form supports 1 only. */
-    int32_t pdl;              /* 1: consecutive step kernels use programmatic dependent launch */
+    int32_t pdl;              /* 1: consecutive step kernels use programmatic dependent launch
+                                 (default 0: measured slower on GB300 for these grids) */
     int32_t graph;            /* 1: iontrap_step enqueues CUDA graphs of 100 steps; 0: single launches */
 } iontrap_config;
 

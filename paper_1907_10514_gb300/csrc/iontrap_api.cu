@@ -52,7 +52,7 @@ struct iontrap {
   long long* d_step = nullptr;
   int* d_err = nullptr;
   // launch configuration
-  int T = 128, I = 1, packed = 0, jsplit = 128, fused = 1, pdl = 1, use_graph = 1;
+  int T = 128, I = 1, packed = 0, jsplit = 128, fused = 1, pdl = 0, use_graph = 1;
   StepArgs args{};
   // graph of kGraphSteps chained steps
   cudaGraph_t graph = nullptr;
@@ -188,15 +188,13 @@ int64_t gcd64(int64_t a, int64_t b) {
 // over more ions.  The number of j-splits S makes the grid a multiple of the SM count
 // (equal work per SM) with at least two CTAs per SM where n allows.
 void default_config(int64_t n, int f64, int sms, int* T, int* I, int* packed, int* jsplit, int* fused) {
-  *fused = f64 ? 1 : 0;
+  *fused = 1;
   if (f64) {
     *T = 128;
     *I = 1;
     *packed = 0;
-  } else if (n <= 2048) {
-    *T = 64, *I = 1, *packed = 0;
   } else if (n <= 8192) {
-    *T = 64, *I = 2, *packed = 1;
+    *T = 64, *I = 1, *packed = 0;
   } else if (n <= 32768) {
     *T = 128, *I = 4, *packed = 1;
   } else {
