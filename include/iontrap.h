@@ -57,6 +57,7 @@ extern "C" {
 #define IONTRAP_ENONFINITE 4  /* a step produced a non-finite acceleration, velocity or position */
 #define IONTRAP_ETIMEOUT 5    /* a bounded device-side wait expired */
 #define IONTRAP_ECUDA 6       /* a CUDA runtime call failed */
+#define IONTRAP_ETOOLARGE 7   /* n exceeds the fixed scratch of iontrap_forces_noalloc */
 
 /* iontrap_params.flags */
 #define IONTRAP_RF_OFF 1u            /* drop the RF (q) term: static trap */
@@ -183,6 +184,28 @@ typedef struct {
  * give bitwise equal trajectories. */
 int iontrap_get_config(const iontrap_t *h, iontrap_config *cfg);
 int iontrap_set_config(iontrap_t *h, const iontrap_config *cfg);
+
+/* Allocation-free Coulomb accelerations, for callers that cannot call cudaMalloc (a
+ * process whose memory pool owns all device memory, a host that loads this library as a
+ * plugin and owns every buffer, a loop that cannot afford cudaMalloc's implicit
+ * synchronisation).  The paper has no counterpart: it is a deployment variant of the
+ * force evaluation that iontrap_forces performs on a handle.
+ *   species[n_species]    host species table, as for iontrap_create
+ *   d_species_of_ion[n]   DEVICE array of species indices
+ *   d_x[3n]               DEVICE positions, SoA, metres
+ *   d_acc[3n]             DEVICE output: k_e e^2 z_i/M_i sum_j z_j (x_i - x_j)/r_ij^3
+ *   cuda_stream           stream to enqueue on (NULL: legacy default stream)
+ * Asynchronous: the result is ready when the stream reaches it.  Allocates nothing: the
+ * pair stream, split partials and counters live in one fixed device array that is part
+ * of the library image (2.25 MiB on every GPU that loads the library, held until the
+ * process exits).  n > 8192 returns IONTRAP_ETOOLARGE and launches nothing.  The first
+ * call on a device looks up that array's device address (cudaGetSymbolAddress) with the
+ * device current; make that first call before any stream capture.  All calls on a
+ * device share the array and each clears its counters before launching: calls whose
+ * work overlaps on the GPU race and must be serialised by the caller.  EINVAL on bad
+ * arguments, ECUDA when a launch fails. */
+int iontrap_forces_noalloc(const iontrap_species *species, int n_species, const uint8_t *d_species_of_ion,
+                           const double *d_x, int64_t n, double *d_acc, void *cuda_stream);
 
 /* Profiling hook: run ONE step with per-CTA phase timestamps (%globaltimer, ns) and copy
  * them to marks[cap].  Layout: 4 marks per force-kernel CTA, CTA id = y*grid.x + x

@@ -382,6 +382,7 @@ const char* iontrap_strerror(int status) {
     case IONTRAP_ENONFINITE: return "a step produced a non-finite acceleration, velocity or position";
     case IONTRAP_ETIMEOUT: return "a bounded device-side wait expired";
     case IONTRAP_ECUDA: return "CUDA runtime error";
+    case IONTRAP_ETOOLARGE: return "n exceeds the allocation-free scratch capacity (8192 ions)";
     default: return "unknown status";
   }
 }

@@ -23,6 +23,7 @@ IONTRAP_EUNSTABLE = 3
 IONTRAP_ENONFINITE = 4
 IONTRAP_ETIMEOUT = 5
 IONTRAP_ECUDA = 6
+IONTRAP_ETOOLARGE = 7
 
 IONTRAP_RF_OFF = 1
 IONTRAP_COULOMB_OFF = 2
@@ -78,6 +79,8 @@ SIGNATURES = {
                                        ctypes.c_int, _dp]),
     "iontrap_get_config": (ctypes.c_int, [_vp, ctypes.POINTER(iontrap_config)]),
     "iontrap_set_config": (ctypes.c_int, [_vp, ctypes.POINTER(iontrap_config)]),
+    "iontrap_forces_noalloc": (ctypes.c_int, [ctypes.POINTER(iontrap_species), ctypes.c_int, _vp, _vp,
+                                              ctypes.c_int64, _vp, _vp]),
     "iontrap_trace_step": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int64, _i64p, _i64p]),
     "iontrap_alu_probe": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_longlong, _dp, _dp]),
 }
@@ -253,6 +256,14 @@ def iontrap_set_config(h, threads: int, ions_per_thread: int, packed: int, jspli
     c = iontrap_config(int(threads), int(ions_per_thread), int(packed), int(jsplit), int(fused), int(pdl),
                        int(graph))
     _check(_lib.iontrap_set_config(h, ctypes.byref(c)), "iontrap_set_config")
+
+
+def iontrap_forces_noalloc(species: Sequence, d_species_of_ion: int, d_x: int, n: int, d_acc: int,
+                           stream=None) -> None:
+    """Device-pointer, allocation-free Coulomb accelerations (see include/iontrap.h).
+    d_species_of_ion, d_x and d_acc are device addresses (e.g. tensor.data_ptr())."""
+    _check(_lib.iontrap_forces_noalloc(_species_array(species), len(species), int(d_species_of_ion), int(d_x),
+                                       int(n), int(d_acc), _stream_ptr(stream)), "iontrap_forces_noalloc")
 
 
 def iontrap_trace_step(h, cap: int = 1 << 22):
