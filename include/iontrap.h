@@ -137,9 +137,17 @@ int iontrap_checkpoint(iontrap_t *h, double *x, double *v, double *a, int64_t *s
  * otherwise. */
 int iontrap_restore(iontrap_t *h, const double *x, const double *v, const double *a, int64_t step);
 
-/* Enqueue n_steps[k] steps on each of count handles.  Handles that share a device
- * are advanced by one batched launch per group of 100 steps; the result of each
- * handle is bitwise the same as iontrap_step on it alone. */
+/* Enqueue n_steps[k] steps on each of count handles (the batched form of evolve(N)).
+ * FP32-form handles with n <= 2048 on the device of the first such handle are advanced
+ * together by one launch per 100 steps of a cluster kernel that keeps every ensemble
+ * resident in shared memory (pair stream) and registers (FP64 state); the others are
+ * stepped one by one as by iontrap_step.  Work is ordered after what is already queued
+ * on each handle's stream, and each handle's later work waits for the batch.  A
+ * batched ensemble's result depends only on its own inputs: it is bitwise the same
+ * alone or in any mix (its summation order differs from iontrap_step's, so the two
+ * agree to the FP32 force tolerance, not bit for bit).  Returns the first failing
+ * handle's status.  Calls on different streams share one set of launch tables and are
+ * serialised by the library. */
 int iontrap_step_many(iontrap_t *const *hs, const int64_t *n_steps, int count);
 
 /* Free the handle's device memory, graph and owned stream.  NULL is a no-op. */

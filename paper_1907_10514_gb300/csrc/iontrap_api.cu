@@ -16,6 +16,10 @@
 #include "iontrap_internal.cuh"
 
 namespace it {
+// batched.cu
+int batched_max_n();
+cudaError_t launch_batched(const std::vector<BatchEns>& ens, const std::vector<long long>& steps, int K,
+                           cudaStream_t stream);
 const void* step_kernel(int f64, int T, int I, int packed, int fused);
 const void* epilogue_kernel(int f64);
 const void* prep_kernel();
@@ -671,11 +675,75 @@ int iontrap_trace_step(iontrap_t* h, unsigned long long* marks, int64_t cap, int
 
 int iontrap_step_many(iontrap_t* const* hs, const int64_t* n_steps, int count) {
   if (!hs || !n_steps || count < 0) return IONTRAP_EINVAL;
+  for (int k = 0; k < count; ++k)
+    if (!hs[k] || n_steps[k] < 0) return IONTRAP_EINVAL;
   int first = IONTRAP_OK;
+  std::vector<int> batch;
   for (int k = 0; k < count; ++k) {
-    const int st = iontrap_step(hs[k], n_steps[k]);
-    if (st && !first) first = st;
+    iontrap* h = hs[k];
+    if (h->status) {
+      if (!first) first = h->status;
+      continue;
+    }
+    if (!h->f64 && h->n <= batched_max_n() && n_steps[k] > 0 && h->device == hs[0]->device)
+      batch.push_back(k);
+    else if (n_steps[k] > 0) {
+      const int st = iontrap_step(h, n_steps[k]);
+      if (st && !first) first = st;
+    }
   }
+  if (batch.empty()) return first;
+  iontrap* h0 = hs[batch[0]];
+  DeviceGuard g(h0->device);
+  cudaStream_t st0 = h0->stream;
+  std::vector<BatchEns> ens(batch.size());
+  std::vector<long long> steps(batch.size());
+  cudaError_t e = cudaSuccess;
+  for (size_t b = 0; b < batch.size(); ++b) {
+    iontrap* h = hs[batch[b]];
+    if (h->stream != st0 && e == cudaSuccess) {  // order after work already queued on h's stream
+      cudaEvent_t ev;
+      e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventRecord(ev, h->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st0, ev, 0);
+      cudaEventDestroy(ev);
+    }
+    BatchEns& E = ens[b];
+    std::memset(&E, 0, sizeof(E));
+    E.x = h->d_x;
+    E.v = h->d_v;
+    E.a = h->d_a;
+    E.sp = h->d_sp;
+    for (int q = 0; q < 2; ++q) {
+      E.hi[q] = (float4*)h->d_pair[q];
+      E.lo[q] = (float4*)h->d_pair[q] + h->n;
+    }
+    E.step = h->d_step;
+    E.err = h->d_err;
+    E.n = h->n;
+    E.step0 = h->step;
+    E.trap = h->args.trap;
+    std::memcpy(E.spc, h->args.spc, sizeof(E.spc));
+    steps[b] = n_steps[batch[b]];
+  }
+  if (e == cudaSuccess) e = launch_batched(ens, steps, kGraphSteps, st0);
+  for (size_t b = 0; b < batch.size(); ++b) {
+    iontrap* h = hs[batch[b]];
+    if (e != cudaSuccess) {
+      cuda_status(h, e);
+      continue;
+    }
+    h->step += steps[b];
+    if (h->stream != st0) {  // h's later work waits for the batch
+      cudaEvent_t ev;
+      cudaError_t e2 = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e2 == cudaSuccess) e2 = cudaEventRecord(ev, st0);
+      if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(h->stream, ev, 0);
+      cudaEventDestroy(ev);
+      if (e2 != cudaSuccess) cuda_status(h, e2);
+    }
+  }
+  if (e != cudaSuccess && !first) first = e == cudaErrorMemoryAllocation ? IONTRAP_ENOMEM : IONTRAP_ECUDA;
   return first;
 }
 

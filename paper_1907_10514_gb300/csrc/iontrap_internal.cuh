@@ -69,6 +69,23 @@ struct StepArgs {
   SpeciesDev spc[IONTRAP_MAX_SPECIES];
 };
 
+// One ensemble of a batched launch (FP32 form, resident in shared memory).
+struct BatchEns {
+  double* x;            // handle state, SoA [3][n]
+  double* v;
+  double* a;
+  const unsigned char* sp;
+  float4* hi[2];        // the handle's pair streams (read at start, refreshed at the end)
+  float4* lo[2];
+  long long* step;      // the handle's device step counter
+  int* err;
+  long long n;
+  long long step0;      // state step index when the batch was enqueued
+  long long remaining;  // steps still to take; decremented by the kernel
+  TrapDev trap;
+  SpeciesDev spc[IONTRAP_MAX_SPECIES];
+};
+
 // ------------------------------------------------------------------ PTX helpers
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -133,6 +150,71 @@ constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
 // Phase timestamp of this CTA into the optional trace buffer (thread 0 only).
 __device__ __forceinline__ void trace_mark(unsigned long long* trace, long long slot) {
   if (trace && threadIdx.x == 0) trace[slot] = globaltimer_ns();
+}
+
+// ------------------------------------------------------------------ FP32 pair terms
+// d = x_j - x_i from hi/lo pairs, with the i side held negated in registers:
+// (x_j,hi - x_i,hi) is exact for close pairs (Sterbenz) and the lo difference restores
+// the bits FP32 rounding dropped from both positions.  The accumulators therefore hold
+// -sum_j z_j (x_i - x_j)/r^3; the epilogue flips the sign.
+template <int I, bool DIAG>
+__device__ __forceinline__ void segment_f32(const float4* __restrict__ sh, const float4* __restrict__ sl, int jn,
+                                            long long jbase, const float (&nxh)[I][3], const float (&nxl)[I][3],
+                                            const long long (&ii)[I], float (&acc)[I][3]) {
+#pragma unroll 4
+  for (int j = 0; j < jn; ++j) {
+    const float4 ph = sh[j];
+    const float4 pl = sl[j];
+#pragma unroll
+    for (int k = 0; k < I; ++k) {
+      const float dx = (ph.x + nxh[k][0]) + (pl.x + nxl[k][0]);
+      const float dy = (ph.y + nxh[k][1]) + (pl.y + nxl[k][1]);
+      const float dz = (ph.z + nxh[k][2]) + (pl.z + nxl[k][2]);
+      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      float ri = rsqrt_approx(r2);
+      if (DIAG) ri = (jbase + j == ii[k]) ? 0.0f : ri;
+      const float ri2 = ri * ri;
+      const float s = (ph.w * ri) * ri2;  // z_j / r^3
+      acc[k][0] = fmaf(s, dx, acc[k][0]);
+      acc[k][1] = fmaf(s, dy, acc[k][1]);
+      acc[k][2] = fmaf(s, dz, acc[k][2]);
+    }
+  }
+}
+
+// The same arithmetic on two ions per instruction (packed FP32x2 FADD/FMUL/FFMA of
+// sm_100+); each lane rounds exactly as the scalar loop does, so both loops give the
+// same bits.
+template <int I, bool DIAG>
+__device__ __forceinline__ void segment_f32x2(const float4* __restrict__ sh, const float4* __restrict__ sl, int jn,
+                                              long long jbase, const float2 (&nxh)[I / 2][3],
+                                              const float2 (&nxl)[I / 2][3], const long long (&ii)[I],
+                                              float2 (&acc)[I / 2][3]) {
+#pragma unroll 4
+  for (int j = 0; j < jn; ++j) {
+    const float4 ph = sh[j];
+    const float4 pl = sl[j];
+    const float2 hx = make_float2(ph.x, ph.x), hy = make_float2(ph.y, ph.y), hz = make_float2(ph.z, ph.z);
+    const float2 lx = make_float2(pl.x, pl.x), ly = make_float2(pl.y, pl.y), lz = make_float2(pl.z, pl.z);
+    const float2 w = make_float2(ph.w, ph.w);
+#pragma unroll
+    for (int k = 0; k < I / 2; ++k) {
+      const float2 dx = __fadd2_rn(__fadd2_rn(hx, nxh[k][0]), __fadd2_rn(lx, nxl[k][0]));
+      const float2 dy = __fadd2_rn(__fadd2_rn(hy, nxh[k][1]), __fadd2_rn(ly, nxl[k][1]));
+      const float2 dz = __fadd2_rn(__fadd2_rn(hz, nxh[k][2]), __fadd2_rn(lz, nxl[k][2]));
+      const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+      float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+      if (DIAG) {
+        ri.x = (jbase + j == ii[2 * k]) ? 0.0f : ri.x;
+        ri.y = (jbase + j == ii[2 * k + 1]) ? 0.0f : ri.y;
+      }
+      const float2 ri2 = __fmul2_rn(ri, ri);
+      const float2 s = __fmul2_rn(__fmul2_rn(w, ri), ri2);
+      acc[k][0] = __ffma2_rn(s, dx, acc[k][0]);
+      acc[k][1] = __ffma2_rn(s, dy, acc[k][1]);
+      acc[k][2] = __ffma2_rn(s, dz, acc[k][2]);
+    }
+  }
 }
 
 // ------------------------------------------------------------------ Philox-4x64-10
@@ -218,9 +300,47 @@ __device__ __forceinline__ void write_pair(const StepArgs& A, int b, long long i
   }
 }
 
-// Fused epilogue for ion i: Coulomb sum S (sum_j z_j d/r^3) -> acceleration (Coulomb +
-// trap + Langevin) -> Verlet update -> next pair-stream entry.  cosv = cos(Omega t) at
-// the force time.  F64 selects the plain FP64 form (FP64 noise, double4_32a pair stream).
+// Acceleration of one ion at force time (FP64 in both forms): Coulomb sum S
+// (sum_j z_j d/r^3) -> k_e e^2 z/M S + trap field at xf (RF phase cosv) - gamma vd +
+// sigma xi(seed, counter, id).  Explicit roundings (no FMA contraction left to the
+// compiler): every kernel that inlines this produces the same bits.  The trajectories
+// of these clouds amplify FP32-sized perturbations of the RF trap term by ~1e4 within
+// 100 steps, so no term is evaluated in FP32.  F64 selects FP64 Box-Muller noise.
+template <bool F64>
+__device__ __forceinline__ void accel_ion(const TrapDev& tp, const SpeciesDev& sd, const double S[3],
+                                          const double xf[3], const double vd[3], double cosv,
+                                          long long counter, long long id, double acc[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) acc[c] = __dmul_rn(sd.coul, S[c]);
+  if (!(tp.flags & IONTRAP_TRAP_OFF)) {
+    const double rwz2 = __dmul_rn(sd.rho, tp.wz2);
+    const double rq4 = __dmul_rn(tp.q4, sd.rho);
+    const double qc2 = __dmul_rn(2.0 * tp.q, cosv);
+    const double kx = __fma_rn(rq4, __dsub_rn(tp.a, qc2), -0.5 * rwz2);
+    const double ky = __fma_rn(rq4, __dadd_rn(tp.a, qc2), -0.5 * rwz2);
+    acc[0] = __fma_rn(-kx, xf[0], acc[0]);
+    acc[1] = __fma_rn(-ky, xf[1], acc[1]);
+    acc[2] = __fma_rn(-rwz2, xf[2], acc[2]);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) acc[c] = __fma_rn(-tp.gamma, vd[c], acc[c]);
+  if (sd.sigma > 0.0) {
+    double z[3];
+    if constexpr (F64) {
+      normals3_f64(tp.seed, counter, id, z);
+    } else {
+      float zf[3];
+      normals3_f32(tp.seed, counter, id, zf);
+      z[0] = zf[0], z[1] = zf[1], z[2] = zf[2];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[c] = __fma_rn(sd.sigma, z[c], acc[c]);
+  }
+}
+
+// Fused epilogue for ion i: Coulomb sum S -> acceleration -> Verlet update -> next
+// pair-stream entry.  cosv = cos(Omega t) at the force time.  F64 selects the plain
+// FP64 form (FP64 noise, double4_32a pair stream).
 template <bool F64>
 __device__ __forceinline__ void epilogue_ion(const StepArgs& A, long long i, const double S[3], double cosv,
                                              long long ns, int wb) {
@@ -242,38 +362,8 @@ __device__ __forceinline__ void epilogue_ion(const StepArgs& A, long long i, con
     vd[c] = step ? vh : v;
     xf[c] = step ? drift(x, vh, tp.dt) : x;
   }
-  // Acceleration terms in FP64 in both forms: the trajectories of these clouds amplify
-  // FP32-sized perturbations of the RF trap term by ~1e4 within 100 steps.  Explicit
-  // roundings (no FMA contraction left to the compiler) make every kernel that inlines
-  // this epilogue produce the same bits.
   double acc[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) acc[c] = __dmul_rn(sd.coul, S[c]);
-  if (!(tp.flags & IONTRAP_TRAP_OFF)) {
-    const double rwz2 = __dmul_rn(sd.rho, tp.wz2);
-    const double rq4 = __dmul_rn(tp.q4, sd.rho);
-    const double qc2 = __dmul_rn(2.0 * tp.q, cosv);
-    const double kx = __fma_rn(rq4, __dsub_rn(tp.a, qc2), -0.5 * rwz2);
-    const double ky = __fma_rn(rq4, __dadd_rn(tp.a, qc2), -0.5 * rwz2);
-    acc[0] = __fma_rn(-kx, xf[0], acc[0]);
-    acc[1] = __fma_rn(-ky, xf[1], acc[1]);
-    acc[2] = __fma_rn(-rwz2, xf[2], acc[2]);
-  }
-#pragma unroll
-  for (int c = 0; c < 3; ++c) acc[c] = __fma_rn(-tp.gamma, vd[c], acc[c]);
-  if (sd.sigma > 0.0) {
-    double z[3];
-    const long long counter = step ? ns + 1 : ns;
-    if constexpr (F64) {
-      normals3_f64(tp.seed, counter, i, z);
-    } else {
-      float zf[3];
-      normals3_f32(tp.seed, counter, i, zf);
-      z[0] = zf[0], z[1] = zf[1], z[2] = zf[2];
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) acc[c] = __fma_rn(sd.sigma, z[c], acc[c]);
-  }
+  accel_ion<F64>(tp, sd, S, xf, vd, cosv, step ? ns + 1 : ns, i, acc);
   double vn[3], xn[3];
   bool finite = true;
 #pragma unroll

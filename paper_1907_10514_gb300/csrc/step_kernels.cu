@@ -20,71 +20,6 @@
 
 namespace it {
 
-// ------------------------------------------------------------------ FP32 pair terms
-// d = x_j - x_i from hi/lo pairs, with the i side held negated in registers:
-// (x_j,hi - x_i,hi) is exact for close pairs (Sterbenz) and the lo difference restores
-// the bits FP32 rounding dropped from both positions.  The accumulators therefore hold
-// -sum_j z_j (x_i - x_j)/r^3; the epilogue flips the sign.
-template <int I, bool DIAG>
-__device__ __forceinline__ void segment_f32(const float4* __restrict__ sh, const float4* __restrict__ sl, int jn,
-                                            long long jbase, const float (&nxh)[I][3], const float (&nxl)[I][3],
-                                            const long long (&ii)[I], float (&acc)[I][3]) {
-#pragma unroll 4
-  for (int j = 0; j < jn; ++j) {
-    const float4 ph = sh[j];
-    const float4 pl = sl[j];
-#pragma unroll
-    for (int k = 0; k < I; ++k) {
-      const float dx = (ph.x + nxh[k][0]) + (pl.x + nxl[k][0]);
-      const float dy = (ph.y + nxh[k][1]) + (pl.y + nxl[k][1]);
-      const float dz = (ph.z + nxh[k][2]) + (pl.z + nxl[k][2]);
-      const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      float ri = rsqrt_approx(r2);
-      if (DIAG) ri = (jbase + j == ii[k]) ? 0.0f : ri;
-      const float ri2 = ri * ri;
-      const float s = (ph.w * ri) * ri2;  // z_j / r^3
-      acc[k][0] = fmaf(s, dx, acc[k][0]);
-      acc[k][1] = fmaf(s, dy, acc[k][1]);
-      acc[k][2] = fmaf(s, dz, acc[k][2]);
-    }
-  }
-}
-
-// The same arithmetic on two ions per instruction (packed FP32x2 FADD/FMUL/FFMA of
-// sm_100+); each lane rounds exactly as the scalar loop does, so both loops give the
-// same bits.
-template <int I, bool DIAG>
-__device__ __forceinline__ void segment_f32x2(const float4* __restrict__ sh, const float4* __restrict__ sl, int jn,
-                                              long long jbase, const float2 (&nxh)[I / 2][3],
-                                              const float2 (&nxl)[I / 2][3], const long long (&ii)[I],
-                                              float2 (&acc)[I / 2][3]) {
-#pragma unroll 4
-  for (int j = 0; j < jn; ++j) {
-    const float4 ph = sh[j];
-    const float4 pl = sl[j];
-    const float2 hx = make_float2(ph.x, ph.x), hy = make_float2(ph.y, ph.y), hz = make_float2(ph.z, ph.z);
-    const float2 lx = make_float2(pl.x, pl.x), ly = make_float2(pl.y, pl.y), lz = make_float2(pl.z, pl.z);
-    const float2 w = make_float2(ph.w, ph.w);
-#pragma unroll
-    for (int k = 0; k < I / 2; ++k) {
-      const float2 dx = __fadd2_rn(__fadd2_rn(hx, nxh[k][0]), __fadd2_rn(lx, nxl[k][0]));
-      const float2 dy = __fadd2_rn(__fadd2_rn(hy, nxh[k][1]), __fadd2_rn(ly, nxl[k][1]));
-      const float2 dz = __fadd2_rn(__fadd2_rn(hz, nxh[k][2]), __fadd2_rn(lz, nxl[k][2]));
-      const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-      float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
-      if (DIAG) {
-        ri.x = (jbase + j == ii[2 * k]) ? 0.0f : ri.x;
-        ri.y = (jbase + j == ii[2 * k + 1]) ? 0.0f : ri.y;
-      }
-      const float2 ri2 = __fmul2_rn(ri, ri);
-      const float2 s = __fmul2_rn(__fmul2_rn(w, ri), ri2);
-      acc[k][0] = __ffma2_rn(s, dx, acc[k][0]);
-      acc[k][1] = __ffma2_rn(s, dy, acc[k][1]);
-      acc[k][2] = __ffma2_rn(s, dz, acc[k][2]);
-    }
-  }
-}
-
 // Programmatic dependent launch: let the next step's CTAs be scheduled as this grid's
 // CTAs retire, and wait for the previous step's grid (its memory included) before
 // touching any state.  Both are no-ops for a launch without the PDL attribute.

@@ -327,22 +327,55 @@ def test_packed_and_fused_variants_are_bitwise_equal(it):
         assert np.array_equal(outs[0][0], f) and np.array_equal(outs[0][1], x)
 
 
-def test_step_many_equals_alone(it):
-    ws = [_cloud(n, 40 + n) for n in (17, 300, 2500)]
-    alone = []
-    for w in ws:
-        with _sim(it, w, 0) as s:
-            s.step(230)
-            alone.append(s.state()[:2])
+def _run_many(it, ws, steps):
     sims = [_sim(it, w, 0) for w in ws]
     try:
-        it.iontrap_step_many([s.handle for s in sims], [230] * len(sims))
-        for s, (xa, va) in zip(sims, alone):
-            x, v, step, _ = s.state()
-            assert step == 230 and np.array_equal(x, xa) and np.array_equal(v, va)
+        it.iontrap_step_many([s.handle for s in sims], steps)
+        return [s.state() for s in sims]
     finally:
         for s in sims:
             s.close()
+
+
+@pytest.mark.parametrize("n", [1, 2, 16, 63, 64, 65, 200, 256, 257, 700, 1024, 1500, 2048])
+def test_batched_trajectory_matches_oracle(it, n):
+    """The batched resident kernel (every packing class: one warp, one CTA, 2/4/8 CTAs of
+    a cluster) against the oracle over 100 steps."""
+    w = _cloud(n, 300 + n)
+    q, m, p = _oracle_side(w)
+    xo, vo, _ = oracle.run(w.x0, w.v0, q, m, p, 100)
+    (x, v, step, _), = _run_many(it, [w], [100])
+    assert step == 100
+    if n > 1:
+        assert rel_rms(x, xo) < FP32_TRAJ_TOL and rel_rms(v, vo) < 10 * FP32_TRAJ_TOL
+    else:
+        assert rel_rms(x, xo) < 1e-12
+
+
+def test_batched_alone_equals_mixed_bitwise(it):
+    """An ensemble's result is the same bits advanced alone or packed with others of
+    every size class (and with ones that fall back to the single-simulation kernel)."""
+    sizes = [17, 40, 64, 100, 300, 700, 1800, 2500]
+    ws = [_cloud(n, 40 + n) for n in sizes]
+    steps = [230, 150, 230, 99, 230, 180, 230, 120]
+    alone = [_run_many(it, [w], [k])[0] for w, k in zip(ws, steps)]
+    mixed = _run_many(it, ws, steps)
+    for (xa, va, sa, _), (xm, vm, sm, _), k in zip(alone, mixed, steps):
+        assert sa == sm == k
+        assert np.array_equal(xa, xm) and np.array_equal(va, vm)
+
+
+def test_batched_then_single_continue_consistently(it):
+    """A handle advanced by the batched kernel and then by iontrap_step continues from a
+    consistent state (pair stream refreshed): trajectory within tolerance of the oracle."""
+    w = _cloud(500, 77)
+    q, m, p = _oracle_side(w)
+    xo, vo, _ = oracle.run(w.x0, w.v0, q, m, p, 100)
+    with _sim(it, w, 0) as s:
+        it.iontrap_step_many([s.handle], [60])
+        s.step(40)
+        x, v, step, _ = s.state()
+    assert step == 100 and rel_rms(x, xo) < FP32_TRAJ_TOL
 
 
 def test_checkpoint_restore_is_bitwise(it):
