@@ -348,8 +348,8 @@ def test_batched_trajectory_matches_oracle(it, n):
     assert step == 100
     if n > 1:
         assert rel_rms(x, xo) < FP32_TRAJ_TOL and rel_rms(v, vo) < 10 * FP32_TRAJ_TOL
-    else:
-        assert rel_rms(x, xo) < 1e-12
+    else:  # a lone ion: only the FP32 Box-Muller noise differs from the oracle's FP64 noise
+        assert rel_rms(x, xo) < 1e-9
 
 
 def test_batched_alone_equals_mixed_bitwise(it):
