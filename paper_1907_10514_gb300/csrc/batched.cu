@@ -334,7 +334,8 @@ struct BatchBuffers {
   size_t ens_cap = 0;
   BatchCta* d_cta = nullptr;
   size_t cta_cap = 0;
-  cudaStream_t last = nullptr;  // stream of the previous batched launches (may still read the tables)
+  cudaEvent_t done = nullptr;  // recorded after the previous launches, which read the tables
+  bool pending = false;
 };
 static BatchBuffers g_bb;
 
@@ -352,9 +353,16 @@ cudaError_t launch_batched(const std::vector<BatchEns>& ens_in, const std::vecto
   }
   if (max_steps == 0) return cudaSuccess;
   BatchPlan plan = plan_batch(n);
-  if (g_bb.last && g_bb.last != stream) {
-    cudaError_t e = cudaStreamSynchronize(g_bb.last);
+  // The tables below are shared by all calls: wait until the previous launches, which
+  // may run on another (possibly since destroyed) stream, have finished reading them.
+  if (!g_bb.done) {
+    cudaError_t e = cudaEventCreateWithFlags(&g_bb.done, cudaEventDisableTiming);
     if (e != cudaSuccess) return e;
+  }
+  if (g_bb.pending) {
+    cudaError_t e = cudaEventSynchronize(g_bb.done);
+    if (e != cudaSuccess) return e;
+    g_bb.pending = false;
   }
   if (ens_in.size() > g_bb.ens_cap) {
     if (g_bb.d_ens) cudaFree(g_bb.d_ens);
@@ -388,13 +396,14 @@ cudaError_t launch_batched(const std::vector<BatchEns>& ens_in, const std::vecto
   const size_t smem = std::max<size_t>(plan.smem, 16);
   err = cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  g_bb.last = stream;
   for (long long done = 0; done < max_steps; done += K) {
     k_batched<<<(unsigned)plan.ctas.size(), kBThreads, smem, stream>>>(g_bb.d_ens, g_bb.d_cta, K);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
   }
-  return cudaSuccess;
+  err = cudaEventRecord(g_bb.done, stream);
+  if (err == cudaSuccess) g_bb.pending = true;
+  return err;
 }
 
 }  // namespace it
