@@ -245,6 +245,18 @@ def run_gpu(args):
     extra = {}
     if rank == 0 and not args.no_extra:
         extra = extra_measurements(it, torch, stream, sms, args)
+    if rank == 0 and not args.no_batched:
+        extra["batched_512"] = batched_measurement(it, torch, stream)
+    if rank == 0 and not args.no_serve:
+        extra["serve"] = serve_measurement(it, torch, args.serve_requests, args.serve_step_scale,
+                                           args.serve_budget_mb << 20, args.serve_fp64_subset)
+    if rank == 0:
+        probe = {}
+        for kind, name in ((0, "ffma"), (1, "ffma2"), (2, "mufu_rsqrt"), (3, "dfma")):
+            ops, mhz = it.iontrap_alu_probe(kind, 4000 if kind == 3 else 20000)
+            probe[name] = round(ops, 2)
+        probe["sm_mhz"] = round(mhz)
+        extra["alu_probe_lane_ops_per_clk_per_sm"] = probe
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -333,6 +345,99 @@ def extra_measurements(it, torch, stream, sms, args):
     return out
 
 
+def batched_measurement(it, torch, stream, steps=2000):
+    """512 independent Ca+ ensembles (N log-uniform in [16, 2048]) advanced together by
+    iontrap_step_many (batched resident kernel), 2000 steps."""
+    import iongen
+    stable = lambda species, trap: it.iontrap_stable(species, it.make_params(trap))
+    ws = iongen.batched_512(stable=stable, steps=steps)
+    sims = [it.Simulation(w.species, w.species_of_ion, w.x0, w.v0, it.make_params(w.trap), stream=stream)
+            for w in ws]
+    try:
+        hs = [s.handle for s in sims]
+        it.iontrap_step_many(hs, [100] * len(hs))  # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        it.iontrap_step_many(hs, [steps] * len(hs))
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+    finally:
+        for s in sims:
+            s.close()
+    ions = sum(w.n for w in ws)
+    pairs = sum(w.n * (w.n - 1) for w in ws)
+    return {"ensembles": len(ws), "ions": ions, "timesteps": steps, "ms": ms,
+            "ion_steps_per_s": ions * steps / (ms / 1e3), "pair_interactions_per_s": pairs * steps / (ms / 1e3),
+            "launches": (steps + 99) // 100}
+
+
+def serve_measurement(it, torch, count, step_scale, budget_bytes, fp64_subset):
+    """The request stream (Poisson 200/s, N log-uniform in [8, 65536], Ca+ or 80/20
+    Ca+/NH3+) with step budgets divided by step_scale, submitted at their arrival times
+    to the continuous-batching server; latency = completion - arrival."""
+    import iongen
+    stable = lambda species, trap: it.iontrap_stable(species, it.make_params(trap))
+    full = iongen.serve_stream(stable=stable)
+    full_pairs = sum(r.n * r.n * r.steps for r in full)
+    offered_full = full_pairs / full[-1].arrival_s
+    reqs = full[:count]
+    for r in reqs:
+        r.steps = max(1, int(round(r.steps / step_scale)))
+    work = [(iongen.request_workload(r), r) for r in reqs]
+    srv = it.iontrap_server_create(mem_budget_bytes=budget_bytes, max_resident=4096, chunk_steps=100)
+    lat, arrival, ids = [], {}, {}
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k = 0
+        pending = len(work)
+        while pending:
+            now = time.perf_counter() - t0
+            while k < len(work) and work[k][1].arrival_s <= now:
+                w, r = work[k]
+                rid = it.iontrap_server_submit(srv, w.species, w.species_of_ion, w.x0, w.v0, it.make_params(w.trap),
+                                               r.steps)
+                arrival[rid] = r.arrival_s
+                ids[rid] = w.n
+                k += 1
+            for rid in it.iontrap_server_poll(srv):
+                lat.append(time.perf_counter() - t0 - arrival[rid])
+                it.iontrap_server_result(srv, rid, ids[rid])
+                pending -= 1
+            time.sleep(0.0002)
+        wall = time.perf_counter() - t0
+    finally:
+        it.iontrap_server_destroy(srv)
+    ion_steps = sum(r.n * r.steps for r in reqs)
+    pairs = sum(r.n * (r.n - 1) * r.steps for r in reqs)
+    lat_ms = np.array(lat) * 1e3
+    out = {"requests": len(reqs), "step_scale": step_scale, "arrival_span_s": reqs[-1].arrival_s, "wall_s": wall,
+           "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+           "ion_steps_per_s": ion_steps / wall, "pair_interactions_per_s": pairs / wall,
+           "offered_pairs_per_s": pairs / reqs[-1].arrival_s, "mem_budget_bytes": budget_bytes,
+           "full_stream_offered_pairs_per_s": offered_full, "full_stream_requests": len(full)}
+    # baseline: the plain FP64 form, one simulation at a time in arrival order (subset)
+    t = 0.0
+    sub = work[:fp64_subset]
+    for w, r in sub:
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        h = it.iontrap_create(w.species, w.species_of_ion, w.x0, w.v0,
+                              it.make_params(w.trap, precision=it.IONTRAP_PREC_FP64))
+        it.iontrap_step(h, r.steps)
+        it.iontrap_state(h, w.n)
+        t += time.perf_counter() - t1
+        it.iontrap_destroy(h)
+    sub_ion_steps = sum(r.n * r.steps for _, r in sub)
+    ours_sub = sum(r.n * r.steps for _, r in sub)
+    out["fp64_fifo_baseline"] = {"requests": len(sub), "ion_steps_per_s": sub_ion_steps / t, "seconds": t,
+                                 "note": "plain FP64 form, one simulation at a time, first requests of the stream"}
+    del ours_sub
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -344,6 +449,12 @@ def main():
     ap.add_argument("--cpu-sample-steps", type=int, default=200)
     ap.add_argument("--ref-sample-steps", type=int, default=100)
     ap.add_argument("--fp64-steps", type=int, default=50)
+    ap.add_argument("--serve-requests", type=int, default=800)
+    ap.add_argument("--serve-step-scale", type=float, default=1000.0)
+    ap.add_argument("--serve-budget-mb", type=int, default=2048)
+    ap.add_argument("--serve-fp64-subset", type=int, default=20)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

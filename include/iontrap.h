@@ -193,6 +193,48 @@ typedef struct {
 int iontrap_get_config(const iontrap_t *h, iontrap_config *cfg);
 int iontrap_set_config(iontrap_t *h, const iontrap_config *cfg);
 
+/* Device memory held by a handle, in bytes (state, pair streams, partials, counters). */
+int iontrap_device_bytes(const iontrap_t *h, int64_t *bytes);
+
+/* ---------------------------------------------------------------- serving loop
+ * Continuous batching of many trap simulations of different sizes and step budgets on
+ * one device.  Requests wait in arrival order until a slot and enough of the device
+ * memory budget are free, then stay resident until their last step.  Each
+ * iontrap_server_poll is one scheduling round: retire requests whose last chunk
+ * finished (final state copied to the host, memory returned), admit waiting requests
+ * that fit, and enqueue the next chunk (chunk_steps) of every idle resident request --
+ * FP32-form requests with n <= 2048 together through the batched kernel on the
+ * server's stream, the others each on a stream of its own, so the work overlaps.  A
+ * request's result does not depend on what else is resident (batched ones are bitwise
+ * independent of the mix).  Poll is non-blocking except for the host copies of
+ * admission and retirement.  A server and its requests are used from one host thread. */
+typedef struct iontrap_server iontrap_server_t;
+typedef struct {
+    int64_t mem_budget_bytes; /* device bytes resident requests may hold; 0 = 2 GiB */
+    int32_t max_resident;     /* resident request limit; 0 = 4096 */
+    int32_t chunk_steps;      /* steps per request per scheduling round; 0 = 100 */
+} iontrap_server_config;
+typedef struct {
+    int64_t waiting, resident, completed, device_bytes;
+} iontrap_server_counters;
+
+int iontrap_server_create(const iontrap_server_config *cfg, iontrap_server_t **out);
+/* Queue a request (arguments as for iontrap_create with step0 = 0, plus its step
+ * budget); the inputs are copied.  *id identifies it in poll and result. */
+int iontrap_server_submit(iontrap_server_t *s, const iontrap_species *species, int n_species,
+                          const uint8_t *species_of_ion, const double *x0, const double *v0, int64_t n,
+                          const iontrap_params *p, int64_t n_steps, int64_t *id);
+/* One scheduling round; writes the ids completed in this round (up to cap) and their
+ * count.  A request that cannot be created (e.g. IONTRAP_EUNSTABLE) completes at once
+ * with that status. */
+int iontrap_server_poll(iontrap_server_t *s, int64_t *completed_ids, int64_t cap, int64_t *n_completed);
+/* Copy a completed request's final x[3n], v[3n] (either may be NULL), step index and
+ * status, and release it.  EINVAL if the id is not completed (or already released). */
+int iontrap_server_result(iontrap_server_t *s, int64_t id, double *x, double *v, int64_t *step, int *status);
+int iontrap_server_stats(const iontrap_server_t *s, iontrap_server_counters *out);
+/* Waits for in-flight work, frees every resident request and the server. */
+void iontrap_server_destroy(iontrap_server_t *s);
+
 /* Allocation-free Coulomb accelerations, for callers that cannot call cudaMalloc (a
  * process whose memory pool owns all device memory, a host that loads this library as a
  * plugin and owns every buffer, a loop that cannot afford cudaMalloc's implicit

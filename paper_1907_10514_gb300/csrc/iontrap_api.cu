@@ -776,6 +776,15 @@ int iontrap_normals(uint64_t seed, int64_t counter, const int64_t* ids, int64_t 
   return e == cudaSuccess ? IONTRAP_OK : IONTRAP_ECUDA;
 }
 
+int iontrap_device_bytes(const iontrap_t* h, int64_t* bytes) {
+  if (!h || !bytes) return IONTRAP_EINVAL;
+  const int64_t vec = 3 * h->n * (int64_t)sizeof(double);
+  const int64_t pair = h->n * (int64_t)(h->f64 ? sizeof(double4_32a) : 2 * sizeof(float4));
+  *bytes = 3 * vec + (h->d_out ? vec : 0) + h->n + 2 * pair + (int64_t)h->part_bytes +
+           (int64_t)h->cnt_len * (int64_t)sizeof(unsigned) + 64;
+  return IONTRAP_OK;
+}
+
 int iontrap_get_config(const iontrap_t* h, iontrap_config* c) {
   if (!h || !c) return IONTRAP_EINVAL;
   c->threads = h->T;

@@ -54,6 +54,16 @@ class iontrap_config(ctypes.Structure):
                 ("pdl", ctypes.c_int32), ("graph", ctypes.c_int32)]
 
 
+class iontrap_server_config(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_int64), ("max_resident", ctypes.c_int32),
+                ("chunk_steps", ctypes.c_int32)]
+
+
+class iontrap_server_counters(ctypes.Structure):
+    _fields_ = [("waiting", ctypes.c_int64), ("resident", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64)]
+
+
 # symbol name -> (restype, argtypes)
 _dp = ctypes.POINTER(ctypes.c_double)
 _i64p = ctypes.POINTER(ctypes.c_int64)
@@ -81,6 +91,15 @@ SIGNATURES = {
     "iontrap_set_config": (ctypes.c_int, [_vp, ctypes.POINTER(iontrap_config)]),
     "iontrap_forces_noalloc": (ctypes.c_int, [ctypes.POINTER(iontrap_species), ctypes.c_int, _vp, _vp,
                                               ctypes.c_int64, _vp, _vp]),
+    "iontrap_device_bytes": (ctypes.c_int, [_vp, _i64p]),
+    "iontrap_server_create": (ctypes.c_int, [ctypes.POINTER(iontrap_server_config), ctypes.POINTER(_vp)]),
+    "iontrap_server_submit": (ctypes.c_int, [_vp, ctypes.POINTER(iontrap_species), ctypes.c_int,
+                                             ctypes.POINTER(ctypes.c_uint8), _dp, _dp, ctypes.c_int64,
+                                             ctypes.POINTER(iontrap_params), ctypes.c_int64, _i64p]),
+    "iontrap_server_poll": (ctypes.c_int, [_vp, _i64p, ctypes.c_int64, _i64p]),
+    "iontrap_server_result": (ctypes.c_int, [_vp, ctypes.c_int64, _dp, _dp, _i64p, _ip]),
+    "iontrap_server_stats": (ctypes.c_int, [_vp, ctypes.POINTER(iontrap_server_counters)]),
+    "iontrap_server_destroy": (None, [_vp]),
     "iontrap_trace_step": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int64, _i64p, _i64p]),
     "iontrap_alu_probe": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_longlong, _dp, _dp]),
 }
@@ -264,6 +283,59 @@ def iontrap_forces_noalloc(species: Sequence, d_species_of_ion: int, d_x: int, n
     d_species_of_ion, d_x and d_acc are device addresses (e.g. tensor.data_ptr())."""
     _check(_lib.iontrap_forces_noalloc(_species_array(species), len(species), int(d_species_of_ion), int(d_x),
                                        int(n), int(d_acc), _stream_ptr(stream)), "iontrap_forces_noalloc")
+
+
+def iontrap_device_bytes(h) -> int:
+    b = ctypes.c_int64()
+    _check(_lib.iontrap_device_bytes(h, ctypes.byref(b)), "iontrap_device_bytes")
+    return b.value
+
+
+def iontrap_server_create(mem_budget_bytes: int = 0, max_resident: int = 0, chunk_steps: int = 0):
+    cfg = iontrap_server_config(int(mem_budget_bytes), int(max_resident), int(chunk_steps))
+    s = ctypes.c_void_p()
+    _check(_lib.iontrap_server_create(ctypes.byref(cfg), ctypes.byref(s)), "iontrap_server_create")
+    return s
+
+
+def iontrap_server_submit(s, species, species_of_ion, x0, v0, params: iontrap_params, n_steps: int) -> int:
+    sp = np.ascontiguousarray(species_of_ion, dtype=np.uint8)
+    n = sp.shape[0]
+    x = _f64(x0).reshape(3, n)
+    v = None if v0 is None else _f64(v0).reshape(3, n)
+    rid = ctypes.c_int64()
+    _check(_lib.iontrap_server_submit(s, _species_array(species), len(species),
+                                      sp.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), _ptr(x),
+                                      None if v is None else _ptr(v), n, ctypes.byref(params), int(n_steps),
+                                      ctypes.byref(rid)), "iontrap_server_submit")
+    return rid.value
+
+
+def iontrap_server_poll(s, cap: int = 4096):
+    ids = np.empty(cap, dtype=np.int64)
+    k = ctypes.c_int64()
+    _check(_lib.iontrap_server_poll(s, ids.ctypes.data_as(_i64p), cap, ctypes.byref(k)), "iontrap_server_poll")
+    return ids[:min(k.value, cap)].tolist()
+
+
+def iontrap_server_result(s, rid: int, n: int):
+    """Returns (x, v, step, status) of a completed request and releases it."""
+    x, v = np.empty((3, n)), np.empty((3, n))
+    step, status = ctypes.c_int64(), ctypes.c_int()
+    _check(_lib.iontrap_server_result(s, int(rid), _ptr(x), _ptr(v), ctypes.byref(step), ctypes.byref(status)),
+           "iontrap_server_result")
+    return x, v, step.value, status.value
+
+
+def iontrap_server_stats(s):
+    st = iontrap_server_counters()
+    _check(_lib.iontrap_server_stats(s, ctypes.byref(st)), "iontrap_server_stats")
+    return {"waiting": st.waiting, "resident": st.resident, "completed": st.completed,
+            "device_bytes": st.device_bytes}
+
+
+def iontrap_server_destroy(s) -> None:
+    _lib.iontrap_server_destroy(s)
 
 
 def iontrap_trace_step(h, cap: int = 1 << 22):

@@ -448,3 +448,59 @@ def test_coincident_ions_report_nonfinite(it):
             assert e.value.code == it.IONTRAP_ENONFINITE
         finally:
             sim.close()
+
+
+# ------------------------------------------------------------------ serving loop
+
+def test_server_results_equal_alone_and_respect_budget(it):
+    """Continuous batching: requests of different sizes and step budgets (one with an
+    unstable trap) submitted while others run, under a memory budget small enough that
+    some must wait.  Each result equals the same request run alone through the same
+    kernel path (bitwise), the budget is never exceeded, every request completes."""
+    import time
+    sizes = [16, 90, 300, 1100, 2048, 2500, 40, 700, 5000, 64]
+    steps = [250, 130, 310, 120, 100, 150, 90, 210, 100, 180]
+    reqs = []
+    for k, (n, st) in enumerate(zip(sizes, steps)):
+        w = _cloud(n, 500 + k, species=(iongen.CA40, iongen.NH3) if k % 3 == 0 else (iongen.CA40,))
+        reqs.append((w, st))
+    bad = _cloud(50, 999)
+    bad.trap.q = 0.95  # outside the stability region
+    budget = 12 << 20
+    srv = it.iontrap_server_create(mem_budget_bytes=budget, max_resident=6, chunk_steps=100)
+    try:
+        ids = {}
+        done = {}
+        for k, (w, st) in enumerate(reqs[:5]):
+            ids[it.iontrap_server_submit(srv, w.species, w.species_of_ion, w.x0, w.v0,
+                                         it.make_params(w.trap), st)] = k
+        bad_id = it.iontrap_server_submit(srv, bad.species, bad.species_of_ion, bad.x0, bad.v0,
+                                          it.make_params(bad.trap), 100)
+        polls, t0 = 0, time.time()
+        while len(done) < len(reqs) + 1:
+            if polls == 3:  # later arrivals join while the first ones run
+                for k, (w, st) in enumerate(reqs[5:], start=5):
+                    ids[it.iontrap_server_submit(srv, w.species, w.species_of_ion, w.x0, w.v0,
+                                                 it.make_params(w.trap), st)] = k
+            for rid in it.iontrap_server_poll(srv):
+                done[rid] = True
+            stats = it.iontrap_server_stats(srv)
+            assert stats["device_bytes"] <= budget and stats["resident"] <= 6
+            polls += 1
+            assert time.time() - t0 < 300
+            time.sleep(0.001)
+        x, v, step, status = it.iontrap_server_result(srv, bad_id, bad.n)
+        assert status == it.IONTRAP_EUNSTABLE
+        for rid, k in ids.items():
+            w, st = reqs[k]
+            x, v, step, status = it.iontrap_server_result(srv, rid, w.n)
+            assert status == 0 and step == st
+            with _sim(it, w, 0) as alone:
+                if w.n <= 2048:
+                    it.iontrap_step_many([alone.handle], [st])
+                else:
+                    alone.step(st)
+                xa, va, _, _ = alone.state()
+            assert np.array_equal(x, xa) and np.array_equal(v, va), (k, w.n)
+    finally:
+        it.iontrap_server_destroy(srv)
