@@ -193,8 +193,12 @@ typedef struct {
 int iontrap_get_config(const iontrap_t *h, iontrap_config *cfg);
 int iontrap_set_config(iontrap_t *h, const iontrap_config *cfg);
 
-/* Device memory held by a handle, in bytes (state, pair streams, partials, counters). */
+/* Device memory held by a handle, in bytes (state, pair streams, partials, counters),
+ * and the bytes a handle of n ions in the given precision form would hold when created
+ * now on the current device (its default configuration, Coulomb term on); the latter does
+ * no device work. */
 int iontrap_device_bytes(const iontrap_t *h, int64_t *bytes);
+int iontrap_estimate_bytes(int64_t n, int precision, int64_t *bytes);
 
 /* ---------------------------------------------------------------- serving loop
  * Continuous batching of many trap simulations of different sizes and step budgets on

@@ -204,13 +204,24 @@ void default_config(int64_t n, int f64, int sms, int* T, int* I, int* packed, in
   } else {
     *T = 128, *I = 4, *packed = 1;
   }
+  // Split count S: a score of wave efficiency (CTAs fill whole waves of SMs), fill (at
+  // least two CTAs per SM) and a small preference for fewer splits (less partial
+  // traffic); at most 64 splits, at least 32 j per split.
   const int64_t iblocks = cdiv(n, (int64_t)(*T) * (*I));
-  const int64_t step = sms / gcd64(iblocks, sms);  // S multiple of this => grid multiple of sms
-  const int64_t min_j = f64 ? 32 : 32;
-  const int64_t s_max = std::max<int64_t>(1, n / min_j);
-  int64_t S = step;
-  while (S * iblocks < 2 * (int64_t)sms && S + step <= s_max) S += step;
-  if (S > s_max) S = std::max<int64_t>(1, std::min(s_max, cdiv(2 * (int64_t)sms, iblocks)));
+  const int64_t s_max = std::max<int64_t>(1, std::min<int64_t>(64, n / 32));
+  int64_t S = 1;
+  double best = -1e30;
+  for (int64_t cand = 1; cand <= s_max; ++cand) {
+    const double ctas = (double)(iblocks * cand);
+    const double waves = ctas / sms;
+    const double eff = waves / std::ceil(waves);
+    const double fill = std::min(1.0, ctas / (2.0 * sms));
+    const double score = eff * fill - 0.002 * (double)cand;
+    if (score > best + 1e-12) {
+      best = score;
+      S = cand;
+    }
+  }
   int64_t js = cdiv(n, S);
   if (f64) js = std::min<int64_t>(js, kMaxJsplitF64);
   if (!*fused && cdiv(n, js) > kMaxSplitsUnfused) js = cdiv(n, kMaxSplitsUnfused);
@@ -774,6 +785,22 @@ int iontrap_normals(uint64_t seed, int64_t counter, const int64_t* ids, int64_t 
   cudaFree(d_ids);
   cudaFree(d_z);
   return e == cudaSuccess ? IONTRAP_OK : IONTRAP_ECUDA;
+}
+
+int iontrap_estimate_bytes(int64_t n, int precision, int64_t* bytes) {
+  if (n < 1 || !bytes || (precision != IONTRAP_PREC_FP32 && precision != IONTRAP_PREC_FP64)) return IONTRAP_EINVAL;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return IONTRAP_ECUDA;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0) sms = 1;
+  const int f64 = precision == IONTRAP_PREC_FP64;
+  int T, I, P, J, F;
+  default_config(n, f64, sms, &T, &I, &P, &J, &F);
+  const int64_t splits = cdiv(n, J), iblocks = cdiv(n, (int64_t)T * I);
+  const int64_t vec = 3 * n * (int64_t)sizeof(double);
+  const int64_t pair = n * (int64_t)(f64 ? sizeof(double4_32a) : 2 * sizeof(float4));
+  *bytes = 3 * vec + n + 2 * pair + splits * n * 32 + iblocks * (int64_t)sizeof(unsigned) + 64;
+  return IONTRAP_OK;
 }
 
 int iontrap_device_bytes(const iontrap_t* h, int64_t* bytes) {

@@ -56,9 +56,10 @@ struct Request {
 };
 
 // Device bytes a request will hold before its handle exists (for admission).
-int64_t estimate_bytes(int64_t n) {
-  const int64_t splits = n <= 2048 ? 32 : 64;
-  return n * (3 * 3 * 8 + 1 + 2 * 32 + 32 * splits) + 4096;
+int64_t estimate_bytes(int64_t n, int precision) {
+  int64_t b = 0;
+  if (iontrap_estimate_bytes(n, precision, &b) != IONTRAP_OK) b = n * (3 * 3 * 8 + 1 + 2 * 32 + 32 * 64) + 4096;
+  return b;
 }
 
 }  // namespace
@@ -133,7 +134,7 @@ int iontrap_server_submit(iontrap_server_t* s, const iontrap_species* species, i
   r->p = *p;
   r->steps = n_steps;
   r->batched = p->precision == IONTRAP_PREC_FP32 && n <= 2048;
-  r->bytes = estimate_bytes(n);
+  r->bytes = estimate_bytes(n, p->precision);
   *id = r->id;
   s->waiting.push_back(std::move(r));
   return IONTRAP_OK;

@@ -92,6 +92,7 @@ SIGNATURES = {
     "iontrap_forces_noalloc": (ctypes.c_int, [ctypes.POINTER(iontrap_species), ctypes.c_int, _vp, _vp,
                                               ctypes.c_int64, _vp, _vp]),
     "iontrap_device_bytes": (ctypes.c_int, [_vp, _i64p]),
+    "iontrap_estimate_bytes": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, _i64p]),
     "iontrap_server_create": (ctypes.c_int, [ctypes.POINTER(iontrap_server_config), ctypes.POINTER(_vp)]),
     "iontrap_server_submit": (ctypes.c_int, [_vp, ctypes.POINTER(iontrap_species), ctypes.c_int,
                                              ctypes.POINTER(ctypes.c_uint8), _dp, _dp, ctypes.c_int64,
@@ -288,6 +289,12 @@ def iontrap_forces_noalloc(species: Sequence, d_species_of_ion: int, d_x: int, n
 def iontrap_device_bytes(h) -> int:
     b = ctypes.c_int64()
     _check(_lib.iontrap_device_bytes(h, ctypes.byref(b)), "iontrap_device_bytes")
+    return b.value
+
+
+def iontrap_estimate_bytes(n: int, precision: int = IONTRAP_PREC_FP32) -> int:
+    b = ctypes.c_int64()
+    _check(_lib.iontrap_estimate_bytes(int(n), int(precision), ctypes.byref(b)), "iontrap_estimate_bytes")
     return b.value
 
 

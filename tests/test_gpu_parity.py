@@ -452,6 +452,14 @@ def test_coincident_ions_report_nonfinite(it):
 
 # ------------------------------------------------------------------ serving loop
 
+def test_estimate_bytes_matches_handle(it):
+    for n in (1, 100, 2048, 5000, 40000):
+        w = _cloud(n, 60 + n)
+        for prec in (0, 1):
+            with _sim(it, w, prec) as s:
+                assert it.iontrap_device_bytes(s.handle) == it.iontrap_estimate_bytes(n, prec)
+
+
 def test_server_results_equal_alone_and_respect_budget(it):
     """Continuous batching: requests of different sizes and step budgets (one with an
     unstable trap) submitted while others run, under a memory budget small enough that
@@ -486,6 +494,7 @@ def test_server_results_equal_alone_and_respect_budget(it):
                 done[rid] = True
             stats = it.iontrap_server_stats(srv)
             assert stats["device_bytes"] <= budget and stats["resident"] <= 6
+
             polls += 1
             assert time.time() - t0 < 300
             time.sleep(0.001)
