@@ -192,6 +192,7 @@ def run_gpu(args):
     params = it.make_params(w.trap, precision=it.IONTRAP_PREC_FP32)
     # per-rank replica (weak scaling: every rank advances its own copy of the workload)
     sim = it.Simulation(w.species, w.species_of_ion, w.x0, w.v0, params, stream=stream)
+    tuned, tuned_us = sim.autotune(trial_us=args.tune_us)  # the library's autotuner (state unchanged)
     cfg = sim.config()
     sim.step(200)
     sim.sync()
@@ -275,6 +276,7 @@ def run_gpu(args):
                                "q=0.3 a=-0.001 f_z=0.2 MHz, Langevin 1e5/s 1 mK, dt=T_RF/20, "
                                "FP32 pairs + Kahan, FP64 state",
                    "n_ions": n, "timesteps_per_step": nsteps, "tile": list(cfg),
+                   "tile_fields": "threads, ions_per_thread, packed, jsplit, fused, pdl, graph (autotuned)",
                    "l2": "flushed (256 MB write) between timed steps; state is L2-resident within a step"},
         "pair_interactions_per_s": value * (n - 1),
         "e2e": {"value": e2e_value, "unit": "ion-steps/s", "h2d_bytes_per_step": h2d,
@@ -325,6 +327,7 @@ def extra_measurements(it, torch, stream, sms, args):
     nc = wc.n
     pc = it.make_params(wc.trap, precision=it.IONTRAP_PREC_FP32)
     with it.Simulation(wc.species, wc.species_of_ion, wc.x0, wc.v0, pc, stream=stream) as s:
+        s.autotune(trial_us=args.tune_us * 4)
         s.step(10)
         s.sync()
         k = 1000
@@ -450,6 +453,7 @@ def main():
     ap.add_argument("--ref-sample-steps", type=int, default=100)
     ap.add_argument("--fp64-steps", type=int, default=50)
     ap.add_argument("--serve-requests", type=int, default=800)
+    ap.add_argument("--tune-us", type=float, default=3000.0)
     ap.add_argument("--serve-step-scale", type=float, default=1000.0)
     ap.add_argument("--serve-budget-mb", type=int, default=2048)
     ap.add_argument("--serve-fp64-subset", type=int, default=20)

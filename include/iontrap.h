@@ -269,6 +269,26 @@ int iontrap_forces_noalloc(const iontrap_species *species, int n_species, const 
  * Synchronous; EINVAL if cap is too small. */
 int iontrap_trace_step(iontrap_t *h, unsigned long long *marks, int64_t cap, int64_t *n_force, int64_t *n_epi);
 
+/* Autotuner.  Times candidate launch configurations (threads x ions per thread x packed,
+ * a ladder of split counts, fused or separate epilogue) on this handle's own workload,
+ * each for about trial_us of steps, installs the fastest and records it in the
+ * process-wide tuning table under (precision, floor(log2 n)) for the current device;
+ * handles created later with n in that bucket start from it.  The handle's state is
+ * checkpointed before and restored after, so tuning does not advance the simulation.
+ * *best and *best_us_per_step (either may be NULL) receive the winner.  Synchronous. */
+typedef struct {
+    int32_t precision;        /* IONTRAP_PREC_* */
+    int32_t log2n;            /* bucket: floor(log2 n) */
+    int32_t threads, ions_per_thread, packed, splits, fused, pdl, graph;
+    float us_per_step;        /* measured time of the winner */
+} iontrap_tuning_entry;
+int iontrap_autotune(iontrap_t *h, double trial_us, iontrap_config *best, double *best_us_per_step);
+/* Read the tuning table of the current device (up to cap entries; *count = entries). */
+int iontrap_tuning_get(iontrap_tuning_entry *out, int cap, int *count);
+/* Add or replace entries of the current device's tuning table (e.g. saved from an
+ * earlier autotuning run on the same kind of GPU). */
+int iontrap_tuning_put(const iontrap_tuning_entry *in, int count);
+
 /* Microbenchmark of the pipes the step kernels use (not part of the method): runs
  * independent dependency chains of one instruction kind on every SM of the current
  * device and reports lane operations per SM clock and the SM clock seen.

@@ -6,10 +6,13 @@
 // are enqueued as an instantiated CUDA graph of 100 chained kernel nodes (built node by
 // node, so any stream works, including the legacy default stream) plus single launches
 // for the remainder; no host round trip happens between steps.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -185,6 +188,37 @@ int64_t gcd64(int64_t a, int64_t b) {
     b = t;
   }
   return a;
+}
+
+// Process-wide tuning table: (device, precision, floor(log2 n)) -> configuration.
+struct TuneKey {
+  int dev, prec, log2n;
+  bool operator<(const TuneKey& o) const {
+    return dev != o.dev ? dev < o.dev : (prec != o.prec ? prec < o.prec : log2n < o.log2n);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, iontrap_tuning_entry> g_tune;
+
+int log2_floor(int64_t n) {
+  int k = 0;
+  while ((n >> (k + 1)) > 0) ++k;
+  return k;
+}
+
+bool tuned_config(int64_t n, int f64, int dev, iontrap_config* c) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tune.find(TuneKey{dev, f64, log2_floor(n)});
+  if (it == g_tune.end()) return false;
+  const iontrap_tuning_entry& e = it->second;
+  c->threads = e.threads;
+  c->ions_per_thread = e.ions_per_thread;
+  c->packed = e.packed;
+  c->fused = e.fused;
+  c->pdl = e.pdl;
+  c->graph = e.graph;
+  c->jsplit = (int32_t)std::max<int64_t>(1, cdiv(n, std::max(1, e.splits)));
+  return true;
 }
 
 // Default tile configuration for n ions.  The i-block (T*I ions) grows with n: small
@@ -460,6 +494,15 @@ int iontrap_create(const iontrap_species* species, int n_species, const uint8_t*
     h->own_stream = true;
   }
   default_config(n, h->f64, h->sms, &h->T, &h->I, &h->packed, &h->jsplit, &h->fused);
+  {
+    iontrap_config tc{};
+    if (tuned_config(n, h->f64, h->device, &tc) && step_kernel(h->f64, tc.threads, tc.ions_per_thread, tc.packed, tc.fused) &&
+        tc.jsplit >= 1 && tc.jsplit <= n && (!h->f64 || tc.jsplit <= kMaxJsplitF64) &&
+        (tc.fused || cdiv(n, tc.jsplit) <= kMaxSplitsUnfused)) {
+      h->T = tc.threads, h->I = tc.ions_per_thread, h->packed = tc.packed, h->jsplit = tc.jsplit;
+      h->fused = tc.fused, h->pdl = tc.pdl, h->use_graph = tc.graph;
+    }
+  }
 
   // species table
   const double dt = h->p.dt;
@@ -796,10 +839,144 @@ int iontrap_estimate_bytes(int64_t n, int precision, int64_t* bytes) {
   const int f64 = precision == IONTRAP_PREC_FP64;
   int T, I, P, J, F;
   default_config(n, f64, sms, &T, &I, &P, &J, &F);
+  iontrap_config tc{};
+  if (tuned_config(n, f64, dev, &tc) && step_kernel(f64, tc.threads, tc.ions_per_thread, tc.packed, tc.fused)) {
+    T = tc.threads, I = tc.ions_per_thread, J = tc.jsplit;
+  }
   const int64_t splits = cdiv(n, J), iblocks = cdiv(n, (int64_t)T * I);
   const int64_t vec = 3 * n * (int64_t)sizeof(double);
   const int64_t pair = n * (int64_t)(f64 ? sizeof(double4_32a) : 2 * sizeof(float4));
   *bytes = 3 * vec + n + 2 * pair + splits * n * 32 + iblocks * (int64_t)sizeof(unsigned) + 64;
+  return IONTRAP_OK;
+}
+
+int iontrap_autotune(iontrap_t* h, double trial_us, iontrap_config* best, double* best_us) {
+  if (!h || !(trial_us > 0)) return IONTRAP_EINVAL;
+  int st = iontrap_sync(h);
+  if (st) return st;
+  const int64_t n = h->n;
+  std::vector<double> cx(3 * n), cv(3 * n), ca(3 * n);
+  int64_t cstep = 0;
+  st = iontrap_checkpoint(h, cx.data(), cv.data(), ca.data(), &cstep);
+  if (st) return st;
+  iontrap_config orig{};
+  iontrap_get_config(h, &orig);
+  // candidates
+  struct Shape {
+    int T, I, P;
+  };
+  std::vector<Shape> shapes;
+  if (h->f64) {
+    shapes = {{64, 1, 0}, {128, 1, 0}, {128, 2, 0}, {256, 1, 0}};
+  } else {
+    const Shape small[] = {{64, 1, 0}, {128, 1, 0}, {64, 2, 1}, {128, 2, 1}};
+    const Shape large[] = {{64, 4, 1}, {128, 4, 1}, {256, 4, 1}, {128, 2, 1}};
+    if (n < 16384) {
+      for (const Shape& sh : small)
+        if ((int64_t)sh.T * sh.I <= std::max<int64_t>(64, 2 * n)) shapes.push_back(sh);
+    } else {
+      for (const Shape& sh : large) shapes.push_back(sh);
+    }
+  }
+  std::vector<iontrap_config> cands;
+  for (const Shape& sh : shapes) {
+    const int64_t iblocks = cdiv(n, (int64_t)sh.T * sh.I);
+    std::vector<int64_t> splits = {1, 2, 4};
+    for (int w = 1; w <= 16; w *= 2) {
+      const int64_t S = cdiv((int64_t)w * h->sms, iblocks);
+      splits.push_back(S);
+      const int64_t g = h->sms / gcd64(iblocks, h->sms);  // grid an exact multiple of the SM count
+      splits.push_back(cdiv(S, g) * g);
+    }
+    std::sort(splits.begin(), splits.end());
+    splits.erase(std::unique(splits.begin(), splits.end()), splits.end());
+    for (int64_t S : splits) {
+      if (S < 1 || S > 64 || S > std::max<int64_t>(1, n / 32)) continue;
+      int64_t js = cdiv(n, S);
+      if (h->f64 && js > kMaxJsplitF64) continue;
+      for (int fused = 1; fused >= (h->f64 ? 1 : 0); --fused) {
+        if (!fused && cdiv(n, js) > kMaxSplitsUnfused) continue;
+        iontrap_config c{sh.T, sh.I, sh.P, (int32_t)js, fused, 0, 1};
+        if (step_kernel(h->f64, c.threads, c.ions_per_thread, c.packed, c.fused)) cands.push_back(c);
+      }
+    }
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return IONTRAP_ECUDA;
+  double best_t = 1e300;
+  iontrap_config bc = orig;
+  for (const iontrap_config& c : cands) {
+    if (iontrap_set_config(h, &c)) continue;
+    // calibrate on a few single launches, then time whole graphs for about trial_us
+    if (iontrap_step(h, 2) || iontrap_sync(h)) break;
+    cudaEventRecord(e0, h->stream);
+    iontrap_step(h, 5);
+    cudaEventRecord(e1, h->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double graph_us = ms * 1e3 / 5.0 * kGraphSteps;
+    const int64_t reps = std::max<int64_t>(1, std::min<int64_t>(50, (int64_t)(trial_us / std::max(1.0, graph_us))));
+    iontrap_step(h, kGraphSteps);  // instantiates the graph outside the timed region
+    cudaEventRecord(e0, h->stream);
+    iontrap_step(h, reps * kGraphSteps);
+    cudaEventRecord(e1, h->stream);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double us = ms * 1e3 / (double)(reps * kGraphSteps);
+    if (h->status) break;
+    if (us < best_t) {
+      best_t = us;
+      bc = c;
+    }
+    if (iontrap_restore(h, cx.data(), cv.data(), ca.data(), cstep)) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (h->status) return h->status;
+  st = iontrap_set_config(h, &bc);
+  if (!st) st = iontrap_restore(h, cx.data(), cv.data(), ca.data(), cstep);
+  if (st) return st;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    iontrap_tuning_entry e{};
+    e.precision = h->f64;
+    e.log2n = log2_floor(n);
+    e.threads = bc.threads, e.ions_per_thread = bc.ions_per_thread, e.packed = bc.packed;
+    e.splits = (int32_t)cdiv(n, bc.jsplit), e.fused = bc.fused, e.pdl = bc.pdl, e.graph = bc.graph;
+    e.us_per_step = (float)best_t;
+    g_tune[TuneKey{h->device, h->f64, e.log2n}] = e;
+  }
+  if (best) *best = bc;
+  if (best_us) *best_us = best_t;
+  return IONTRAP_OK;
+}
+
+int iontrap_tuning_get(iontrap_tuning_entry* out, int cap, int* count) {
+  if (!count || cap < 0 || (cap > 0 && !out)) return IONTRAP_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return IONTRAP_ECUDA;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  int k = 0;
+  for (const auto& kv : g_tune)
+    if (kv.first.dev == dev) {
+      if (k < cap) out[k] = kv.second;
+      ++k;
+    }
+  *count = k;
+  return IONTRAP_OK;
+}
+
+int iontrap_tuning_put(const iontrap_tuning_entry* in, int count) {
+  if (count < 0 || (count > 0 && !in)) return IONTRAP_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return IONTRAP_ECUDA;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  for (int k = 0; k < count; ++k) {
+    const iontrap_tuning_entry& e = in[k];
+    if ((e.precision != 0 && e.precision != 1) || e.log2n < 0 || e.log2n > 40 || e.splits < 1) return IONTRAP_EINVAL;
+    g_tune[TuneKey{dev, e.precision, e.log2n}] = e;
+  }
   return IONTRAP_OK;
 }
 

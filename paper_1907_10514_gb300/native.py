@@ -64,6 +64,13 @@ class iontrap_server_counters(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64)]
 
 
+class iontrap_tuning_entry(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("log2n", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("ions_per_thread", ctypes.c_int32), ("packed", ctypes.c_int32), ("splits", ctypes.c_int32),
+                ("fused", ctypes.c_int32), ("pdl", ctypes.c_int32), ("graph", ctypes.c_int32),
+                ("us_per_step", ctypes.c_float)]
+
+
 # symbol name -> (restype, argtypes)
 _dp = ctypes.POINTER(ctypes.c_double)
 _i64p = ctypes.POINTER(ctypes.c_int64)
@@ -92,6 +99,9 @@ SIGNATURES = {
     "iontrap_forces_noalloc": (ctypes.c_int, [ctypes.POINTER(iontrap_species), ctypes.c_int, _vp, _vp,
                                               ctypes.c_int64, _vp, _vp]),
     "iontrap_device_bytes": (ctypes.c_int, [_vp, _i64p]),
+    "iontrap_autotune": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.POINTER(iontrap_config), _dp]),
+    "iontrap_tuning_get": (ctypes.c_int, [ctypes.POINTER(iontrap_tuning_entry), ctypes.c_int, _ip]),
+    "iontrap_tuning_put": (ctypes.c_int, [ctypes.POINTER(iontrap_tuning_entry), ctypes.c_int]),
     "iontrap_estimate_bytes": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, _i64p]),
     "iontrap_server_create": (ctypes.c_int, [ctypes.POINTER(iontrap_server_config), ctypes.POINTER(_vp)]),
     "iontrap_server_submit": (ctypes.c_int, [_vp, ctypes.POINTER(iontrap_species), ctypes.c_int,
@@ -292,6 +302,34 @@ def iontrap_device_bytes(h) -> int:
     return b.value
 
 
+def iontrap_autotune(h, trial_us: float = 3000.0):
+    """Returns ((threads, ions_per_thread, packed, jsplit, fused, pdl, graph), us_per_step)."""
+    c = iontrap_config()
+    us = ctypes.c_double()
+    _check(_lib.iontrap_autotune(h, float(trial_us), ctypes.byref(c), ctypes.byref(us)), "iontrap_autotune")
+    return (c.threads, c.ions_per_thread, c.packed, c.jsplit, c.fused, c.pdl, c.graph), us.value
+
+
+_TUNE_FIELDS = [f for f, _ in iontrap_tuning_entry._fields_]
+
+
+def iontrap_tuning_get():
+    """The current device's tuning table as a list of dicts."""
+    cnt = ctypes.c_int()
+    _check(_lib.iontrap_tuning_get(None, 0, ctypes.byref(cnt)), "iontrap_tuning_get")
+    arr = (iontrap_tuning_entry * max(1, cnt.value))()
+    _check(_lib.iontrap_tuning_get(arr, cnt.value, ctypes.byref(cnt)), "iontrap_tuning_get")
+    return [{f: getattr(arr[k], f) for f in _TUNE_FIELDS} for k in range(cnt.value)]
+
+
+def iontrap_tuning_put(entries) -> None:
+    arr = (iontrap_tuning_entry * max(1, len(entries)))()
+    for k, e in enumerate(entries):
+        for f in _TUNE_FIELDS:
+            setattr(arr[k], f, e[f])
+    _check(_lib.iontrap_tuning_put(arr, len(entries)), "iontrap_tuning_put")
+
+
 def iontrap_estimate_bytes(n: int, precision: int = IONTRAP_PREC_FP32) -> int:
     b = ctypes.c_int64()
     _check(_lib.iontrap_estimate_bytes(int(n), int(precision), ctypes.byref(b)), "iontrap_estimate_bytes")
@@ -390,6 +428,9 @@ class Simulation:
 
     def config(self):
         return iontrap_get_config(self.handle)
+
+    def autotune(self, trial_us: float = 3000.0):
+        return iontrap_autotune(self.handle, trial_us)
 
     def set_config(self, threads, ions_per_thread, packed, jsplit, fused=1, pdl=1, graph=1) -> None:
         iontrap_set_config(self.handle, threads, ions_per_thread, packed, jsplit, fused, pdl, graph)

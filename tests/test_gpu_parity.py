@@ -522,3 +522,33 @@ def test_server_results_equal_alone_and_respect_budget(it):
             assert np.array_equal(x, xa) and np.array_equal(v, va), (k, w.n)
     finally:
         it.iontrap_server_destroy(srv)
+
+
+# ------------------------------------------------------------------ autotuner
+
+def test_autotune_keeps_state_and_records_bucket(it):
+    n = 3000
+    w = _cloud(n, 88)
+    q, m, _ = _oracle_side(w)
+    with _sim(it, w, 0) as sim:
+        sim.step(37)
+        before = sim.checkpoint()
+        cfg, us = sim.autotune(trial_us=400.0)
+        after = sim.checkpoint()
+        assert after[3] == before[3] == 37
+        for b, a in zip(before[:3], after[:3]):
+            assert np.array_equal(a, b)
+        assert sim.config() == cfg and us > 0
+        f = sim.forces()
+        assert rel_rms(f, oracle.coulomb_accel(after[0], q, m)) < FP32_FORCE_TOL
+    table = it.iontrap_tuning_get()
+    entry = [e for e in table if e["precision"] == 0 and e["log2n"] == 11]
+    assert len(entry) == 1 and entry[0]["threads"] == cfg[0] and entry[0]["splits"] == -(-n // cfg[3])
+    # a new handle in the same bucket starts from the tuned configuration
+    w2 = _cloud(2500, 89)
+    with _sim(it, w2, 0) as s2:
+        c2 = s2.config()
+        assert c2[:3] == cfg[:3] and c2[4] == cfg[4] and -(-2500 // c2[3]) == entry[0]["splits"]
+    # the table round-trips
+    it.iontrap_tuning_put(table)
+    assert it.iontrap_tuning_get() == table
