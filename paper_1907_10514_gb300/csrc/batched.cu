@@ -48,15 +48,23 @@ struct BatchCta {
   int rank0, nranks;       // cluster ranks that hold copies of ens[0] (multi-CTA ensemble)
 };
 
-__global__ void __cluster_dims__(kBCluster, 1, 1) __launch_bounds__(kBThreads)
-    k_batched(BatchEns* __restrict__ E, const BatchCta* __restrict__ J, int K) {
+// clustered = 1: launched in clusters of 8 (ensembles spread over several CTAs, synced by
+// the hardware cluster barrier); 0: every CTA holds whole ensembles and only syncs itself.
+__global__ void __launch_bounds__(kBThreads)
+    k_batched(BatchEns* __restrict__ E, const BatchCta* __restrict__ J, int K, int clustered) {
   extern __shared__ __align__(16) float4 sm[];
   __shared__ BatchCta job;
-  __shared__ double s_cos[kBWarps];
+  __shared__ double s_springs[kBWarps][IONTRAP_MAX_SPECIES][3];
   __shared__ int s_steps[kBWarps];
   __shared__ long long s_n0[kBWarps];
   cg::cluster_group cluster = cg::this_cluster();
-  const unsigned my_rank = cluster.block_rank();
+  const unsigned my_rank = clustered ? cluster.block_rank() : 0u;
+  auto sync_all = [&]() {
+    if (clustered)
+      cluster.sync();
+    else
+      __syncthreads();
+  };
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   if (tid == 0) job = J[blockIdx.x];
@@ -96,16 +104,20 @@ __global__ void __cluster_dims__(kBCluster, 1, 1) __launch_bounds__(kBThreads)
     spi[q] = ok ? ens->sp[ii[q]] : 0;
   }
   bool finite = true;
-  cluster.sync();  // every copy staged before any CTA writes into another's
+  sync_all();  // every copy staged before any CTA writes into another's
 
   int kmax = 0;
   for (int q = 0; q < job.nens; ++q) kmax = max(kmax, s_steps[q]);
   // kmax is uniform within a CTA; CTAs of one cluster may differ, so the loop runs to K
   for (int k = 0; k < K; ++k) {
+    // per held ensemble: RF phase at the force time, then its species' spring constants
     if (tid < job.nens && k < s_steps[tid]) {
-      const TrapDev& tp = E[job.ens[tid]].trap;
+      const BatchEns& e = E[job.ens[tid]];
+      const TrapDev& tp = e.trap;
       const long long nf = s_n0[tid] + k + 1;
-      s_cos[tid] = (tp.flags & (IONTRAP_RF_OFF | IONTRAP_TRAP_OFF)) ? 0.0 : cos(tp.Omega * ((double)nf * tp.dt));
+      const double cosv =
+          (tp.flags & (IONTRAP_RF_OFF | IONTRAP_TRAP_OFF)) ? 0.0 : cos(tp.Omega * ((double)nf * tp.dt));
+      for (int sp = 0; sp < e.nspecies; ++sp) trap_springs(tp, e.spc[sp], cosv, s_springs[tid][sp]);
     }
     __syncthreads();
     const bool active = ens && k < s_steps[le];
@@ -152,7 +164,7 @@ __global__ void __cluster_dims__(kBCluster, 1, 1) __launch_bounds__(kBThreads)
 #pragma unroll
         for (int c = 0; c < 3; ++c) S[q][c] = (double)kc[q][c] - (double)ks[q][c];  // negated sums
     }
-    cluster.sync();  // every read of every stream copy in the cluster is done
+    sync_all();  // every read of every stream copy is done
     if (active) {
       const TrapDev& tp = ens->trap;
       const long long ns = s_n0[le] + k;
@@ -167,7 +179,7 @@ __global__ void __cluster_dims__(kBCluster, 1, 1) __launch_bounds__(kBThreads)
           vd[c] = half_kick(v[q][c], a[q][c], tp.hdt);
           xf[c] = drift(x[q][c], vd[c], tp.dt);
         }
-        accel_ion<false>(tp, sd, S[q], xf, vd, s_cos[le], ns + 1, ii[q], acc);
+        accel_ion<false>(tp, sd, s_springs[le][spi[q]], S[q], xf, vd, ns + 1, ii[q], acc);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const double vn = half_kick(vd[c], acc[c], tp.hdt);
@@ -186,13 +198,13 @@ __global__ void __cluster_dims__(kBCluster, 1, 1) __launch_bounds__(kBThreads)
         const float4 h4 = make_float4(hv[0], hv[1], hv[2], sd.w);
         const float4 l4 = make_float4(lv[0], lv[1], lv[2], 0.0f);
         for (int r = job.rank0; r < job.rank0 + job.nranks; ++r) {
-          float4* dst = (r == (int)my_rank) ? sh : cluster.map_shared_rank(sh, r);
+          float4* dst = (r == (int)my_rank) ? sh : cluster.map_shared_rank(sh, (unsigned)r);
           dst[ii[q]] = h4;
           dst[n + ii[q]] = l4;
         }
       }
     }
-    cluster.sync();  // new entries visible in every copy
+    sync_all();  // new entries visible in every copy
   }
   (void)kmax;
 
@@ -224,11 +236,15 @@ __global__ void __cluster_dims__(kBCluster, 1, 1) __launch_bounds__(kBThreads)
 
 // ------------------------------------------------------------------ host side
 struct BatchPlan {
-  std::vector<BatchCta> ctas;
-  size_t smem = 0;
+  std::vector<BatchCta> clustered;  // CTAs of ensembles spread over 2, 4 or 8 CTAs (clusters of 8)
+  std::vector<BatchCta> single;     // CTAs holding whole ensembles (no cluster)
+  size_t smem_clustered = 0, smem_single = 0;
 };
 
-// Pack ensembles (sizes n[e]) into CTAs and clusters of 8.
+// Pack ensembles (sizes n[e]) into CTAs: ensembles above one CTA's 256 ions into
+// aligned power-of-two groups of clusters of 8 (largest first, similar sizes together);
+// the rest one per CTA (64 < N <= 256) or four per CTA (N <= 64), heaviest first, in a
+// grid without clusters.
 static BatchPlan plan_batch(const std::vector<long long>& n) {
   BatchPlan plan;
   struct Job {
@@ -236,18 +252,22 @@ static BatchPlan plan_batch(const std::vector<long long>& n) {
     int ctas;
     long long work;
   };
-  std::vector<Job> big, small;
+  std::vector<Job> big, mid, small;
   for (int e = 0; e < (int)n.size(); ++e) {
     if (n[e] <= kBWarpIons) {
-      small.push_back({e, 0, n[e] * n[e]});
+      small.push_back({e, 1, n[e] * n[e]});
+    } else if (n[e] <= kBCtaIons) {
+      mid.push_back({e, 1, n[e] * n[e]});
     } else {
-      int c = 1;
+      int c = 2;
       while ((long long)c * kBCtaIons < n[e]) c *= 2;
       big.push_back({e, c, n[e] * n[e]});
     }
   }
-  std::sort(big.begin(), big.end(), [](const Job& a, const Job& b) { return a.ctas != b.ctas ? a.ctas > b.ctas : a.work > b.work; });
-  std::sort(small.begin(), small.end(), [](const Job& a, const Job& b) { return a.work > b.work; });
+  auto heavier = [](const Job& a, const Job& b) { return a.ctas != b.ctas ? a.ctas > b.ctas : a.work > b.work; };
+  std::sort(big.begin(), big.end(), heavier);
+  std::sort(mid.begin(), mid.end(), heavier);
+  std::sort(small.begin(), small.end(), heavier);
   auto blank = []() {
     BatchCta c{};
     c.nens = 0;
@@ -256,51 +276,42 @@ static BatchPlan plan_batch(const std::vector<long long>& n) {
     c.nranks = 1;
     return c;
   };
-  size_t smem = 0;
-  // multi-CTA and single-CTA ensembles: buddy placement inside clusters of 8
-  std::vector<BatchCta> cl;
+  auto whole = [&](const Job& j, int r, int r0, int c) {
+    BatchCta t = blank();
+    t.nens = 1;
+    t.ens[0] = j.e;
+    t.soff[0] = 0;
+    for (int w = 0; w < kBWarps; ++w) {
+      const long long i0 = (long long)r * kBCtaIons + (long long)w * kBWarpIons;
+      if (i0 < n[j.e]) {
+        t.warp_le[w] = 0;
+        t.warp_i0[w] = (int)i0;
+      }
+    }
+    t.rank0 = r0;
+    t.nranks = c;
+    return t;
+  };
+  // clustered grid: buddy placement of power-of-two groups inside clusters of 8
   int used = 0;
-  auto flush = [&]() {
-    while (used % kBCluster) {
-      cl.push_back(blank());
+  for (const Job& j : big) {
+    while (used % j.ctas) {
+      plan.clustered.push_back(blank());
       ++used;
     }
-    plan.ctas.insert(plan.ctas.end(), cl.begin(), cl.end());
-    cl.clear();
-    used = 0;
-  };
-  for (const Job& j : big) {
-    const int c = j.ctas;
-    if (used % c) {  // keep power-of-two groups aligned inside the cluster
-      while (used % c) {
-        cl.push_back(blank());
-        ++used;
-      }
-    }
-    if (used + c > kBCluster) flush();
+    if (used == kBCluster) used = 0;
     const int r0 = used;
-    const long long N = n[j.e];
-    for (int r = 0; r < c; ++r) {
-      BatchCta t = blank();
-      t.nens = 1;
-      t.ens[0] = j.e;
-      t.soff[0] = 0;
-      for (int w = 0; w < kBWarps; ++w) {
-        const long long i0 = (long long)r * kBCtaIons + (long long)w * kBWarpIons;
-        if (i0 < N) {
-          t.warp_le[w] = 0;
-          t.warp_i0[w] = (int)i0;
-        }
-      }
-      t.rank0 = r0;
-      t.nranks = c;
-      cl.push_back(t);
-    }
-    used += c;
-    smem = std::max(smem, (size_t)N * 2 * sizeof(float4));
-    if (used == kBCluster) flush();
+    for (int r = 0; r < j.ctas; ++r) plan.clustered.push_back(whole(j, r, r0, j.ctas));
+    used += j.ctas;
+    if (used == kBCluster) used = 0;
+    plan.smem_clustered = std::max(plan.smem_clustered, (size_t)n[j.e] * 2 * sizeof(float4));
   }
-  // small ensembles: four per CTA, one warp each
+  while (plan.clustered.size() % kBCluster) plan.clustered.push_back(blank());
+  // single grid
+  for (const Job& j : mid) {
+    plan.single.push_back(whole(j, 0, 0, 1));
+    plan.smem_single = std::max(plan.smem_single, (size_t)n[j.e] * 2 * sizeof(float4));
+  }
   for (size_t k = 0; k < small.size(); k += kBWarps) {
     BatchCta t = blank();
     int off = 0;
@@ -313,18 +324,9 @@ static BatchPlan plan_batch(const std::vector<long long>& n) {
       off += (int)n[e] * 2;
       t.nens = w + 1;
     }
-    t.rank0 = used;
-    t.nranks = 1;
-    cl.push_back(t);
-    ++used;
-    smem = std::max(smem, (size_t)off * sizeof(float4));
-    if (used == kBCluster) flush();
+    plan.single.push_back(t);
+    plan.smem_single = std::max(plan.smem_single, (size_t)off * sizeof(float4));
   }
-  if (used) flush();
-  // single-CTA placements: a CTA's own rank is its position in its cluster
-  for (size_t c = 0; c < plan.ctas.size(); ++c)
-    if (plan.ctas[c].nranks == 1) plan.ctas[c].rank0 = (int)(c % kBCluster);
-  plan.smem = smem;
   return plan;
 }
 
@@ -334,12 +336,25 @@ struct BatchBuffers {
   size_t ens_cap = 0;
   BatchCta* d_cta = nullptr;
   size_t cta_cap = 0;
-  cudaEvent_t done = nullptr;  // recorded after the previous launches, which read the tables
+  cudaStream_t side = nullptr;  // second stream: the single-CTA grid runs beside the clustered one
+  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaEvent_t done = nullptr;   // recorded after the previous launches, which read the tables
   bool pending = false;
 };
 static BatchBuffers g_bb;
 
 int batched_max_n() { return kBMaxN; }
+
+static cudaError_t grow(void** p, size_t* cap, size_t need, size_t elem) {
+  if (need <= *cap) return cudaSuccess;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  const size_t c = std::max(need, (size_t)64);
+  cudaError_t e = cudaMalloc(p, c * elem);
+  if (e == cudaSuccess) *cap = c;
+  return e;
+}
 
 // Enqueue `steps[e]` steps of every ensemble on `stream`, K steps per launch.
 cudaError_t launch_batched(const std::vector<BatchEns>& ens_in, const std::vector<long long>& steps, int K,
@@ -353,55 +368,67 @@ cudaError_t launch_batched(const std::vector<BatchEns>& ens_in, const std::vecto
   }
   if (max_steps == 0) return cudaSuccess;
   BatchPlan plan = plan_batch(n);
-  // The tables below are shared by all calls: wait until the previous launches, which
-  // may run on another (possibly since destroyed) stream, have finished reading them.
+  cudaError_t err = cudaSuccess;
   if (!g_bb.done) {
-    cudaError_t e = cudaEventCreateWithFlags(&g_bb.done, cudaEventDisableTiming);
-    if (e != cudaSuccess) return e;
-  }
-  if (g_bb.pending) {
-    cudaError_t e = cudaEventSynchronize(g_bb.done);
-    if (e != cudaSuccess) return e;
-    g_bb.pending = false;
-  }
-  if (ens_in.size() > g_bb.ens_cap) {
-    if (g_bb.d_ens) cudaFree(g_bb.d_ens);
-    g_bb.ens_cap = std::max(ens_in.size(), (size_t)64);
-    cudaError_t e = cudaMalloc(&g_bb.d_ens, g_bb.ens_cap * sizeof(BatchEns));
-    if (e != cudaSuccess) {
-      g_bb.ens_cap = 0;
-      g_bb.d_ens = nullptr;
-      return e;
-    }
-  }
-  if (plan.ctas.size() > g_bb.cta_cap) {
-    if (g_bb.d_cta) cudaFree(g_bb.d_cta);
-    g_bb.cta_cap = std::max(plan.ctas.size(), (size_t)64);
-    cudaError_t e = cudaMalloc(&g_bb.d_cta, g_bb.cta_cap * sizeof(BatchCta));
-    if (e != cudaSuccess) {
-      g_bb.cta_cap = 0;
-      g_bb.d_cta = nullptr;
-      return e;
-    }
-  }
-  std::vector<BatchEns> ens = ens_in;
-  for (size_t e = 0; e < ens.size(); ++e) ens[e].remaining = steps[e];
-  // synchronous copies: the host vectors die with this call
-  cudaError_t err = cudaStreamSynchronize(stream);
-  if (err == cudaSuccess)
-    err = cudaMemcpy(g_bb.d_ens, ens.data(), ens.size() * sizeof(BatchEns), cudaMemcpyHostToDevice);
-  if (err == cudaSuccess)
-    err = cudaMemcpy(g_bb.d_cta, plan.ctas.data(), plan.ctas.size() * sizeof(BatchCta), cudaMemcpyHostToDevice);
-  if (err != cudaSuccess) return err;
-  const size_t smem = std::max<size_t>(plan.smem, 16);
-  err = cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return err;
-  for (long long done = 0; done < max_steps; done += K) {
-    k_batched<<<(unsigned)plan.ctas.size(), kBThreads, smem, stream>>>(g_bb.d_ens, g_bb.d_cta, K);
-    err = cudaGetLastError();
+    err = cudaEventCreateWithFlags(&g_bb.done, cudaEventDisableTiming);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&g_bb.fork, cudaEventDisableTiming);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&g_bb.join, cudaEventDisableTiming);
+    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&g_bb.side, cudaStreamNonBlocking);
     if (err != cudaSuccess) return err;
   }
-  err = cudaEventRecord(g_bb.done, stream);
+  // The tables are shared by all calls: wait until the previous launches, which may run
+  // on another (possibly since destroyed) stream, have finished reading them.
+  if (g_bb.pending) {
+    err = cudaEventSynchronize(g_bb.done);
+    if (err != cudaSuccess) return err;
+    g_bb.pending = false;
+  }
+  const size_t nc = plan.clustered.size(), ns = plan.single.size();
+  err = grow((void**)&g_bb.d_ens, &g_bb.ens_cap, ens_in.size(), sizeof(BatchEns));
+  if (err == cudaSuccess) err = grow((void**)&g_bb.d_cta, &g_bb.cta_cap, nc + ns, sizeof(BatchCta));
+  if (err != cudaSuccess) return err;
+  std::vector<BatchEns> ens = ens_in;
+  for (size_t e = 0; e < ens.size(); ++e) ens[e].remaining = steps[e];
+  std::vector<BatchCta> ctas = plan.clustered;
+  ctas.insert(ctas.end(), plan.single.begin(), plan.single.end());
+  // synchronous copies: the host vectors die with this call
+  err = cudaStreamSynchronize(stream);
+  if (err == cudaSuccess)
+    err = cudaMemcpy(g_bb.d_ens, ens.data(), ens.size() * sizeof(BatchEns), cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMemcpy(g_bb.d_cta, ctas.data(), ctas.size() * sizeof(BatchCta), cudaMemcpyHostToDevice);
+  if (err != cudaSuccess) return err;
+  const size_t smem = std::max<size_t>(std::max(plan.smem_clustered, plan.smem_single), 16);
+  err = cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  // fork: the single-CTA grid on the side stream, the clustered grid on `stream`
+  err = cudaEventRecord(g_bb.fork, stream);
+  if (err == cudaSuccess) err = cudaStreamWaitEvent(g_bb.side, g_bb.fork, 0);
+  for (long long done = 0; done < max_steps && err == cudaSuccess; done += K) {
+    if (nc) {
+      cudaLaunchConfig_t cfg{};
+      cfg.gridDim = dim3((unsigned)nc);
+      cfg.blockDim = dim3(kBThreads);
+      cfg.dynamicSmemBytes = std::max<size_t>(plan.smem_clustered, 16);
+      cfg.stream = stream;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = kBCluster;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      err = cudaLaunchKernelEx(&cfg, k_batched, g_bb.d_ens, (const BatchCta*)g_bb.d_cta, K, 1);
+    }
+    if (ns && err == cudaSuccess) {
+      k_batched<<<(unsigned)ns, kBThreads, std::max<size_t>(plan.smem_single, 16), g_bb.side>>>(
+          g_bb.d_ens, g_bb.d_cta + nc, K, 0);
+      err = cudaGetLastError();
+    }
+  }
+  // join
+  if (err == cudaSuccess) err = cudaEventRecord(g_bb.join, g_bb.side);
+  if (err == cudaSuccess) err = cudaStreamWaitEvent(stream, g_bb.join, 0);
+  if (err == cudaSuccess) err = cudaEventRecord(g_bb.done, stream);
   if (err == cudaSuccess) g_bb.pending = true;
   return err;
 }

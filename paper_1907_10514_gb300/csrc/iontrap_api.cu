@@ -777,6 +777,7 @@ int iontrap_step_many(iontrap_t* const* hs, const int64_t* n_steps, int count) {
     E.n = h->n;
     E.step0 = h->step;
     E.trap = h->args.trap;
+    E.nspecies = h->nspecies;
     std::memcpy(E.spc, h->args.spc, sizeof(E.spc));
     steps[b] = n_steps[batch[b]];
   }

@@ -82,6 +82,7 @@ struct BatchEns {
   long long n;
   long long step0;      // state step index when the batch was enqueued
   long long remaining;  // steps still to take; decremented by the kernel
+  int nspecies;
   TrapDev trap;
   SpeciesDev spc[IONTRAP_MAX_SPECIES];
 };
@@ -300,30 +301,37 @@ __device__ __forceinline__ void write_pair(const StepArgs& A, int b, long long i
   }
 }
 
+// Trap spring constants of one species at force time (RF phase cosv): the trap
+// acceleration is (-kx x, -ky y, -kz z).  Computed once per species per step.
+__device__ __forceinline__ void trap_springs(const TrapDev& tp, const SpeciesDev& sd, double cosv, double k[3]) {
+  if (tp.flags & IONTRAP_TRAP_OFF) {
+    k[0] = k[1] = k[2] = 0.0;
+    return;
+  }
+  const double rwz2 = __dmul_rn(sd.rho, tp.wz2);
+  const double rq4 = __dmul_rn(tp.q4, sd.rho);
+  const double qc2 = __dmul_rn(2.0 * tp.q, cosv);
+  k[0] = __fma_rn(rq4, __dsub_rn(tp.a, qc2), -0.5 * rwz2);
+  k[1] = __fma_rn(rq4, __dadd_rn(tp.a, qc2), -0.5 * rwz2);
+  k[2] = rwz2;
+}
+
 // Acceleration of one ion at force time (FP64 in both forms): Coulomb sum S
-// (sum_j z_j d/r^3) -> k_e e^2 z/M S + trap field at xf (RF phase cosv) - gamma vd +
+// (sum_j z_j d/r^3) -> k_e e^2 z/M S - k xf (springs of the ion's species) - gamma vd +
 // sigma xi(seed, counter, id).  Explicit roundings (no FMA contraction left to the
 // compiler): every kernel that inlines this produces the same bits.  The trajectories
 // of these clouds amplify FP32-sized perturbations of the RF trap term by ~1e4 within
 // 100 steps, so no term is evaluated in FP32.  F64 selects FP64 Box-Muller noise.
 template <bool F64>
-__device__ __forceinline__ void accel_ion(const TrapDev& tp, const SpeciesDev& sd, const double S[3],
-                                          const double xf[3], const double vd[3], double cosv,
+__device__ __forceinline__ void accel_ion(const TrapDev& tp, const SpeciesDev& sd, const double k[3],
+                                          const double S[3], const double xf[3], const double vd[3],
                                           long long counter, long long id, double acc[3]) {
 #pragma unroll
-  for (int c = 0; c < 3; ++c) acc[c] = __dmul_rn(sd.coul, S[c]);
-  if (!(tp.flags & IONTRAP_TRAP_OFF)) {
-    const double rwz2 = __dmul_rn(sd.rho, tp.wz2);
-    const double rq4 = __dmul_rn(tp.q4, sd.rho);
-    const double qc2 = __dmul_rn(2.0 * tp.q, cosv);
-    const double kx = __fma_rn(rq4, __dsub_rn(tp.a, qc2), -0.5 * rwz2);
-    const double ky = __fma_rn(rq4, __dadd_rn(tp.a, qc2), -0.5 * rwz2);
-    acc[0] = __fma_rn(-kx, xf[0], acc[0]);
-    acc[1] = __fma_rn(-ky, xf[1], acc[1]);
-    acc[2] = __fma_rn(-rwz2, xf[2], acc[2]);
+  for (int c = 0; c < 3; ++c) {
+    acc[c] = __dmul_rn(sd.coul, S[c]);
+    acc[c] = __fma_rn(-k[c], xf[c], acc[c]);
+    acc[c] = __fma_rn(-tp.gamma, vd[c], acc[c]);
   }
-#pragma unroll
-  for (int c = 0; c < 3; ++c) acc[c] = __fma_rn(-tp.gamma, vd[c], acc[c]);
   if (sd.sigma > 0.0) {
     double z[3];
     if constexpr (F64) {
@@ -342,10 +350,11 @@ __device__ __forceinline__ void accel_ion(const TrapDev& tp, const SpeciesDev& s
 // pair-stream entry.  cosv = cos(Omega t) at the force time.  F64 selects the plain
 // FP64 form (FP64 noise, double4_32a pair stream).
 template <bool F64>
-__device__ __forceinline__ void epilogue_ion(const StepArgs& A, long long i, const double S[3], double cosv,
-                                             long long ns, int wb) {
+__device__ __forceinline__ void epilogue_ion(const StepArgs& A, long long i, const double S[3],
+                                             const double (*springs)[3], long long ns, int wb) {
   const long long n = A.n;
-  const SpeciesDev sd = A.spc[A.sp[i]];
+  const int spi = A.sp[i];
+  const SpeciesDev sd = A.spc[spi];
   if (A.mode == MODE_FORCES) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) A.out[c * n + i] = sd.coul * S[c];
@@ -363,7 +372,7 @@ __device__ __forceinline__ void epilogue_ion(const StepArgs& A, long long i, con
     xf[c] = step ? drift(x, vh, tp.dt) : x;
   }
   double acc[3];
-  accel_ion<F64>(tp, sd, S, xf, vd, cosv, step ? ns + 1 : ns, i, acc);
+  accel_ion<F64>(tp, sd, springs[spi], S, xf, vd, step ? ns + 1 : ns, i, acc);
   double vn[3], xn[3];
   bool finite = true;
 #pragma unroll

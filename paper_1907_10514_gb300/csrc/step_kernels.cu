@@ -144,6 +144,7 @@ __global__ void __launch_bounds__(T) k_step_f32(const __grid_constant__ StepArgs
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int s_flag;
   __shared__ double s_cos;
+  __shared__ double s_springs[IONTRAP_MAX_SPECIES][3];
 
   pdl_wait();
   const int tid = threadIdx.x;
@@ -280,7 +281,8 @@ __global__ void __launch_bounds__(T) k_step_f32(const __grid_constant__ StepArgs
 
   if (tid == 0) s_cos = force_time_cos(A, ns);
   __syncthreads();
-  const double cosv = s_cos;
+  if (tid < IONTRAP_MAX_SPECIES) trap_springs(A.trap, A.spc[tid], s_cos, s_springs[tid]);
+  __syncthreads();
   const int wb = rb ^ 1;
 #pragma unroll
   for (int k = 0; k < I; ++k) {
@@ -288,7 +290,7 @@ __global__ void __launch_bounds__(T) k_step_f32(const __grid_constant__ StepArgs
     if (i >= n) continue;
     double S[3];
     merge_f32(part, n, i, (int)gridDim.y, S);  // fused path: the last CTA of the i-block
-    epilogue_ion<false>(A, i, S, cosv, ns, wb);
+    epilogue_ion<false>(A, i, S, s_springs, ns, wb);
   }
   finish_iblock(A, ns);
   trace_mark(A.trace, tslot + 3);
@@ -305,6 +307,7 @@ constexpr int kEpiMaxRec = 8;  // records per lane: splits up to 8 * 8 = 64
 
 __global__ void __launch_bounds__(kEpiThreads) k_epilogue_f32(const __grid_constant__ StepArgs A) {
   __shared__ double s_cos;
+  __shared__ double s_springs[IONTRAP_MAX_SPECIES][3];
   __shared__ int s_last;
   pdl_wait();
   const long long n = A.n;
@@ -349,12 +352,14 @@ __global__ void __launch_bounds__(kEpiThreads) k_epilogue_f32(const __grid_const
   }
   pdl_trigger();
   __syncthreads();  // s_cos
+  if (threadIdx.x < IONTRAP_MAX_SPECIES) trap_springs(A.trap, A.spc[threadIdx.x], s_cos, s_springs[threadIdx.x]);
+  __syncthreads();
   // one lane per ion integrates; the 32 ions are spread over the 8 warps (4 per warp)
   if (sub == 0 && i < n) {
     double S[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) S[c] = (double)cc[c] - (double)s[c];
-    epilogue_ion<false>(A, i, S, s_cos, ns, rb ^ 1);
+    epilogue_ion<false>(A, i, S, s_springs, ns, rb ^ 1);
   }
   __threadfence();
   __syncthreads();
@@ -402,6 +407,7 @@ __global__ void __launch_bounds__(T) k_step_f64(const __grid_constant__ StepArgs
   __shared__ int s_flag;
   __shared__ double s_cos;
   double4_32a* sp = reinterpret_cast<double4_32a*>(smraw);
+  __shared__ double s_springs[IONTRAP_MAX_SPECIES][3];
 
   pdl_wait();
   const int tid = threadIdx.x;
@@ -456,7 +462,8 @@ __global__ void __launch_bounds__(T) k_step_f64(const __grid_constant__ StepArgs
 
   if (tid == 0) s_cos = force_time_cos(A, ns);
   __syncthreads();
-  const double cosv = s_cos;
+  if (tid < IONTRAP_MAX_SPECIES) trap_springs(A.trap, A.spc[tid], s_cos, s_springs[tid]);
+  __syncthreads();
   const int wb = rb ^ 1;
   const int nsplit = gridDim.y;
 #pragma unroll
@@ -465,7 +472,7 @@ __global__ void __launch_bounds__(T) k_step_f64(const __grid_constant__ StepArgs
     if (i >= n) continue;
     double S[3];
     merge_f64(part, n, i, nsplit, S);
-    epilogue_ion<true>(A, i, S, cosv, ns, wb);
+    epilogue_ion<true>(A, i, S, s_springs, ns, wb);
   }
   finish_iblock(A, ns);
 }
