@@ -177,9 +177,13 @@ typedef struct {
     int32_t packed;           /* 1: the FP32 pair arithmetic runs on packed FP32x2 instructions,
                                  two ions per instruction; bitwise identical to 0 */
     int32_t jsplit;           /* j-range per CTA: grid.y = ceil(n / jsplit) */
-    int32_t fused;            /* 1: the last CTA of each i-block merges the split partials and
-                                 integrates; 0: a separate epilogue kernel does, one ion per
-                                 thread over all SMs.  The FP64 form supports 1 only. */
+    int32_t fused;            /* how the split partials are merged and integrated:
+                                 1: by the last CTA of each i-block (arrival counter);
+                                 0: by a separate epilogue kernel over all SMs;
+                                 2: the splits of an i-block form a thread-block cluster
+                                    (at most 8 splits) and merge through distributed shared
+                                    memory, each CTA integrating a slice of the i-block.
+                                 The FP64 form supports 1 only. */
     int32_t pdl;              /* 1: consecutive step kernels use programmatic dependent launch
                                  (default 0: measured slower on GB300 for these grids) */
     int32_t graph;            /* 1: iontrap_step enqueues CUDA graphs of 100 steps; 0: single launches */

@@ -35,7 +35,8 @@ using namespace it;
 
 static constexpr int kGraphSteps = 100;
 static constexpr int kMaxJsplitF64 = 2048;  // FP64 form stages its whole j-range
-static constexpr int64_t kMaxSplitsUnfused = 64;   // records one epilogue lane group folds
+static constexpr int64_t kMaxSplitsUnfused = 64;
+static constexpr int64_t kMaxClusterSplits = 8;  // portable cluster size   // records one epilogue lane group folds
 
 struct iontrap {
   int64_t n = 0;
@@ -330,14 +331,25 @@ cudaError_t launch_step_on(iontrap* h, StepArgs& a, cudaStream_t st) {
   cfg.blockDim = dim3(h->T);
   cfg.dynamicSmemBytes = smem_of(h);
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchAttribute attr[2];
+  int na = 0;
+  if (h->pdl) {
+    attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
+  if (h->fused == 2) {  // the j-splits of an i-block form one cluster
+    attr[na].id = cudaLaunchAttributeClusterDimension;
+    attr[na].val.clusterDim.x = 1;
+    attr[na].val.clusterDim.y = cfg.gridDim.y;
+    attr[na].val.clusterDim.z = 1;
+    ++na;
+  }
   cfg.attrs = attr;
-  cfg.numAttrs = h->pdl ? 1 : 0;
+  cfg.numAttrs = na;
   void* params[] = {&a};
   cudaError_t e = cudaLaunchKernelExC(&cfg, step_kernel(h->f64, h->T, h->I, h->packed, h->fused), params);
-  if (e != cudaSuccess || h->fused) return e;
+  if (e != cudaSuccess || h->fused != 0) return e;
   cfg.gridDim = dim3((unsigned)cdiv(h->n, 32));  // 32 ions per epilogue CTA
   cfg.blockDim = dim3(256);
   cfg.dynamicSmemBytes = 0;
@@ -498,7 +510,8 @@ int iontrap_create(const iontrap_species* species, int n_species, const uint8_t*
     iontrap_config tc{};
     if (tuned_config(n, h->f64, h->device, &tc) && step_kernel(h->f64, tc.threads, tc.ions_per_thread, tc.packed, tc.fused) &&
         tc.jsplit >= 1 && tc.jsplit <= n && (!h->f64 || tc.jsplit <= kMaxJsplitF64) &&
-        (tc.fused || cdiv(n, tc.jsplit) <= kMaxSplitsUnfused)) {
+        (tc.fused || cdiv(n, tc.jsplit) <= kMaxSplitsUnfused) &&
+        (tc.fused != 2 || (cdiv(n, tc.jsplit) <= kMaxClusterSplits && !(p->flags & IONTRAP_COULOMB_OFF)))) {
       h->T = tc.threads, h->I = tc.ions_per_thread, h->packed = tc.packed, h->jsplit = tc.jsplit;
       h->fused = tc.fused, h->pdl = tc.pdl, h->use_graph = tc.graph;
     }
@@ -870,7 +883,7 @@ int iontrap_autotune(iontrap_t* h, double trial_us, iontrap_config* best, double
   if (h->f64) {
     shapes = {{64, 1, 0}, {128, 1, 0}, {128, 2, 0}, {256, 1, 0}};
   } else {
-    const Shape small[] = {{64, 1, 0}, {128, 1, 0}, {64, 2, 1}, {128, 2, 1}};
+    const Shape small[] = {{32, 1, 0}, {64, 1, 0}, {128, 1, 0}, {64, 2, 1}, {128, 2, 1}};
     const Shape large[] = {{64, 4, 1}, {128, 4, 1}, {256, 4, 1}, {128, 2, 1}};
     if (n < 16384) {
       for (const Shape& sh : small)
@@ -882,7 +895,7 @@ int iontrap_autotune(iontrap_t* h, double trial_us, iontrap_config* best, double
   std::vector<iontrap_config> cands;
   for (const Shape& sh : shapes) {
     const int64_t iblocks = cdiv(n, (int64_t)sh.T * sh.I);
-    std::vector<int64_t> splits = {1, 2, 4};
+    std::vector<int64_t> splits = {1, 2, 3, 4, 6, 8};
     for (int w = 1; w <= 16; w *= 2) {
       const int64_t S = cdiv((int64_t)w * h->sms, iblocks);
       splits.push_back(S);
@@ -895,7 +908,8 @@ int iontrap_autotune(iontrap_t* h, double trial_us, iontrap_config* best, double
       if (S < 1 || S > 64 || S > std::max<int64_t>(1, n / 32)) continue;
       int64_t js = cdiv(n, S);
       if (h->f64 && js > kMaxJsplitF64) continue;
-      for (int fused = 1; fused >= (h->f64 ? 1 : 0); --fused) {
+      for (int fused = 2; fused >= (h->f64 ? 1 : 0); --fused) {
+        if (fused == 2 && (h->f64 || cdiv(n, js) > kMaxClusterSplits || (h->p.flags & IONTRAP_COULOMB_OFF))) continue;
         if (!fused && cdiv(n, js) > kMaxSplitsUnfused) continue;
         iontrap_config c{sh.T, sh.I, sh.P, (int32_t)js, fused, 0, 1};
         if (step_kernel(h->f64, c.threads, c.ions_per_thread, c.packed, c.fused)) cands.push_back(c);
@@ -1007,6 +1021,8 @@ int iontrap_set_config(iontrap_t* h, const iontrap_config* c) {
   if (!step_kernel(h->f64, c->threads, c->ions_per_thread, c->packed, c->fused)) return IONTRAP_EINVAL;
   if (c->jsplit < 1 || c->jsplit > h->n || (h->f64 && c->jsplit > kMaxJsplitF64)) return IONTRAP_EINVAL;
   if (!c->fused && cdiv(h->n, c->jsplit) > kMaxSplitsUnfused) return IONTRAP_EINVAL;
+  if (c->fused == 2 && cdiv(h->n, c->jsplit) > kMaxClusterSplits) return IONTRAP_EINVAL;
+  if ((c->fused == 2) && (h->p.flags & IONTRAP_COULOMB_OFF)) return IONTRAP_EINVAL;
   if (h->status) return h->status;
   DeviceGuard g(h->device);
   cudaError_t e = cudaStreamSynchronize(h->stream);

@@ -14,9 +14,13 @@
 // Summation order is a function of (n, T, I, jsplit) only: j ascending inside each
 // 128-wide segment (plain FP32), segments Kahan-added per CTA, CTA partials merged in
 // split order.  The same configuration always gives the same bits.
+#include <cooperative_groups.h>
+
 #include <cstdio>
 
 #include "iontrap_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace it {
 
@@ -137,36 +141,19 @@ __device__ __forceinline__ void merge_f64(const double4_32a* __restrict__ part, 
 // ------------------------------------------------------------------ FP32 form
 constexpr int kChunk = kSeg;  // j-chunk staged per TMA transaction = one Kahan segment
 
-template <int T, int I, bool PACK, bool FUSED>
-__global__ void __launch_bounds__(T) k_step_f32(const __grid_constant__ StepArgs A) {
-  __shared__ __align__(128) float4 sh[2][kChunk];
-  __shared__ __align__(128) float4 sl[2][kChunk];
-  __shared__ __align__(8) uint64_t bar[2];
-  __shared__ int s_flag;
-  __shared__ double s_cos;
-  __shared__ double s_springs[IONTRAP_MAX_SPECIES][3];
-
-  pdl_wait();
+// The pair sum of one CTA: its i-block (T*I ions, I per thread in registers) against
+// its j-range [j0, j1), staged in 128-ion chunks by double-buffered bulk TMA.  Leaves
+// the per-thread Kahan pairs (ks, kc) -- negated sums -- and returns false if a staged
+// chunk never arrived (error flag set, copies drained).
+template <int T, int I, bool PACK>
+__device__ __forceinline__ bool pair_sums(const StepArgs& A, float4 (&sh)[2][kChunk], float4 (&sl)[2][kChunk],
+                                          uint64_t (&bar)[2], const float4* __restrict__ ghi,
+                                          const float4* __restrict__ glo, long long i0, long long j0, long long j1,
+                                          float (&ks)[I][3], float (&kc)[I][3]) {
   const int tid = threadIdx.x;
   const long long n = A.n;
-  const long long i0 = (long long)blockIdx.x * (T * I);
-  const long long j0 = (long long)blockIdx.y * A.jsplit;
-  const long long j1 = min(j0 + (long long)A.jsplit, n);
   const int nch = (int)((j1 - j0 + kChunk - 1) / kChunk);
-  const long long ns = *A.step;
-  const int rb = (A.mode == MODE_STEP) ? (int)((ns + 1) & 1) : (int)(ns & 1);
   const bool coulomb = !(A.trap.flags & IONTRAP_COULOMB_OFF);
-  const float4* __restrict__ ghi = A.hi[rb];
-  const float4* __restrict__ glo = A.lo[rb];
-  const long long tslot = 4ll * (blockIdx.y * (long long)gridDim.x + blockIdx.x);
-  trace_mark(A.trace, tslot + 0);
-
-  float ks[I][3], kc[I][3];
-#pragma unroll
-  for (int k = 0; k < I; ++k)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) ks[k][c] = kc[k][c] = 0.0f;
-
   if (coulomb) {
     auto issue = [&](int c) {
       const long long jc = j0 + (long long)c * kChunk;
@@ -254,7 +241,7 @@ __global__ void __launch_bounds__(T) k_step_f32(const __grid_constant__ StepArgs
             mbar_wait_bounded(&bar[q & 1], (uint32_t)((q >> 1) & 1), kWaitLimitNs);
         }
         __syncthreads();
-        return;
+        return false;
       }
       if (tid == 0 && c + 2 < nch) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -262,6 +249,39 @@ __global__ void __launch_bounds__(T) k_step_f32(const __grid_constant__ StepArgs
       }
     }
   }
+
+  return true;
+}
+
+template <int T, int I, bool PACK, bool FUSED>
+__global__ void __launch_bounds__(T) k_step_f32(const __grid_constant__ StepArgs A) {
+  __shared__ __align__(128) float4 sh[2][kChunk];
+  __shared__ __align__(128) float4 sl[2][kChunk];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int s_flag;
+  __shared__ double s_cos;
+  __shared__ double s_springs[IONTRAP_MAX_SPECIES][3];
+
+  pdl_wait();
+  const int tid = threadIdx.x;
+  const long long n = A.n;
+  const long long i0 = (long long)blockIdx.x * (T * I);
+  const long long j0 = (long long)blockIdx.y * A.jsplit;
+  const long long j1 = min(j0 + (long long)A.jsplit, n);
+  const long long ns = *A.step;
+  const int rb = (A.mode == MODE_STEP) ? (int)((ns + 1) & 1) : (int)(ns & 1);
+  const float4* __restrict__ ghi = A.hi[rb];
+  const float4* __restrict__ glo = A.lo[rb];
+  const long long tslot = 4ll * (blockIdx.y * (long long)gridDim.x + blockIdx.x);
+  trace_mark(A.trace, tslot + 0);
+
+  float ks[I][3], kc[I][3];
+#pragma unroll
+  for (int k = 0; k < I; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ks[k][c] = kc[k][c] = 0.0f;
+
+  if (!pair_sums<T, I, PACK>(A, sh, sl, bar, ghi, glo, i0, j0, j1, ks, kc)) return;
 
   trace_mark(A.trace, tslot + 1);
   pdl_trigger();  // dependents launch as the last CTAs finish their pair loops
@@ -294,6 +314,96 @@ __global__ void __launch_bounds__(T) k_step_f32(const __grid_constant__ StepArgs
   }
   finish_iblock(A, ns);
   trace_mark(A.trace, tslot + 3);
+}
+
+// Cluster form: the S CTAs that sum one i-block over the S j-splits (grid.y = S <= 8)
+// are one thread-block cluster.  Each CTA leaves its (sum, compensation) pairs in its
+// shared memory; after a cluster barrier, CTA r merges ions [r*B/S, (r+1)*B/S) of the
+// i-block (B = T*I) by reading the S partials through distributed shared memory in
+// split order, and integrates them.  No global partials, no arrival counters, and the
+// FP64 epilogue is spread over S SMs.  Same merge order as the other forms: identical
+// bits for an equal (T*I, jsplit).
+template <int T, int I, bool PACK>
+__global__ void __launch_bounds__(T) k_step_f32_cl(const __grid_constant__ StepArgs A) {
+  __shared__ __align__(128) float4 sh[2][kChunk];
+  __shared__ __align__(128) float4 sl[2][kChunk];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(16) float4 s_part[T * I][2];
+  __shared__ double s_cos;
+  __shared__ double s_springs[IONTRAP_MAX_SPECIES][3];
+  cg::cluster_group cluster = cg::this_cluster();
+
+  pdl_wait();
+  const int tid = threadIdx.x;
+  const long long n = A.n;
+  const long long i0 = (long long)blockIdx.x * (T * I);
+  const long long j0 = (long long)blockIdx.y * A.jsplit;
+  const long long j1 = min(j0 + (long long)A.jsplit, n);
+  const long long ns = *A.step;
+  const int rb = (A.mode == MODE_STEP) ? (int)((ns + 1) & 1) : (int)(ns & 1);
+  const long long tslot = 4ll * (blockIdx.y * (long long)gridDim.x + blockIdx.x);
+  trace_mark(A.trace, tslot + 0);
+  if (tid == 0) s_cos = force_time_cos(A, ns);
+
+  float ks[I][3], kc[I][3];
+#pragma unroll
+  for (int k = 0; k < I; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ks[k][c] = kc[k][c] = 0.0f;
+  // on an expired wait the error flag is set and the CTA still meets every cluster
+  // barrier below (the result of this step is then discarded by the caller)
+  pair_sums<T, I, PACK>(A, sh, sl, bar, A.hi[rb], A.lo[rb], i0, j0, j1, ks, kc);
+  trace_mark(A.trace, tslot + 1);
+  pdl_trigger();
+#pragma unroll
+  for (int k = 0; k < I; ++k) {
+    s_part[k * T + tid][0] = make_float4(ks[k][0], ks[k][1], ks[k][2], 0.0f);
+    s_part[k * T + tid][1] = make_float4(kc[k][0], kc[k][1], kc[k][2], 0.0f);
+  }
+  __syncthreads();  // s_cos
+  if (tid < IONTRAP_MAX_SPECIES) trap_springs(A.trap, A.spc[tid], s_cos, s_springs[tid]);
+  cluster.sync();  // every CTA's partials written; springs ready
+  trace_mark(A.trace, tslot + 2);
+
+  const int S = (int)gridDim.y;
+  const int r = (int)cluster.block_rank();
+  constexpr int B = T * I;
+  const int per = (B + S - 1) / S;
+  for (int q = r * per + tid; q < min(B, (r + 1) * per); q += T) {
+    const long long i = i0 + q;
+    if (i >= n) continue;
+    float4 pa[8], pc[8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p)
+      if (p < S) {
+        const float4* rec = cluster.map_shared_rank(&s_part[q][0], (unsigned)p);
+        pa[p] = rec[0];
+        pc[p] = rec[1];
+      }
+    float su[3] = {0.f, 0.f, 0.f}, cu[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int p = 0; p < 8; ++p)
+      if (p < S) {
+        kahan_merge(su[0], cu[0], pa[p].x, pc[p].x);
+        kahan_merge(su[1], cu[1], pa[p].y, pc[p].y);
+        kahan_merge(su[2], cu[2], pa[p].z, pc[p].z);
+      }
+    double Sd[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Sd[c] = (double)cu[c] - (double)su[c];
+    epilogue_ion<false>(A, i, Sd, s_springs, ns, rb ^ 1);
+  }
+  cluster.sync();  // no CTA leaves while another may still read its partials
+  trace_mark(A.trace, tslot + 3);
+  if (r == 0 && tid == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(A.done, 1u);
+    if (prev == gridDim.x - 1u) {
+      *A.done = 0u;
+      if (A.mode == MODE_STEP) *A.step = ns + 1;
+      __threadfence();
+    }
+  }
 }
 
 // Separate epilogue over all SMs.  A CTA of 256 threads serves 32 ions: 8 lanes per ion
@@ -532,8 +642,10 @@ struct KernelEntry {
 };
 
 #define IT_F32(T, I, P) {0, T, I, P, 1, (const void*)k_step_f32<T, I, P, true>}, \
-                        {0, T, I, P, 0, (const void*)k_step_f32<T, I, P, false>}
+                        {0, T, I, P, 0, (const void*)k_step_f32<T, I, P, false>}, \
+                        {0, T, I, P, 2, (const void*)k_step_f32_cl<T, I, P>}
 static const KernelEntry kKernels[] = {
+    IT_F32(32, 1, false),  IT_F32(32, 2, true),
     IT_F32(64, 1, false),  IT_F32(64, 2, false),  IT_F32(64, 2, true),  IT_F32(64, 4, true),
     IT_F32(128, 1, false), IT_F32(128, 2, false), IT_F32(128, 2, true), IT_F32(128, 4, false),
     IT_F32(128, 4, true),  IT_F32(256, 1, false), IT_F32(256, 2, true), IT_F32(256, 4, true),

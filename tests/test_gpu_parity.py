@@ -84,7 +84,8 @@ def test_forces_match_oracle(it, n):
 
 
 @pytest.mark.parametrize("cfg", [(64, 1, 0, 128, 1), (64, 4, 1, 256, 0), (128, 2, 1, 384, 1), (256, 2, 1, 3001, 0),
-                                 (256, 4, 0, 100, 1), (128, 4, 1, 1152, 0), (128, 1, 0, 7, 1), (64, 2, 0, 1000, 0)])
+                                 (256, 4, 0, 100, 1), (128, 4, 1, 1152, 0), (128, 1, 0, 7, 1), (64, 2, 0, 1000, 0),
+                                 (32, 1, 0, 376, 2), (64, 1, 0, 501, 2), (128, 4, 1, 1001, 2), (32, 2, 1, 3001, 2)])
 def test_forces_every_tile_config(it, cfg):
     n = 3001
     w = _cloud(n, 5)
@@ -323,10 +324,11 @@ def test_bitwise_determinism_and_graph_split(it):
 
 def test_packed_and_fused_variants_are_bitwise_equal(it):
     """The packed FP32x2 pair loop rounds lane by lane as the scalar loop does, and the
-    separate epilogue kernel merges the partials exactly as the fused one does."""
+    three merge forms (last CTA, separate epilogue kernel, cluster through distributed
+    shared memory) fold the split partials in the same order."""
     w = _cloud(2100, 12)
     outs = []
-    for packed, fused in ((0, 1), (1, 1), (1, 0), (0, 0)):
+    for packed, fused in ((0, 1), (1, 1), (1, 0), (0, 0), (1, 2), (0, 2)):
         with _sim(it, w, 0) as sim:
             sim.set_config(128, 2, packed, 700, fused)
             f = sim.forces()
