@@ -393,8 +393,8 @@ __global__ void __launch_bounds__(T) k_step_f32_cl(const __grid_constant__ StepA
     for (int c = 0; c < 3; ++c) Sd[c] = (double)cu[c] - (double)su[c];
     epilogue_ion<false>(A, i, Sd, s_springs, ns, rb ^ 1);
   }
-  cluster.sync();  // no CTA leaves while another may still read its partials
   trace_mark(A.trace, tslot + 3);
+  cluster.sync();  // no CTA leaves while another may still read its partials
   if (r == 0 && tid == 0) {
     __threadfence();
     const unsigned prev = atomicAdd(A.done, 1u);
