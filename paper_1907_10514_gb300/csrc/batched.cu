@@ -179,14 +179,15 @@ __global__ void __launch_bounds__(kBThreads)
           vd[c] = half_kick(v[q][c], a[q][c], tp.hdt);
           xf[c] = drift(x[q][c], vd[c], tp.dt);
         }
-        accel_ion<false>(tp, sd, s_springs[le][spi[q]], S[q], xf, vd, ns + 1, ii[q], acc);
+        double ext[3];
+        accel_ext<false>(tp, sd, s_springs[le][spi[q]], xf, vd, ns + 1, ii[q], ext);
+        accel_total(sd, S[q], ext, acc);
+        double vn[3];
+        finite = verlet_finish(tp, xf, vd, acc, vn, xn) && finite;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const double vn = half_kick(vd[c], acc[c], tp.hdt);
-          xn[c] = drift(xf[c], half_kick(vn, acc[c], tp.hdt), tp.dt);
-          finite = finite && isfinite(acc[c]) && isfinite(vn) && isfinite(xn[c]);
           x[q][c] = xf[c];
-          v[q][c] = vn;
+          v[q][c] = vn[c];
           a[q][c] = acc[c];
         }
         float hv[3], lv[3];

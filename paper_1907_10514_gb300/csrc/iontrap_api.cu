@@ -278,8 +278,12 @@ int64_t splits_of(const iontrap* h) {
   return cdiv(h->n, h->jsplit);
 }
 
+// ions per i-block: T*I, except the cluster + warp-split form (fused = 3) whose warps
+// all hold the same 32*I ions
+int64_t iblock_ions(const iontrap* h) { return h->fused == 3 ? 32 * (int64_t)h->I : (int64_t)h->T * h->I; }
+
 dim3 grid_of(const iontrap* h) {
-  return dim3((unsigned)cdiv(h->n, (int64_t)h->T * h->I), (unsigned)splits_of(h), 1);
+  return dim3((unsigned)cdiv(h->n, iblock_ions(h)), (unsigned)splits_of(h), 1);
 }
 
 size_t smem_of(const iontrap* h) {
@@ -299,7 +303,7 @@ int alloc_scratch(iontrap* h) {
   const int64_t splits = splits_of(h);
   // one 32-byte record per (split, ion) in both forms
   const size_t part = (size_t)splits * (size_t)h->n * 32;
-  const size_t cnt = (size_t)cdiv(h->n, (int64_t)h->T * h->I);
+  const size_t cnt = (size_t)cdiv(h->n, iblock_ions(h));
   if (part > h->part_bytes) {
     if (h->d_part) cudaFree(h->d_part);
     h->d_part = nullptr;
@@ -338,7 +342,7 @@ cudaError_t launch_step_on(iontrap* h, StepArgs& a, cudaStream_t st) {
     attr[na].val.programmaticStreamSerializationAllowed = 1;
     ++na;
   }
-  if (h->fused == 2) {  // the j-splits of an i-block form one cluster
+  if (h->fused >= 2) {  // the j-splits of an i-block form one cluster
     attr[na].id = cudaLaunchAttributeClusterDimension;
     attr[na].val.clusterDim.x = 1;
     attr[na].val.clusterDim.y = cfg.gridDim.y;
@@ -511,7 +515,7 @@ int iontrap_create(const iontrap_species* species, int n_species, const uint8_t*
     if (tuned_config(n, h->f64, h->device, &tc) && step_kernel(h->f64, tc.threads, tc.ions_per_thread, tc.packed, tc.fused) &&
         tc.jsplit >= 1 && tc.jsplit <= n && (!h->f64 || tc.jsplit <= kMaxJsplitF64) &&
         (tc.fused || cdiv(n, tc.jsplit) <= kMaxSplitsUnfused) &&
-        (tc.fused != 2 || (cdiv(n, tc.jsplit) <= kMaxClusterSplits && !(p->flags & IONTRAP_COULOMB_OFF)))) {
+        (tc.fused < 2 || (cdiv(n, tc.jsplit) <= kMaxClusterSplits && !(p->flags & IONTRAP_COULOMB_OFF)))) {
       h->T = tc.threads, h->I = tc.ions_per_thread, h->packed = tc.packed, h->jsplit = tc.jsplit;
       h->fused = tc.fused, h->pdl = tc.pdl, h->use_graph = tc.graph;
     }
@@ -855,9 +859,9 @@ int iontrap_estimate_bytes(int64_t n, int precision, int64_t* bytes) {
   default_config(n, f64, sms, &T, &I, &P, &J, &F);
   iontrap_config tc{};
   if (tuned_config(n, f64, dev, &tc) && step_kernel(f64, tc.threads, tc.ions_per_thread, tc.packed, tc.fused)) {
-    T = tc.threads, I = tc.ions_per_thread, J = tc.jsplit;
+    T = tc.threads, I = tc.ions_per_thread, J = tc.jsplit, F = tc.fused;
   }
-  const int64_t splits = cdiv(n, J), iblocks = cdiv(n, (int64_t)T * I);
+  const int64_t splits = cdiv(n, J), iblocks = cdiv(n, (F == 3 ? 32 : (int64_t)T) * I);
   const int64_t vec = 3 * n * (int64_t)sizeof(double);
   const int64_t pair = n * (int64_t)(f64 ? sizeof(double4_32a) : 2 * sizeof(float4));
   *bytes = 3 * vec + n + 2 * pair + splits * n * 32 + iblocks * (int64_t)sizeof(unsigned) + 64;
@@ -915,6 +919,15 @@ int iontrap_autotune(iontrap_t* h, double trial_us, iontrap_config* best, double
         if (step_kernel(h->f64, c.threads, c.ions_per_thread, c.packed, c.fused)) cands.push_back(c);
       }
     }
+  }
+  if (!h->f64 && !(h->p.flags & IONTRAP_COULOMB_OFF)) {  // cluster + warp-split shapes
+    const int cw[][2] = {{1, 2}, {1, 4}, {2, 2}, {2, 4}};
+    for (const auto& iw : cw)
+      for (int64_t S = 2; S <= kMaxClusterSplits; S *= 2) {
+        if (S > std::max<int64_t>(1, n / 128)) continue;
+        iontrap_config c{32 * iw[1], iw[0], iw[0] == 2 ? 1 : 0, (int32_t)cdiv(n, S), 3, 0, 1};
+        if (step_kernel(0, c.threads, c.ions_per_thread, c.packed, 3)) cands.push_back(c);
+      }
   }
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return IONTRAP_ECUDA;
@@ -1021,8 +1034,8 @@ int iontrap_set_config(iontrap_t* h, const iontrap_config* c) {
   if (!step_kernel(h->f64, c->threads, c->ions_per_thread, c->packed, c->fused)) return IONTRAP_EINVAL;
   if (c->jsplit < 1 || c->jsplit > h->n || (h->f64 && c->jsplit > kMaxJsplitF64)) return IONTRAP_EINVAL;
   if (!c->fused && cdiv(h->n, c->jsplit) > kMaxSplitsUnfused) return IONTRAP_EINVAL;
-  if (c->fused == 2 && cdiv(h->n, c->jsplit) > kMaxClusterSplits) return IONTRAP_EINVAL;
-  if ((c->fused == 2) && (h->p.flags & IONTRAP_COULOMB_OFF)) return IONTRAP_EINVAL;
+  if (c->fused >= 2 && cdiv(h->n, c->jsplit) > kMaxClusterSplits) return IONTRAP_EINVAL;
+  if ((c->fused >= 2) && (h->p.flags & IONTRAP_COULOMB_OFF)) return IONTRAP_EINVAL;
   if (h->status) return h->status;
   DeviceGuard g(h->device);
   cudaError_t e = cudaStreamSynchronize(h->stream);

@@ -316,22 +316,21 @@ __device__ __forceinline__ void trap_springs(const TrapDev& tp, const SpeciesDev
   k[2] = rwz2;
 }
 
-// Acceleration of one ion at force time (FP64 in both forms): Coulomb sum S
-// (sum_j z_j d/r^3) -> k_e e^2 z/M S - k xf (springs of the ion's species) - gamma vd +
-// sigma xi(seed, counter, id).  Explicit roundings (no FMA contraction left to the
-// compiler): every kernel that inlines this produces the same bits.  The trajectories
-// of these clouds amplify FP32-sized perturbations of the RF trap term by ~1e4 within
-// 100 steps, so no term is evaluated in FP32.  F64 selects FP64 Box-Muller noise.
+// Acceleration of one ion at force time, FP64 in both forms, split in two so that the
+// part that does not depend on the Coulomb sum can be evaluated before the sum is known:
+//   ext = -k xf - gamma vd + sigma xi(seed, counter, id)   (accel_ext)
+//   acc = k_e e^2 z/M S + ext                             (accel_total)
+// with k the spring constants of the ion's species and S = sum_j z_j d/r^3.  Explicit
+// roundings (no FMA contraction left to the compiler): every kernel produces the same
+// bits.  The trajectories of these clouds amplify FP32-sized perturbations of the RF trap
+// term by ~1e4 within 100 steps, so no term is evaluated in FP32.  F64 selects FP64
+// Box-Muller noise.
 template <bool F64>
-__device__ __forceinline__ void accel_ion(const TrapDev& tp, const SpeciesDev& sd, const double k[3],
-                                          const double S[3], const double xf[3], const double vd[3],
-                                          long long counter, long long id, double acc[3]) {
+__device__ __forceinline__ void accel_ext(const TrapDev& tp, const SpeciesDev& sd, const double k[3],
+                                          const double xf[3], const double vd[3], long long counter, long long id,
+                                          double ext[3]) {
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    acc[c] = __dmul_rn(sd.coul, S[c]);
-    acc[c] = __fma_rn(-k[c], xf[c], acc[c]);
-    acc[c] = __fma_rn(-tp.gamma, vd[c], acc[c]);
-  }
+  for (int c = 0; c < 3; ++c) ext[c] = __fma_rn(-tp.gamma, vd[c], __dmul_rn(-k[c], xf[c]));
   if (sd.sigma > 0.0) {
     double z[3];
     if constexpr (F64) {
@@ -342,8 +341,28 @@ __device__ __forceinline__ void accel_ion(const TrapDev& tp, const SpeciesDev& s
       z[0] = zf[0], z[1] = zf[1], z[2] = zf[2];
     }
 #pragma unroll
-    for (int c = 0; c < 3; ++c) acc[c] = __fma_rn(sd.sigma, z[c], acc[c]);
+    for (int c = 0; c < 3; ++c) ext[c] = __fma_rn(sd.sigma, z[c], ext[c]);
   }
+}
+
+__device__ __forceinline__ void accel_total(const SpeciesDev& sd, const double S[3], const double ext[3],
+                                            double acc[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) acc[c] = __fma_rn(sd.coul, S[c], ext[c]);
+}
+
+// The rest of the step once the acceleration is known: v_{n+1}, the next positions and
+// their pair-stream entry, the stores and the finiteness check.
+__device__ __forceinline__ bool verlet_finish(const TrapDev& tp, const double xf[3], const double vd[3],
+                                              const double acc[3], double vn[3], double xn[3]) {
+  bool finite = true;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    vn[c] = half_kick(vd[c], acc[c], tp.hdt);
+    xn[c] = drift(xf[c], half_kick(vn[c], acc[c], tp.hdt), tp.dt);
+    finite = finite && isfinite(acc[c]) && isfinite(vn[c]) && isfinite(xn[c]);
+  }
+  return finite;
 }
 
 // Fused epilogue for ion i: Coulomb sum S -> acceleration -> Verlet update -> next
@@ -371,8 +390,9 @@ __device__ __forceinline__ void epilogue_ion(const StepArgs& A, long long i, con
     vd[c] = step ? vh : v;
     xf[c] = step ? drift(x, vh, tp.dt) : x;
   }
-  double acc[3];
-  accel_ion<F64>(tp, sd, springs[spi], S, xf, vd, step ? ns + 1 : ns, i, acc);
+  double ext[3], acc[3];
+  accel_ext<F64>(tp, sd, springs[spi], xf, vd, step ? ns + 1 : ns, i, ext);
+  accel_total(sd, S, ext, acc);
   double vn[3], xn[3];
   bool finite = true;
 #pragma unroll

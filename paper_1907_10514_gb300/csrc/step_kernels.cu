@@ -406,6 +406,252 @@ __global__ void __launch_bounds__(T) k_step_f32_cl(const __grid_constant__ StepA
   }
 }
 
+// Cluster + warp-split form (fused = 3): the i-block is 32*I ions (I per lane, the same
+// ions in every warp); the W warps of a CTA sum interleaved 128-ion chunks of the CTA's
+// j-range (warp w takes chunks w, w+W, ...; one bulk TMA per round stages W consecutive
+// chunks, double-buffered), their partials are folded in warp order, and the S CTAs of
+// an i-block (a cluster, S <= 8) are folded in split order through distributed shared
+// memory.  The part of each ion's epilogue that does not depend on the Coulomb sum
+// (kick, drift, trap, drag, noise) is evaluated before the pair loop, so after the
+// final fold only the last few FP64 operations remain.
+template <int I, int W, bool PACK>
+__global__ void __launch_bounds__(32 * W) k_step_f32_cw(const __grid_constant__ StepArgs A) {
+  constexpr int T = 32 * W;
+  constexpr int B = 32 * I;
+  static_assert(W * kChunk * 64 + W * B * 32 + B * 32 <= 47 * 1024, "static shared memory above the 48 KB limit");
+  __shared__ __align__(128) float4 sh[2][W * kChunk];
+  __shared__ __align__(128) float4 sl[2][W * kChunk];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(16) float4 s_wp[W][B][2];
+  __shared__ __align__(16) float4 s_part[B][2];
+  __shared__ double s_cos;
+  __shared__ double s_springs[IONTRAP_MAX_SPECIES][3];
+  cg::cluster_group cluster = cg::this_cluster();
+
+  pdl_wait();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const long long n = A.n;
+  const long long i0 = (long long)blockIdx.x * B;
+  const long long j0 = (long long)blockIdx.y * A.jsplit;
+  const long long j1 = min(j0 + (long long)A.jsplit, n);
+  const long long ns = *A.step;
+  const int rb = (A.mode == MODE_STEP) ? (int)((ns + 1) & 1) : (int)(ns & 1);
+  const float4* __restrict__ ghi = A.hi[rb];
+  const float4* __restrict__ glo = A.lo[rb];
+  const long long tslot = 4ll * (blockIdx.y * (long long)gridDim.x + blockIdx.x);
+  trace_mark(A.trace, tslot + 0);
+  const int nch = (int)((j1 - j0 + kChunk - 1) / kChunk);
+  const int nr = (nch + W - 1) / W;
+  auto issue = [&](int k) {  // round k: chunks kW .. kW+W-1, consecutive in j
+    const long long jc = j0 + (long long)k * W * kChunk;
+    const uint32_t bytes = (uint32_t)min((long long)W * kChunk, j1 - jc) * 16u;
+    const int b = k & 1;
+    mbar_arrive_expect_tx(&bar[b], 2u * bytes);
+    tma_bulk_g2s(sh[b], ghi + jc, bytes, &bar[b]);
+    tma_bulk_g2s(sl[b], glo + jc, bytes, &bar[b]);
+  };
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    s_cos = force_time_cos(A, ns);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (nr > 0) issue(0);
+    if (nr > 1) issue(1);
+  }
+  if (tid < IONTRAP_MAX_SPECIES) trap_springs(A.trap, A.spc[tid], s_cos, s_springs[tid]);
+  __syncthreads();
+
+  // this thread's epilogue ion (CTA r of the cluster integrates a slice of the i-block)
+  const int S = (int)gridDim.y;
+  const int r = (int)cluster.block_rank();
+  const int per = (B + S - 1) / S;
+  const int q = r * per + tid;
+  const long long ie = i0 + q;
+  const bool own = tid < per && q < B && ie < n;
+  const bool step = (A.mode == MODE_STEP), forces = (A.mode == MODE_FORCES);
+  double xf[3], vd[3], v0[3], ext[3];
+  int spe = 0;
+  if (own && !forces) {
+    spe = A.sp[ie];
+    const TrapDev& tp = A.trap;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double x = A.x[c * n + ie], v = A.v[c * n + ie], a = A.a[c * n + ie];
+      const double vh = half_kick(v, a, tp.hdt);
+      v0[c] = v;
+      vd[c] = step ? vh : v;
+      xf[c] = step ? drift(x, vh, tp.dt) : x;
+    }
+    accel_ext<false>(tp, A.spc[spe], s_springs[spe], xf, vd, step ? ns + 1 : ns, ie, ext);
+  }
+
+  // pair sums of this warp's chunks
+  long long ii[I];
+  float nxh[I][3], nxl[I][3], ks[I][3], kc[I][3];
+#pragma unroll
+  for (int k = 0; k < I; ++k) {
+    ii[k] = i0 + k * 32 + lane;
+    float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
+    if (ii[k] < n) {
+      h = ghi[ii[k]];
+      l = glo[ii[k]];
+    }
+    nxh[k][0] = -h.x, nxh[k][1] = -h.y, nxh[k][2] = -h.z;
+    nxl[k][0] = -l.x, nxl[k][1] = -l.y, nxl[k][2] = -l.z;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ks[k][c] = kc[k][c] = 0.0f;
+  }
+  const long long iend = i0 + B;
+  const bool coulomb = !(A.trap.flags & IONTRAP_COULOMB_OFF);
+  for (int k = 0; coulomb && k < nr; ++k) {
+    const int b = k & 1;
+    const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)((k >> 1) & 1), kWaitLimitNs);
+    const int c = k * W + warp;
+    if (c < nch) {
+      const long long jc = j0 + (long long)c * kChunk;
+      const int jn = (int)min((long long)kChunk, j1 - jc);
+      const bool diag = (jc < iend) && (i0 < jc + jn);
+      const float4* csh = sh[b] + warp * kChunk;
+      const float4* csl = sl[b] + warp * kChunk;
+      float acc[I][3];
+      if constexpr (PACK) {
+        float2 nxh2[I / 2][3], nxl2[I / 2][3], acc2[I / 2][3];
+#pragma unroll
+        for (int k2 = 0; k2 < I / 2; ++k2)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            nxh2[k2][d] = make_float2(nxh[2 * k2][d], nxh[2 * k2 + 1][d]);
+            nxl2[k2][d] = make_float2(nxl[2 * k2][d], nxl[2 * k2 + 1][d]);
+            acc2[k2][d] = make_float2(0.0f, 0.0f);
+          }
+        if (diag)
+          segment_f32x2<I, true>(csh, csl, jn, jc, nxh2, nxl2, ii, acc2);
+        else
+          segment_f32x2<I, false>(csh, csl, jn, jc, nxh2, nxl2, ii, acc2);
+#pragma unroll
+        for (int k2 = 0; k2 < I / 2; ++k2)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            acc[2 * k2][d] = acc2[k2][d].x;
+            acc[2 * k2 + 1][d] = acc2[k2][d].y;
+          }
+      } else {
+#pragma unroll
+        for (int k2 = 0; k2 < I; ++k2)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) acc[k2][d] = 0.0f;
+        if (diag)
+          segment_f32<I, true>(csh, csl, jn, jc, nxh, nxl, ii, acc);
+        else
+          segment_f32<I, false>(csh, csl, jn, jc, nxh, nxl, ii, acc);
+      }
+#pragma unroll
+      for (int k2 = 0; k2 < I; ++k2)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const float y = acc[k2][d] - kc[k2][d];
+          const float t = ks[k2][d] + y;
+          kc[k2][d] = (t - ks[k2][d]) - y;
+          ks[k2][d] = t;
+        }
+    }
+    if (__syncthreads_or(!ok)) {  // a staged round never arrived: drain, flag, and still meet the cluster
+      if (tid == 0) {
+        atomicOr(A.err, ERR_TIMEOUT);
+        for (int kk = k; kk < min(k + 2, nr); ++kk)
+          mbar_wait_bounded(&bar[kk & 1], (uint32_t)((kk >> 1) & 1), kWaitLimitNs);
+      }
+      __syncthreads();
+      break;
+    }
+    if (tid == 0 && k + 2 < nr) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(k + 2);
+    }
+  }
+  trace_mark(A.trace, tslot + 1);
+  pdl_trigger();
+  // fold the warps' partials in warp order
+#pragma unroll
+  for (int k = 0; k < I; ++k) {
+    s_wp[warp][k * 32 + lane][0] = make_float4(ks[k][0], ks[k][1], ks[k][2], 0.0f);
+    s_wp[warp][k * 32 + lane][1] = make_float4(kc[k][0], kc[k][1], kc[k][2], 0.0f);
+  }
+  __syncthreads();
+  for (int qq = tid; qq < B; qq += T) {
+    float su[3] = {0.f, 0.f, 0.f}, cu[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      const float4 pa = s_wp[w][qq][0], pc = s_wp[w][qq][1];
+      kahan_merge(su[0], cu[0], pa.x, pc.x);
+      kahan_merge(su[1], cu[1], pa.y, pc.y);
+      kahan_merge(su[2], cu[2], pa.z, pc.z);
+    }
+    s_part[qq][0] = make_float4(su[0], su[1], su[2], 0.0f);
+    s_part[qq][1] = make_float4(cu[0], cu[1], cu[2], 0.0f);
+  }
+  cluster.sync();  // every CTA's partials are folded and visible
+  trace_mark(A.trace, tslot + 2);
+  if (own) {
+    float4 pa[8], pc[8];
+#pragma unroll
+    for (int p = 0; p < 8; ++p)
+      if (p < S) {
+        const float4* rec = cluster.map_shared_rank(&s_part[q][0], (unsigned)p);
+        pa[p] = rec[0];
+        pc[p] = rec[1];
+      }
+    float su[3] = {0.f, 0.f, 0.f}, cu[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int p = 0; p < 8; ++p)
+      if (p < S) {
+        kahan_merge(su[0], cu[0], pa[p].x, pc[p].x);
+        kahan_merge(su[1], cu[1], pa[p].y, pc[p].y);
+        kahan_merge(su[2], cu[2], pa[p].z, pc[p].z);
+      }
+    double Sd[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Sd[c] = (double)cu[c] - (double)su[c];
+    if (forces) {
+      const SpeciesDev& sd = A.spc[A.sp[ie]];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) A.out[c * n + ie] = sd.coul * Sd[c];
+    } else {
+      const SpeciesDev& sd = A.spc[spe];
+      const TrapDev& tp = A.trap;
+      double acc[3], vn[3], xn[3];
+      accel_total(sd, Sd, ext, acc);
+      bool finite = true;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        vn[c] = step ? half_kick(vd[c], acc[c], tp.hdt) : v0[c];
+        xn[c] = drift(xf[c], half_kick(vn[c], acc[c], tp.hdt), tp.dt);
+        finite = finite && isfinite(acc[c]) && isfinite(vn[c]) && isfinite(xn[c]);
+        if (step) {
+          A.x[c * n + ie] = xf[c];
+          A.v[c * n + ie] = vn[c];
+        }
+        A.a[c * n + ie] = acc[c];
+      }
+      write_pair<false>(A, rb ^ 1, ie, xn, sd.w);
+      if (!finite) atomicOr(A.err, ERR_NONFINITE);
+    }
+  }
+  trace_mark(A.trace, tslot + 3);
+  cluster.sync();  // no CTA leaves while another may still read its partials
+  if (r == 0 && tid == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(A.done, 1u);
+    if (prev == gridDim.x - 1u) {
+      *A.done = 0u;
+      if (A.mode == MODE_STEP) *A.step = ns + 1;
+      __threadfence();
+    }
+  }
+}
+
 // Separate epilogue over all SMs.  A CTA of 256 threads serves 32 ions: 8 lanes per ion
 // fetch the ion's split records together (one memory round trip instead of one per
 // split), fold them in split order through warp shuffles, and leave the merged sum in
@@ -644,7 +890,9 @@ struct KernelEntry {
 #define IT_F32(T, I, P) {0, T, I, P, 1, (const void*)k_step_f32<T, I, P, true>}, \
                         {0, T, I, P, 0, (const void*)k_step_f32<T, I, P, false>}, \
                         {0, T, I, P, 2, (const void*)k_step_f32_cl<T, I, P>}
+#define IT_CW(I, W, P) {0, 32 * W, I, P, 3, (const void*)k_step_f32_cw<I, W, P>}
 static const KernelEntry kKernels[] = {
+    IT_CW(1, 2, false), IT_CW(1, 4, false), IT_CW(2, 2, true), IT_CW(2, 4, true),
     IT_F32(32, 1, false),  IT_F32(32, 2, true),
     IT_F32(64, 1, false),  IT_F32(64, 2, false),  IT_F32(64, 2, true),  IT_F32(64, 4, true),
     IT_F32(128, 1, false), IT_F32(128, 2, false), IT_F32(128, 2, true), IT_F32(128, 4, false),
@@ -654,6 +902,7 @@ static const KernelEntry kKernels[] = {
     {1, 128, 2, 0, 1, (const void*)k_step_f64<128, 2>}, {1, 256, 1, 0, 1, (const void*)k_step_f64<256, 1>},
 };
 #undef IT_F32
+#undef IT_CW
 
 const void* step_kernel(int f64, int T, int I, int packed, int fused) {
   for (const auto& e : kKernels)

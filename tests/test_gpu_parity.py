@@ -85,7 +85,8 @@ def test_forces_match_oracle(it, n):
 
 @pytest.mark.parametrize("cfg", [(64, 1, 0, 128, 1), (64, 4, 1, 256, 0), (128, 2, 1, 384, 1), (256, 2, 1, 3001, 0),
                                  (256, 4, 0, 100, 1), (128, 4, 1, 1152, 0), (128, 1, 0, 7, 1), (64, 2, 0, 1000, 0),
-                                 (32, 1, 0, 376, 2), (64, 1, 0, 501, 2), (128, 4, 1, 1001, 2), (32, 2, 1, 3001, 2)])
+                                 (32, 1, 0, 376, 2), (64, 1, 0, 501, 2), (128, 4, 1, 1001, 2), (32, 2, 1, 3001, 2),
+                                 (64, 1, 0, 501, 3), (128, 2, 1, 1001, 3), (128, 1, 0, 376, 3), (64, 2, 1, 3001, 3)])
 def test_forces_every_tile_config(it, cfg):
     n = 3001
     w = _cloud(n, 5)
@@ -374,6 +375,22 @@ def test_batched_alone_equals_mixed_bitwise(it):
     for (xa, va, sa, _), (xm, vm, sm, _), k in zip(alone, mixed, steps):
         assert sa == sm == k
         assert np.array_equal(xa, xm) and np.array_equal(va, vm)
+
+
+@pytest.mark.parametrize("cfg", [(64, 1, 0, 3), (128, 2, 1, 3), (128, 1, 0, 2), (64, 2, 1, 1)])
+def test_cluster_forms_trajectory_matches_oracle(it, cfg):
+    """The cluster forms (and the last-CTA form) over 100 steps on a 3000-ion cloud,
+    including the epilogue evaluated ahead of the pair loop in form 3."""
+    T, I, P, F = cfg
+    n = 3000
+    w = _cloud(n, 401)
+    q, m, p = _oracle_side(w)
+    xo, vo, _ = oracle.run(w.x0, w.v0, q, m, p, 100)
+    with _sim(it, w, 0) as sim:
+        sim.set_config(T, I, P, -(-n // 8), F)
+        sim.step(100)
+        x, v, step, _ = sim.state()
+    assert step == 100 and rel_rms(x, xo) < FP32_TRAJ_TOL and rel_rms(v, vo) < 10 * FP32_TRAJ_TOL
 
 
 def test_batched_then_single_continue_consistently(it):
