@@ -181,7 +181,7 @@ typedef struct {
                                  1: by the last CTA of each i-block (arrival counter);
                                  0: by a separate epilogue kernel over all SMs;
                                  2: the splits of an i-block form a thread-block cluster
-                                    (at most 8 splits) and merge through distributed shared
+                                    (at most 8 splits; 16 in form 3) and merge through distributed shared
                                     memory, each CTA integrating a slice of the i-block;
                                  3: as 2, with an i-block of 32*ions_per_thread ions held by
                                     every warp of the CTA (threads = 32 W) and the W warps
@@ -195,7 +195,7 @@ typedef struct {
 /* iontrap_get_config reads a handle's configuration; iontrap_set_config changes it (the
  * autotuner's knob).  EINVAL for a combination without a compiled kernel, jsplit < 1 or
  * > n, jsplit > 2048 in the FP64 form, more than 64 splits when not fused, or more than
- * 8 splits in the cluster forms.  Results depend only on n, the i-block (threads *
+ * 8 (form 2) or 16 (form 3, a non-portable cluster size) splits in the cluster forms.  Results depend only on n, the i-block (threads *
  * ions_per_thread; 32 * ions_per_thread and the warp count in form 3), jsplit and the
  * parameters: forms 0, 1 and 2 with equal values give bitwise equal trajectories. */
 int iontrap_get_config(const iontrap_t *h, iontrap_config *cfg);

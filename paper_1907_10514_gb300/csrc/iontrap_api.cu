@@ -25,6 +25,7 @@ cudaError_t launch_batched(const std::vector<BatchEns>& ens, const std::vector<l
                            cudaStream_t stream);
 const void* step_kernel(int f64, int T, int I, int packed, int fused);
 const void* epilogue_kernel(int f64);
+cudaError_t allow_large_clusters();
 const void* prep_kernel();
 const void* restore_kernel();
 cudaError_t launch_normals(unsigned long long seed, long long counter, const long long* d_ids, long long m,
@@ -36,7 +37,8 @@ using namespace it;
 static constexpr int kGraphSteps = 100;
 static constexpr int kMaxJsplitF64 = 2048;  // FP64 form stages its whole j-range
 static constexpr int64_t kMaxSplitsUnfused = 64;
-static constexpr int64_t kMaxClusterSplits = 8;  // portable cluster size   // records one epilogue lane group folds
+static constexpr int64_t kMaxClusterSplits = 8;   // portable cluster size (form 2)
+static constexpr int64_t kMaxClusterSplits3 = 16; // non-portable cluster size (form 3)   // records one epilogue lane group folds
 
 struct iontrap {
   int64_t n = 0;
@@ -419,6 +421,7 @@ int prepare_kernels() {
                     cudaSuccess)
         return IONTRAP_ECUDA;
     }
+  if (allow_large_clusters() != cudaSuccess) return IONTRAP_ECUDA;
   done = 1;
   return IONTRAP_OK;
 }
@@ -515,7 +518,8 @@ int iontrap_create(const iontrap_species* species, int n_species, const uint8_t*
     if (tuned_config(n, h->f64, h->device, &tc) && step_kernel(h->f64, tc.threads, tc.ions_per_thread, tc.packed, tc.fused) &&
         tc.jsplit >= 1 && tc.jsplit <= n && (!h->f64 || tc.jsplit <= kMaxJsplitF64) &&
         (tc.fused || cdiv(n, tc.jsplit) <= kMaxSplitsUnfused) &&
-        (tc.fused < 2 || (cdiv(n, tc.jsplit) <= kMaxClusterSplits && !(p->flags & IONTRAP_COULOMB_OFF)))) {
+        (tc.fused < 2 || (cdiv(n, tc.jsplit) <= (tc.fused == 3 ? kMaxClusterSplits3 : kMaxClusterSplits) &&
+                          !(p->flags & IONTRAP_COULOMB_OFF)))) {
       h->T = tc.threads, h->I = tc.ions_per_thread, h->packed = tc.packed, h->jsplit = tc.jsplit;
       h->fused = tc.fused, h->pdl = tc.pdl, h->use_graph = tc.graph;
     }
@@ -923,7 +927,7 @@ int iontrap_autotune(iontrap_t* h, double trial_us, iontrap_config* best, double
   if (!h->f64 && !(h->p.flags & IONTRAP_COULOMB_OFF)) {  // cluster + warp-split shapes
     const int cw[][2] = {{1, 2}, {1, 4}, {2, 2}, {2, 4}};
     for (const auto& iw : cw)
-      for (int64_t S = 2; S <= kMaxClusterSplits; S *= 2) {
+      for (int64_t S = 2; S <= kMaxClusterSplits3; S *= 2) {
         if (S > std::max<int64_t>(1, n / 128)) continue;
         iontrap_config c{32 * iw[1], iw[0], iw[0] == 2 ? 1 : 0, (int32_t)cdiv(n, S), 3, 0, 1};
         if (step_kernel(0, c.threads, c.ions_per_thread, c.packed, 3)) cands.push_back(c);
@@ -1034,7 +1038,8 @@ int iontrap_set_config(iontrap_t* h, const iontrap_config* c) {
   if (!step_kernel(h->f64, c->threads, c->ions_per_thread, c->packed, c->fused)) return IONTRAP_EINVAL;
   if (c->jsplit < 1 || c->jsplit > h->n || (h->f64 && c->jsplit > kMaxJsplitF64)) return IONTRAP_EINVAL;
   if (!c->fused && cdiv(h->n, c->jsplit) > kMaxSplitsUnfused) return IONTRAP_EINVAL;
-  if (c->fused >= 2 && cdiv(h->n, c->jsplit) > kMaxClusterSplits) return IONTRAP_EINVAL;
+  if (c->fused == 2 && cdiv(h->n, c->jsplit) > kMaxClusterSplits) return IONTRAP_EINVAL;
+  if (c->fused == 3 && cdiv(h->n, c->jsplit) > kMaxClusterSplits3) return IONTRAP_EINVAL;
   if ((c->fused >= 2) && (h->p.flags & IONTRAP_COULOMB_OFF)) return IONTRAP_EINVAL;
   if (h->status) return h->status;
   DeviceGuard g(h->device);

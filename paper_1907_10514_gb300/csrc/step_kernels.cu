@@ -595,22 +595,26 @@ __global__ void __launch_bounds__(32 * W) k_step_f32_cw(const __grid_constant__ 
   cluster.sync();  // every CTA's partials are folded and visible
   trace_mark(A.trace, tslot + 2);
   if (own) {
-    float4 pa[8], pc[8];
-#pragma unroll
-    for (int p = 0; p < 8; ++p)
-      if (p < S) {
-        const float4* rec = cluster.map_shared_rank(&s_part[q][0], (unsigned)p);
-        pa[p] = rec[0];
-        pc[p] = rec[1];
-      }
     float su[3] = {0.f, 0.f, 0.f}, cu[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-    for (int p = 0; p < 8; ++p)
-      if (p < S) {
-        kahan_merge(su[0], cu[0], pa[p].x, pc[p].x);
-        kahan_merge(su[1], cu[1], pa[p].y, pc[p].y);
-        kahan_merge(su[2], cu[2], pa[p].z, pc[p].z);
-      }
+    for (int p0 = 0; p0 < 16; p0 += 8) {
+      if (p0 >= S) break;
+      float4 pa[8], pc[8];
+#pragma unroll
+      for (int p = 0; p < 8; ++p)
+        if (p0 + p < S) {
+          const float4* rec = cluster.map_shared_rank(&s_part[q][0], (unsigned)(p0 + p));
+          pa[p] = rec[0];
+          pc[p] = rec[1];
+        }
+#pragma unroll
+      for (int p = 0; p < 8; ++p)
+        if (p0 + p < S) {
+          kahan_merge(su[0], cu[0], pa[p].x, pc[p].x);
+          kahan_merge(su[1], cu[1], pa[p].y, pc[p].y);
+          kahan_merge(su[2], cu[2], pa[p].z, pc[p].z);
+        }
+    }
     double Sd[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) Sd[c] = (double)cu[c] - (double)su[c];
@@ -908,6 +912,16 @@ const void* step_kernel(int f64, int T, int I, int packed, int fused) {
   for (const auto& e : kKernels)
     if (e.f64 == f64 && e.T == T && e.I == I && e.packed == packed && e.fused == fused) return e.fn;
   return nullptr;
+}
+
+// Form 3 kernels may be launched in clusters of up to 16 CTAs (non-portable size).
+cudaError_t allow_large_clusters() {
+  for (const auto& e : kKernels)
+    if (e.fused == 3) {
+      cudaError_t err = cudaFuncSetAttribute(e.fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (err != cudaSuccess) return err;
+    }
+  return cudaSuccess;
 }
 
 const void* epilogue_kernel(int f64) { return f64 ? nullptr : (const void*)k_epilogue_f32; }
