@@ -440,7 +440,8 @@ __global__ void __launch_bounds__(32 * W) k_step_f32_cw(const __grid_constant__ 
   const float4* __restrict__ glo = A.lo[rb];
   const long long tslot = 4ll * (blockIdx.y * (long long)gridDim.x + blockIdx.x);
   trace_mark(A.trace, tslot + 0);
-  const int nch = (int)((j1 - j0 + kChunk - 1) / kChunk);
+  const bool coulomb = !(A.trap.flags & IONTRAP_COULOMB_OFF);
+  const int nch = coulomb ? (int)((j1 - j0 + kChunk - 1) / kChunk) : 0;  // nothing staged without the pair term
   const int nr = (nch + W - 1) / W;
   auto issue = [&](int k) {  // round k: chunks kW .. kW+W-1, consecutive in j
     const long long jc = j0 + (long long)k * W * kChunk;
@@ -504,8 +505,7 @@ __global__ void __launch_bounds__(32 * W) k_step_f32_cw(const __grid_constant__ 
     for (int c = 0; c < 3; ++c) ks[k][c] = kc[k][c] = 0.0f;
   }
   const long long iend = i0 + B;
-  const bool coulomb = !(A.trap.flags & IONTRAP_COULOMB_OFF);
-  for (int k = 0; coulomb && k < nr; ++k) {
+  for (int k = 0; k < nr; ++k) {
     const int b = k & 1;
     const bool ok = mbar_wait_bounded(&bar[b], (uint32_t)((k >> 1) & 1), kWaitLimitNs);
     const int c = k * W + warp;
