@@ -49,6 +49,12 @@ def _dist():
     return ws, rank
 
 
+def shard(items, rank: int, world: int):
+    """The units (ensembles, requests) a rank advances: every world-th one from its
+    rank -- independent problems, no collective on the data path."""
+    return list(items)[rank::world]
+
+
 def _barrier(ws):
     if ws > 1:
         import torch.distributed as dist
