@@ -41,6 +41,9 @@ FP32_OPS_PER_PAIR = 18
 FP32_LANES_PER_SM = 128
 MUFU_PER_SM = 16
 NOMINAL_SM_MHZ = 2070.0
+# DRAM bytes (read + write) per launch of the step kernel, from the ncu capture summarised
+# in profiles/step_f32_cw_mix_n4096.md; valid only for that launch configuration.
+PROFILED_TRAFFIC = {(128, 2, 1, 512, 3): 477696 + 0}
 
 
 def _dist():
@@ -292,7 +295,9 @@ def run_gpu(args):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps * nsteps,
         "roofline": {"bound": "alu", "achieved": achieved_gpairs, "peak": peak_gpairs,
-                     "unit": "Gpair/s", "frac": achieved_gpairs / peak_gpairs, "traffic": None,
+                     "unit": "Gpair/s", "frac": achieved_gpairs / peak_gpairs,
+                     "traffic": PROFILED_TRAFFIC.get(tuple(cfg[:5])),
+                     "traffic_unit": "DRAM bytes per launch (ncu, profiles/step_f32_cw_mix_n4096.md)",
                      "basis": f"{sms} SMs x {NOMINAL_SM_MHZ:.0f} MHz x {FP32_LANES_PER_SM} FP32 lanes / "
                               f"{FP32_OPS_PER_PAIR} FP32 instr per ordered pair (MUFU roof "
                               f"{MUFU_PER_SM}/clk/SM not binding); achieved = N(N-1) per launch / "
