@@ -226,6 +226,7 @@ def run_gpu(args):
         torch.cuda.nvtx.range_pop()
         _barrier(ws)
     sim.sync()
+    force_err = sampled_force_error(it, sim, w) if rank == 0 else None
     ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = _max_over_ranks(ws, sum(ms))
     ms_per_step = total_ms / args.steps
@@ -291,6 +292,9 @@ def run_gpu(args):
                    "tile_fields": "threads, ions_per_thread, packed, jsplit, fused, pdl, graph (autotuned)",
                    "l2": "flushed (256 MB write) between timed steps; state is L2-resident within a step"},
         "pair_interactions_per_s": value * (n - 1),
+        "force_rel_rms_vs_oracle": force_err,
+        "error_note": "GPU Coulomb accelerations vs the FP64 oracle on 256 sampled ions of the final state "
+                      "(bar 1e-5); trajectories: tests/test_gpu_parity.py",
         "e2e": {"value": e2e_value, "unit": "ion-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps * nsteps,
@@ -352,14 +356,34 @@ def extra_measurements(it, torch, stream, sms, args):
         e1.synchronize()
         ms = e0.elapsed_time(e1)
         cfg = s.config()
+    with it.Simulation(wc.species, wc.species_of_ion, wc.x0, wc.v0, pc, stream=stream) as s:
+        errs, done = [], 0
+        for mark in (0, 142, 285, 428, 571, 714, 857, 999):
+            s.step(mark - done)
+            done = mark
+            errs.append(sampled_force_error(it, s, wc, k=256, seed=mark))
     us = 1e3 * ms / k
     gp = nc * (nc - 1) / (us * 1e-6) / 1e9
     peak = sms * NOMINAL_SM_MHZ * 1e6 * FP32_LANES_PER_SM / FP32_OPS_PER_PAIR / 1e9
     out["crystal_n32768"] = {"ion_steps_per_s": nc * k / (ms / 1e3),
                              "pair_interactions_per_s": nc * (nc - 1) * k / (ms / 1e3),
                              "us_per_timestep": us, "timesteps": k, "tile": list(cfg),
-                             "roofline_frac": gp / peak, "achieved_gpair_s": gp, "peak_gpair_s": peak}
+                             "roofline_frac": gp / peak, "achieved_gpair_s": gp, "peak_gpair_s": peak,
+                             "force_rel_rms_vs_oracle_max": max(errs),
+                             "error_sample": "256 ions at steps 0, 142, ..., 999 of a 1000-step run"}
     return out
+
+
+def sampled_force_error(it, sim, w, k=256, seed=0):
+    """Relative RMS of the GPU Coulomb accelerations at the current state against the FP64
+    oracle on k sampled ions (the oracle evaluates those ions' sums exactly)."""
+    import oracle
+    f = sim.forces()
+    x = sim.state()[0]
+    q, m, _ = oracle.ion_arrays(w.species, w.species_of_ion)
+    idx = np.random.default_rng(seed).choice(w.n, min(k, w.n), replace=False)
+    ref = oracle.coulomb_accel(x, q, m, idx=idx)
+    return float(np.sqrt(((f[:, idx] - ref) ** 2).sum() / (ref ** 2).sum()))
 
 
 def batched_measurement(it, torch, stream, steps=2000):
@@ -380,12 +404,15 @@ def batched_measurement(it, torch, stream, steps=2000):
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1)
+        pick = np.random.default_rng(7).choice(len(ws), 8, replace=False)
+        errs = [sampled_force_error(it, sims[k], ws[k], k=64, seed=int(k)) for k in pick]
     finally:
         for s in sims:
             s.close()
     ions = sum(w.n for w in ws)
     pairs = sum(w.n * (w.n - 1) for w in ws)
     return {"ensembles": len(ws), "ions": ions, "timesteps": steps, "ms": ms,
+            "force_rel_rms_vs_oracle_max": max(errs), "error_sample": "8 ensembles, 64 ions each, after the run",
             "ion_steps_per_s": ions * steps / (ms / 1e3), "pair_interactions_per_s": pairs * steps / (ms / 1e3),
             "launches": (steps + 99) // 100}
 
