@@ -104,11 +104,21 @@ __global__ void __launch_bounds__(kBThreads)
     spi[q] = ok ? ens->sp[ii[q]] : 0;
   }
   bool finite = true;
+  // drift and half kick toward the next force evaluation; afterwards they are carried
+  // from step to step (the next step's values are the ones each step ends with)
+  double xf[2][3], vd[2][3];
+  if (ens) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        vd[q][c] = half_kick(v[q][c], a[q][c], ens->trap.hdt);
+        xf[q][c] = drift(x[q][c], vd[q][c], ens->trap.dt);
+      }
+  }
   sync_all();  // every copy staged before any CTA writes into another's
 
-  int kmax = 0;
-  for (int q = 0; q < job.nens; ++q) kmax = max(kmax, s_steps[q]);
-  // kmax is uniform within a CTA; CTAs of one cluster may differ, so the loop runs to K
+  // CTAs of one cluster may hold ensembles with different step counts: the loop runs to K
   for (int k = 0; k < K; ++k) {
     // per held ensemble: RF phase at the force time, then its species' spring constants
     if (tid < job.nens && k < s_steps[tid]) {
@@ -121,6 +131,14 @@ __global__ void __launch_bounds__(kBThreads)
     }
     __syncthreads();
     const bool active = ens && k < s_steps[le];
+    // the force-independent part of the acceleration, ahead of the pair loop
+    double ext[2][3];
+    if (active) {
+      const long long ns = s_n0[le] + k;
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+        if (ii[q] < n) accel_ext<false>(ens->trap, ens->spc[spi[q]], s_springs[le][spi[q]], xf[q], vd[q], ns + 1, ii[q], ext[q]);
+    }
     double S[2][3];
     if (active) {
       const float4* sh = sm + job.soff[le];
@@ -167,28 +185,24 @@ __global__ void __launch_bounds__(kBThreads)
     sync_all();  // every read of every stream copy is done
     if (active) {
       const TrapDev& tp = ens->trap;
-      const long long ns = s_n0[le] + k;
       float4* sh = sm + job.soff[le];
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         if (ii[q] >= n) continue;
         const SpeciesDev& sd = ens->spc[spi[q]];
-        double xf[3], vd[3], acc[3], xn[3];
+        double acc[3], xn[3];
+        accel_total(sd, S[q], ext[q], acc);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          vd[c] = half_kick(v[q][c], a[q][c], tp.hdt);
-          xf[c] = drift(x[q][c], vd[c], tp.dt);
-        }
-        double ext[3];
-        accel_ext<false>(tp, sd, s_springs[le][spi[q]], xf, vd, ns + 1, ii[q], ext);
-        accel_total(sd, S[q], ext, acc);
-        double vn[3];
-        finite = verlet_finish(tp, xf, vd, acc, vn, xn) && finite;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          x[q][c] = xf[c];
-          v[q][c] = vn[c];
+          const double vn = half_kick(vd[q][c], acc[c], tp.hdt);
+          const double vh = half_kick(vn, acc[c], tp.hdt);
+          xn[c] = drift(xf[q][c], vh, tp.dt);
+          finite = finite && isfinite(acc[c]) && isfinite(vn) && isfinite(xn[c]);
+          x[q][c] = xf[q][c];
+          v[q][c] = vn;
           a[q][c] = acc[c];
+          xf[q][c] = xn[c];
+          vd[q][c] = vh;
         }
         float hv[3], lv[3];
 #pragma unroll
@@ -207,7 +221,6 @@ __global__ void __launch_bounds__(kBThreads)
     }
     sync_all();  // new entries visible in every copy
   }
-  (void)kmax;
 
   // write back: FP64 state, the pair stream x_{n+1} of the final state, step, flags
   if (ens) {
