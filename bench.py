@@ -36,14 +36,20 @@ sys.path.insert(0, ROOT)
 
 STEPS_PER_BENCH_STEP = 5000
 # FP32-pipe instructions per ordered pair in the hi/lo pair term: 9 FADD (differences),
-# 3 FMUL/FFMA (r^2), 3 FMUL (z_j r^-3), 3 FFMA (accumulate); plus 1 MUFU rsqrt.
+# 3 FMUL/FFMA (r^2), 3 FMUL (z_j r^-3), 3 FFMA (accumulate); plus 1 MUFU rsqrt.  When every
+# ion is singly charged the z_j product is skipped (it is exact), leaving 17.
 FP32_OPS_PER_PAIR = 18
+
+
+def ops_per_pair(species):
+    return FP32_OPS_PER_PAIR - 1 if all(float(s.charge_e) == 1.0 for s in species) else FP32_OPS_PER_PAIR
+
 FP32_LANES_PER_SM = 128
 MUFU_PER_SM = 16
 NOMINAL_SM_MHZ = 2070.0
 # DRAM bytes (read + write) per launch of the step kernel, from the ncu capture summarised
 # in profiles/step_f32_cw_mix_n4096.md; valid only for that launch configuration.
-PROFILED_TRAFFIC = {(128, 2, 1, 512, 3): 477696 + 0}
+PROFILED_TRAFFIC = {(128, 2, 1, 512, 3): 485376 + 0}
 
 
 def _dist():
@@ -234,7 +240,8 @@ def run_gpu(args):
     pairs = n * (n - 1)
     kernel_us = ms_per_step * 1e3 / nsteps
     achieved_gpairs = pairs / (kernel_us * 1e-6) / 1e9
-    peak_gpairs = sms * NOMINAL_SM_MHZ * 1e6 * min(FP32_LANES_PER_SM / FP32_OPS_PER_PAIR, MUFU_PER_SM) / 1e9
+    opp = ops_per_pair(w.species)
+    peak_gpairs = sms * NOMINAL_SM_MHZ * 1e6 * min(FP32_LANES_PER_SM / opp, MUFU_PER_SM) / 1e9
     sim.close()
 
     # e2e: through the C ABI with host buffers, H2D + D2H inside the timed region
@@ -303,7 +310,7 @@ def run_gpu(args):
                      "traffic": PROFILED_TRAFFIC.get(tuple(cfg[:5])),
                      "traffic_unit": "DRAM bytes per launch (ncu, profiles/step_f32_cw_mix_n4096.md)",
                      "basis": f"{sms} SMs x {NOMINAL_SM_MHZ:.0f} MHz x {FP32_LANES_PER_SM} FP32 lanes / "
-                              f"{FP32_OPS_PER_PAIR} FP32 instr per ordered pair (MUFU roof "
+                              f"{opp} FP32 instr per ordered pair (MUFU roof "
                               f"{MUFU_PER_SM}/clk/SM not binding); achieved = N(N-1) per launch / "
                               "mean launch time over the timed region",
                      "peak_source": "derived from SM count, nominal max SM clock and FP32 lane count",
@@ -364,7 +371,7 @@ def extra_measurements(it, torch, stream, sms, args):
             errs.append(sampled_force_error(it, s, wc, k=256, seed=mark))
     us = 1e3 * ms / k
     gp = nc * (nc - 1) / (us * 1e-6) / 1e9
-    peak = sms * NOMINAL_SM_MHZ * 1e6 * FP32_LANES_PER_SM / FP32_OPS_PER_PAIR / 1e9
+    peak = sms * NOMINAL_SM_MHZ * 1e6 * FP32_LANES_PER_SM / ops_per_pair(wc.species) / 1e9
     out["crystal_n32768"] = {"ion_steps_per_s": nc * k / (ms / 1e3),
                              "pair_interactions_per_s": nc * (nc - 1) * k / (ms / 1e3),
                              "us_per_timestep": us, "timesteps": k, "tile": list(cfg),

@@ -185,7 +185,15 @@ typedef struct {
                                     memory, each CTA integrating a slice of the i-block;
                                  3: as 2, with an i-block of 32*ions_per_thread ions held by
                                     every warp of the CTA (threads = 32 W) and the W warps
-                                    splitting the CTA's j-range into interleaved chunks.
+                                    splitting the CTA's j-range into interleaved chunks;
+                                 4: grid-persistent: one cooperative launch runs up to 1000
+                                    steps with every CTA resident (threads = 256 or 512,
+                                    ions_per_thread = 2, packed = 1; S = ceil(n / jsplit) >= 7
+                                    j-segments; the (ceil(n / (2 threads)) groups x S) CTAs
+                                    must fit on the GPU at once, segments at most 4096 ions);
+                                    each CTA sums a group of 2*threads ions against one
+                                    segment and integrates an equal share of its group; no
+                                    CUDA graph, pdl ignored; not with IONTRAP_COULOMB_OFF.
                                  The FP64 form supports 1 only. */
     int32_t pdl;              /* 1: consecutive step kernels use programmatic dependent launch
                                  (default 0: measured slower on GB300 for these grids) */
@@ -270,7 +278,7 @@ int iontrap_forces_noalloc(const iontrap_species *species, int n_species, const 
                            const double *d_x, int64_t n, double *d_acc, void *cuda_stream);
 
 /* Profiling hook: run ONE step with per-CTA phase timestamps (%globaltimer, ns) and copy
- * them to marks[cap].  Layout: 4 marks per force-kernel CTA, CTA id = y*grid.x + x
+ * them to marks[cap] (EINVAL in the grid-persistent form 4).  Layout: 4 marks per force-kernel CTA, CTA id = y*grid.x + x
  * (start after the grid dependency wait, end of the pair loop, start of the fused
  * epilogue or 0, end of the fused epilogue or 0), then 2 per epilogue-kernel CTA (start,
  * end) when the configuration is not fused.  *n_force and *n_epi receive the counts.

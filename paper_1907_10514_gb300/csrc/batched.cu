@@ -161,10 +161,17 @@ __global__ void __launch_bounds__(kBThreads)
       for (int j0 = 0; j0 < n; j0 += kBChunk) {
         const int jn = min(kBChunk, n - j0);
         float2 acc[1][3] = {{make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)}};
-        if (j0 == w0)
-          segment_f32x2<2, true>(sh + j0, sl + j0, jn, j0, nxh, nxl, iil, acc);
-        else
-          segment_f32x2<2, false>(sh + j0, sl + j0, jn, j0, nxh, nxl, iil, acc);
+        if (ens->unitw) {
+          if (j0 == w0)
+            segment_f32x2<2, true, true>(sh + j0, sl + j0, jn, j0, nxh, nxl, iil, acc);
+          else
+            segment_f32x2<2, false, true>(sh + j0, sl + j0, jn, j0, nxh, nxl, iil, acc);
+        } else {
+          if (j0 == w0)
+            segment_f32x2<2, true>(sh + j0, sl + j0, jn, j0, nxh, nxl, iil, acc);
+          else
+            segment_f32x2<2, false>(sh + j0, sl + j0, jn, j0, nxh, nxl, iil, acc);
+        }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const float av[2] = {acc[0][c].x, acc[0][c].y};

@@ -30,6 +30,10 @@ const void* prep_kernel();
 const void* restore_kernel();
 cudaError_t launch_normals(unsigned long long seed, long long counter, const long long* d_ids, long long m,
                            int f64, double* d_z, cudaStream_t st);
+// persistent.cu
+cudaError_t launch_gp(const StepArgs& a, unsigned* sync, int W, int S, int G, int Lmax, long long K,
+                      cudaStream_t st);
+int gp_max_ctas(int W, int S, int Lmax, int max_lmax, long long max_k, int sms);
 }  // namespace it
 
 using namespace it;
@@ -38,7 +42,18 @@ static constexpr int kGraphSteps = 100;
 static constexpr int kMaxJsplitF64 = 2048;  // FP64 form stages its whole j-range
 static constexpr int64_t kMaxSplitsUnfused = 64;
 static constexpr int64_t kMaxClusterSplits = 8;   // portable cluster size (form 2)
-static constexpr int64_t kMaxClusterSplits3 = 16; // non-portable cluster size (form 3)   // records one epilogue lane group folds
+static constexpr int64_t kMaxClusterSplits3 = 16; // non-portable cluster size (form 3)
+// grid-persistent form (fused = 4)
+static constexpr int64_t kGpMaxSteps = 1000;   // steps per cooperative launch
+static constexpr int64_t kGpMaxSeg = 4096;     // j-segment entries staged in shared memory (128 KB)
+static constexpr int64_t kGpMaxGroups = 255;   // i-groups (one counter each)
+static constexpr size_t kGpSyncBytes = 32 * (1 + kGpMaxGroups) * sizeof(unsigned);
+
+// Launch shape of the grid-persistent form: W warps per CTA, S j-segments (CTAs per
+// i-group of 64 W ions), G = groups x S co-resident CTAs, Lmax entries per segment.
+struct GpShape {
+  int W = 0, S = 0, G = 0, Lmax = 0;
+};
 
 struct iontrap {
   int64_t n = 0;
@@ -63,6 +78,8 @@ struct iontrap {
   int* d_err = nullptr;
   // launch configuration
   int T = 128, I = 1, packed = 0, jsplit = 128, fused = 1, pdl = 0, use_graph = 1;
+  GpShape gp{};                 // fused = 4
+  unsigned* d_gsync = nullptr;  // fused = 4: step and group counters (zero between launches)
   StepArgs args{};
   // graph of kGraphSteps chained steps
   cudaGraph_t graph = nullptr;
@@ -86,6 +103,22 @@ struct DeviceGuard {
 };
 
 int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Shape of a grid-persistent configuration (FP32 form with the pair term, 256 or 512
+// threads, two ions per lane packed, at least seven segments, every CTA co-resident),
+// or false when the configuration does not qualify.
+bool gp_shape(int64_t n, int f64, unsigned flags, int sms, int T, int I, int packed, int64_t jsplit, GpShape* out) {
+  if (f64 || (flags & IONTRAP_COULOMB_OFF) || (T != 256 && T != 512) || I != 2 || packed != 1 || jsplit < 1 ||
+      jsplit > n)
+    return false;
+  const int W = T / 32;
+  const int64_t S = cdiv(n, jsplit), groups = cdiv(n, 64 * (int64_t)W), Lmax = cdiv(n, S);
+  // every CTA integrates at most ceil(64 W / S) ions, one thread per component
+  if (S < 2 || 3 * cdiv(64 * W, S) > 32 * W || groups > kGpMaxGroups || Lmax > kGpMaxSeg) return false;
+  if (S > 64 * W || groups * S > gp_max_ctas(W, (int)S, (int)Lmax, (int)kGpMaxSeg, kGpMaxSteps, sms)) return false;
+  out->W = W, out->S = (int)S, out->G = (int)(groups * S), out->Lmax = (int)Lmax;
+  return true;
+}
 
 double effective_dt(const iontrap_params* p) {
   if (p->dt > 0) return p->dt;
@@ -287,8 +320,12 @@ int64_t splits_of(const iontrap* h) {
 }
 
 // ions per i-block: T*I, except the cluster + warp-split form (fused = 3) whose warps
-// all hold the same 32*I ions
-int64_t iblock_ions(const iontrap* h) { return h->fused == 3 ? 32 * (int64_t)h->I : (int64_t)h->T * h->I; }
+// all hold the same 32*I ions, and the grid-persistent form (fused = 4) whose initial
+// evaluation at creation uses the last-CTA form with 128 x 2 ions
+int64_t iblock_ions(const iontrap* h) {
+  if (h->fused == 4) return 256;
+  return h->fused == 3 ? 32 * (int64_t)h->I : (int64_t)h->T * h->I;
+}
 
 dim3 grid_of(const iontrap* h) {
   return dim3((unsigned)cdiv(h->n, iblock_ions(h)), (unsigned)splits_of(h), 1);
@@ -328,6 +365,13 @@ int alloc_scratch(iontrap* h) {
   }
   if (cudaMemsetAsync(h->d_cnt, 0, h->cnt_len * sizeof(unsigned), h->stream) != cudaSuccess)
     return IONTRAP_ECUDA;
+  if (h->fused == 4) {
+    if (!gp_shape(h->n, h->f64, h->p.flags, h->sms, h->T, h->I, h->packed, h->jsplit, &h->gp)) return IONTRAP_EINVAL;
+    if (!h->d_gsync) {
+      if (cudaMalloc(&h->d_gsync, kGpSyncBytes) != cudaSuccess) return IONTRAP_ENOMEM;
+      if (cudaMemsetAsync(h->d_gsync, 0, kGpSyncBytes, h->stream) != cudaSuccess) return IONTRAP_ECUDA;
+    }
+  }
   h->args.part = h->d_part;
   h->args.cnt = h->d_cnt;
   h->args.jsplit = (h->p.flags & IONTRAP_COULOMB_OFF) ? (int)std::min<int64_t>(h->n, 1 << 30) : h->jsplit;
@@ -338,6 +382,16 @@ int alloc_scratch(iontrap* h) {
 // Launch one step kernel with programmatic dependent launch, so that consecutive steps
 // overlap one grid's launch with the previous grid's tail.
 cudaError_t launch_step_on(iontrap* h, StepArgs& a, cudaStream_t st) {
+  if (h->fused == 4) {
+    if (a.mode != MODE_INIT) return launch_gp(a, h->d_gsync, h->gp.W, h->gp.S, h->gp.G, h->gp.Lmax, 1, st);
+    // the initial evaluation (at creation or after restore): the last-CTA form over the same j-segments
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)cdiv(h->n, 256), (unsigned)splits_of(h), 1);
+    cfg.blockDim = dim3(128);
+    cfg.stream = st;
+    void* params[] = {&a};
+    return cudaLaunchKernelExC(&cfg, step_kernel(0, 128, 2, 1, 1), params);
+  }
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = grid_of(h);
   cfg.blockDim = dim3(h->T);
@@ -435,7 +489,7 @@ int prepare_kernels() {
 void free_all(iontrap* h) {
   destroy_graph(h);
   void* ptrs[] = {h->d_x, h->d_v, h->d_a, h->d_out, h->d_sp, h->d_pair[0], h->d_pair[1],
-                  h->d_part, h->d_cnt, h->d_done, h->d_step, h->d_err};
+                  h->d_part, h->d_cnt, h->d_done, h->d_step, h->d_err, h->d_gsync};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -524,7 +578,14 @@ int iontrap_create(const iontrap_species* species, int n_species, const uint8_t*
   }
   {
     iontrap_config tc{};
-    if (tuned_config(n, h->f64, h->device, &tc) && step_kernel(h->f64, tc.threads, tc.ions_per_thread, tc.packed, tc.fused) &&
+    GpShape gs;
+    const bool tuned = tuned_config(n, h->f64, h->device, &tc);
+    if (tuned && tc.fused == 4) {
+      if (gp_shape(n, h->f64, p->flags, h->sms, tc.threads, tc.ions_per_thread, tc.packed, tc.jsplit, &gs)) {
+        h->T = tc.threads, h->I = tc.ions_per_thread, h->packed = tc.packed, h->jsplit = tc.jsplit;
+        h->fused = 4, h->pdl = 0, h->use_graph = 0;
+      }
+    } else if (tuned && step_kernel(h->f64, tc.threads, tc.ions_per_thread, tc.packed, tc.fused) &&
         tc.jsplit >= 1 && tc.jsplit <= n && (!h->f64 || tc.jsplit <= kMaxJsplitF64) &&
         (tc.fused || cdiv(n, tc.jsplit) <= kMaxSplitsUnfused) &&
         (tc.fused < 2 || (cdiv(n, tc.jsplit) <= (tc.fused == 3 ? kMaxClusterSplits3 : kMaxClusterSplits) &&
@@ -558,6 +619,9 @@ int iontrap_create(const iontrap_species* species, int n_species, const uint8_t*
   A.trap.seed = p->seed;
   A.trap.flags = p->flags;
   A.n = n;
+  A.unitw = 1;  // every species singly charged (+1 e): exact to drop the z_j factor
+  for (int s = 0; s < n_species; ++s)
+    if (species[s].charge_e != 1.0) A.unitw = 0;
 
   const size_t vec = 3 * (size_t)n * sizeof(double);
   const size_t pair = (size_t)n * (h->f64 ? sizeof(double4_32a) : 2 * sizeof(float4));
@@ -626,6 +690,19 @@ int iontrap_step(iontrap_t* h, int64_t n_steps) {
   if (!h || n_steps < 0) return IONTRAP_EINVAL;
   if (h->status) return h->status;
   DeviceGuard g(h->device);
+  if (h->fused == 4) {  // grid-persistent form: up to kGpMaxSteps steps per cooperative launch
+    StepArgs a = h->args;
+    a.mode = MODE_STEP;
+    a.out = nullptr;
+    while (n_steps > 0) {
+      const int64_t k = std::min<int64_t>(n_steps, kGpMaxSteps);
+      cudaError_t e = launch_gp(a, h->d_gsync, h->gp.W, h->gp.S, h->gp.G, h->gp.Lmax, k, h->stream);
+      if (e != cudaSuccess) return cuda_status(h, e);
+      n_steps -= k;
+      h->step += k;
+    }
+    return h->status;
+  }
   if (n_steps >= kGraphSteps && h->use_graph && !h->gexec) {
     cudaError_t e = build_graph(h);
     if (e != cudaSuccess) return cuda_status(h, e);
@@ -729,7 +806,7 @@ int iontrap_restore(iontrap_t* h, const double* x, const double* v, const double
 }
 
 int iontrap_trace_step(iontrap_t* h, unsigned long long* marks, int64_t cap, int64_t* n_force, int64_t* n_epi) {
-  if (!h || !marks || cap < 1) return IONTRAP_EINVAL;
+  if (!h || !marks || cap < 1 || h->fused == 4) return IONTRAP_EINVAL;
   int st = iontrap_sync(h);
   if (st) return st;
   DeviceGuard g(h->device);
@@ -808,6 +885,7 @@ int iontrap_step_many(iontrap_t* const* hs, const int64_t* n_steps, int count) {
     E.step0 = h->step;
     E.trap = h->args.trap;
     E.nspecies = h->nspecies;
+    E.unitw = h->args.unitw;
     std::memcpy(E.spc, h->args.spc, sizeof(E.spc));
     steps[b] = n_steps[batch[b]];
   }
@@ -871,13 +949,18 @@ int iontrap_estimate_bytes(int64_t n, int precision, int64_t* bytes) {
   int T, I, P, J, F;
   default_config(n, f64, sms, &T, &I, &P, &J, &F);
   iontrap_config tc{};
-  if (tuned_config(n, f64, dev, &tc) && step_kernel(f64, tc.threads, tc.ions_per_thread, tc.packed, tc.fused)) {
+  GpShape gs;
+  if (tuned_config(n, f64, dev, &tc) &&
+      (step_kernel(f64, tc.threads, tc.ions_per_thread, tc.packed, tc.fused) ||
+       (tc.fused == 4 && gp_shape(n, f64, 0, sms, tc.threads, tc.ions_per_thread, tc.packed, tc.jsplit, &gs)))) {
     T = tc.threads, I = tc.ions_per_thread, J = tc.jsplit, F = tc.fused;
   }
-  const int64_t splits = cdiv(n, J), iblocks = cdiv(n, (F == 3 ? 32 : (int64_t)T) * I);
+  const int64_t splits = cdiv(n, J);
+  const int64_t iblocks = F == 4 ? cdiv(n, 256) : cdiv(n, (F == 3 ? 32 : (int64_t)T) * I);
   const int64_t vec = 3 * n * (int64_t)sizeof(double);
   const int64_t pair = n * (int64_t)(f64 ? sizeof(double4_32a) : 2 * sizeof(float4));
-  *bytes = 3 * vec + n + 2 * pair + splits * n * 32 + iblocks * (int64_t)sizeof(unsigned) + 64;
+  *bytes = 3 * vec + n + 2 * pair + splits * n * 32 + iblocks * (int64_t)sizeof(unsigned) + 64 +
+           (F == 4 ? (int64_t)kGpSyncBytes : 0);
   return IONTRAP_OK;
 }
 
@@ -940,6 +1023,16 @@ int iontrap_autotune(iontrap_t* h, double trial_us, iontrap_config* best, double
         if (S > std::max<int64_t>(1, n / 128)) continue;
         iontrap_config c{32 * iw[1], iw[0], iw[0] == 2 ? 1 : 0, (int32_t)cdiv(n, S), 3, 0, 1};
         if (step_kernel(0, c.threads, c.ions_per_thread, c.packed, 3)) cands.push_back(c);
+      }
+  }
+  if (!h->f64 && !(h->p.flags & IONTRAP_COULOMB_OFF)) {  // grid-persistent shapes: one or two CTAs per SM
+    for (int W : {8, 16})
+      for (int per = 1; per <= 2; ++per) {
+        const int64_t S = (int64_t)per * h->sms / cdiv(n, 64 * (int64_t)W);
+        if (S < 2) continue;
+        iontrap_config c{32 * W, 2, 1, (int32_t)cdiv(n, S), 4, 0, 0};
+        GpShape gs;
+        if (gp_shape(n, 0, h->p.flags, h->sms, c.threads, 2, 1, c.jsplit, &gs)) cands.push_back(c);
       }
   }
   cudaEvent_t e0, e1;
@@ -1026,7 +1119,7 @@ int iontrap_device_bytes(const iontrap_t* h, int64_t* bytes) {
   const int64_t vec = 3 * h->n * (int64_t)sizeof(double);
   const int64_t pair = h->n * (int64_t)(h->f64 ? sizeof(double4_32a) : 2 * sizeof(float4));
   *bytes = 3 * vec + (h->d_out ? vec : 0) + h->n + 2 * pair + (int64_t)h->part_bytes +
-           (int64_t)h->cnt_len * (int64_t)sizeof(unsigned) + 64;
+           (int64_t)h->cnt_len * (int64_t)sizeof(unsigned) + 64 + (h->d_gsync ? (int64_t)kGpSyncBytes : 0);
   return IONTRAP_OK;
 }
 
@@ -1044,7 +1137,13 @@ int iontrap_get_config(const iontrap_t* h, iontrap_config* c) {
 
 int iontrap_set_config(iontrap_t* h, const iontrap_config* c) {
   if (!h || !c) return IONTRAP_EINVAL;
-  if (!step_kernel(h->f64, c->threads, c->ions_per_thread, c->packed, c->fused)) return IONTRAP_EINVAL;
+  GpShape gs;
+  if (c->fused == 4) {
+    if (!gp_shape(h->n, h->f64, h->p.flags, h->sms, c->threads, c->ions_per_thread, c->packed, c->jsplit, &gs))
+      return IONTRAP_EINVAL;
+  } else if (!step_kernel(h->f64, c->threads, c->ions_per_thread, c->packed, c->fused)) {
+    return IONTRAP_EINVAL;
+  }
   if (c->jsplit < 1 || c->jsplit > h->n || (h->f64 && c->jsplit > kMaxJsplitF64)) return IONTRAP_EINVAL;
   if (!c->fused && cdiv(h->n, c->jsplit) > kMaxSplitsUnfused) return IONTRAP_EINVAL;
   if (c->fused == 2 && cdiv(h->n, c->jsplit) > kMaxClusterSplits) return IONTRAP_EINVAL;

@@ -63,6 +63,7 @@ struct StepArgs {
   unsigned long long* trace;  // optional per-CTA phase timestamps (globaltimer ns), or null
   long long trace_epi;        // offset of the epilogue kernel's marks in trace
   int mode;
+  int unitw;           // every ion has charge +1 e: the pair loop skips the z_j factor (exact)
   int jsplit;          // j-range per CTA (grid.y = ceil(n / jsplit))
   int nsplit;          // ceil(n / jsplit): partials per ion for the epilogue kernel
   TrapDev trap;
@@ -83,6 +84,7 @@ struct BatchEns {
   long long step0;      // state step index when the batch was enqueued
   long long remaining;  // steps still to take; decremented by the kernel
   int nspecies;
+  int unitw;            // every ion has charge +1 e
   TrapDev trap;
   SpeciesDev spc[IONTRAP_MAX_SPECIES];
 };
@@ -158,7 +160,7 @@ __device__ __forceinline__ void trace_mark(unsigned long long* trace, long long 
 // (x_j,hi - x_i,hi) is exact for close pairs (Sterbenz) and the lo difference restores
 // the bits FP32 rounding dropped from both positions.  The accumulators therefore hold
 // -sum_j z_j (x_i - x_j)/r^3; the epilogue flips the sign.
-template <int I, bool DIAG>
+template <int I, bool DIAG, bool UNITW = false>
 __device__ __forceinline__ void segment_f32(const float4* __restrict__ sh, const float4* __restrict__ sl, int jn,
                                             long long jbase, const float (&nxh)[I][3], const float (&nxl)[I][3],
                                             const long long (&ii)[I], float (&acc)[I][3]) {
@@ -175,7 +177,7 @@ __device__ __forceinline__ void segment_f32(const float4* __restrict__ sh, const
       float ri = rsqrt_approx(r2);
       if (DIAG) ri = (jbase + j == ii[k]) ? 0.0f : ri;
       const float ri2 = ri * ri;
-      const float s = (ph.w * ri) * ri2;  // z_j / r^3
+      const float s = (UNITW ? ri : ph.w * ri) * ri2;  // z_j / r^3 (z_j = 1: the product is exact)
       acc[k][0] = fmaf(s, dx, acc[k][0]);
       acc[k][1] = fmaf(s, dy, acc[k][1]);
       acc[k][2] = fmaf(s, dz, acc[k][2]);
@@ -186,7 +188,7 @@ __device__ __forceinline__ void segment_f32(const float4* __restrict__ sh, const
 // The same arithmetic on two ions per instruction (packed FP32x2 FADD/FMUL/FFMA of
 // sm_100+); each lane rounds exactly as the scalar loop does, so both loops give the
 // same bits.
-template <int I, bool DIAG>
+template <int I, bool DIAG, bool UNITW = false>
 __device__ __forceinline__ void segment_f32x2(const float4* __restrict__ sh, const float4* __restrict__ sl, int jn,
                                               long long jbase, const float2 (&nxh)[I / 2][3],
                                               const float2 (&nxl)[I / 2][3], const long long (&ii)[I],
@@ -210,12 +212,57 @@ __device__ __forceinline__ void segment_f32x2(const float4* __restrict__ sh, con
         ri.y = (jbase + j == ii[2 * k + 1]) ? 0.0f : ri.y;
       }
       const float2 ri2 = __fmul2_rn(ri, ri);
-      const float2 s = __fmul2_rn(__fmul2_rn(w, ri), ri2);
+      const float2 s = __fmul2_rn(UNITW ? ri : __fmul2_rn(w, ri), ri2);
       acc[k][0] = __ffma2_rn(s, dx, acc[k][0]);
       acc[k][1] = __ffma2_rn(s, dy, acc[k][1]);
       acc[k][2] = __ffma2_rn(s, dz, acc[k][2]);
     }
   }
+}
+
+// ------------------------------------------------------------------ split partials
+// RF phase at the force time of a launch in the given mode.
+__device__ __forceinline__ double force_time_cos(const StepArgs& A, long long ns) {
+  const long long nf = (A.mode == MODE_STEP) ? ns + 1 : ns;
+  if (A.trap.flags & (IONTRAP_RF_OFF | IONTRAP_TRAP_OFF)) return 0.0;
+  return cos(A.trap.Omega * ((double)nf * A.trap.dt));
+}
+
+// Split partials are stored as one 32-byte record per (split, ion):
+//   FP32 form: float[8] = (sum_x, sum_y, sum_z, 0, comp_x, comp_y, comp_z, 0)
+//   FP64 form: double[4] = (sum_x, sum_y, sum_z, 0)
+// at record index split * n + i.  The merge runs in split order: FP32 form by
+// compensated (Kahan) addition of the (sum, compensation) pairs -- the accumulators hold
+// the negated sum, hence the sign -- FP64 form by a plain FP64 sum.
+__device__ __forceinline__ void kahan_merge(float& s, float& cc, float ps, float pc) {
+  const float y = ps - cc;
+  const float t = s + y;
+  cc = ((t - s) - y) + pc;
+  s = t;
+}
+
+__device__ __forceinline__ void merge_f32(const float4* __restrict__ part, long long n, long long i, int nsplit,
+                                          double S[3]) {
+  float s[3] = {0.f, 0.f, 0.f}, cc[3] = {0.f, 0.f, 0.f};
+  constexpr int U = 4;
+  for (int p0 = 0; p0 < nsplit; p0 += U) {
+    float4 a[U], b[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (p0 + u < nsplit) {
+        a[u] = __ldcg(part + 2 * ((p0 + u) * n + i));
+        b[u] = __ldcg(part + 2 * ((p0 + u) * n + i) + 1);
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (p0 + u < nsplit) {
+        kahan_merge(s[0], cc[0], a[u].x, b[u].x);
+        kahan_merge(s[1], cc[1], a[u].y, b[u].y);
+        kahan_merge(s[2], cc[2], a[u].z, b[u].z);
+      }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) S[c] = (double)cc[c] - (double)s[c];
 }
 
 // ------------------------------------------------------------------ Philox-4x64-10
@@ -325,12 +372,24 @@ __device__ __forceinline__ void trap_springs(const TrapDev& tp, const SpeciesDev
 // bits.  The trajectories of these clouds amplify FP32-sized perturbations of the RF trap
 // term by ~1e4 within 100 steps, so no term is evaluated in FP32.  F64 selects FP64
 // Box-Muller noise.
+// The deterministic part (trap springs and drag) and the kick sigma*xi, separately so
+// that a kernel can draw the normals ahead of time.
+__device__ __forceinline__ void accel_ext_det(const TrapDev& tp, const double k[3], const double xf[3],
+                                              const double vd[3], double ext[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) ext[c] = __fma_rn(-tp.gamma, vd[c], __dmul_rn(-k[c], xf[c]));
+}
+
+__device__ __forceinline__ void accel_add_kick(const SpeciesDev& sd, const double z[3], double ext[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) ext[c] = __fma_rn(sd.sigma, z[c], ext[c]);
+}
+
 template <bool F64>
 __device__ __forceinline__ void accel_ext(const TrapDev& tp, const SpeciesDev& sd, const double k[3],
                                           const double xf[3], const double vd[3], long long counter, long long id,
                                           double ext[3]) {
-#pragma unroll
-  for (int c = 0; c < 3; ++c) ext[c] = __fma_rn(-tp.gamma, vd[c], __dmul_rn(-k[c], xf[c]));
+  accel_ext_det(tp, k, xf, vd, ext);
   if (sd.sigma > 0.0) {
     double z[3];
     if constexpr (F64) {
@@ -340,8 +399,7 @@ __device__ __forceinline__ void accel_ext(const TrapDev& tp, const SpeciesDev& s
       normals3_f32(tp.seed, counter, id, zf);
       z[0] = zf[0], z[1] = zf[1], z[2] = zf[2];
     }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) ext[c] = __fma_rn(sd.sigma, z[c], ext[c]);
+    accel_add_kick(sd, z, ext);
   }
 }
 

@@ -1,0 +1,359 @@
+// persistent.cu -- grid-persistent step form (fused = 4) of libiontrap.so (sm_103a).
+//
+// One cooperative launch advances a simulation by K velocity-Verlet steps (Sec. 6
+// "Integration"); every CTA stays resident for the whole launch.  The work of a step
+// is split statically so that every CTA gets the same number of pair evaluations
+// (Eq. 4, direct sum):
+//   group g    : W i-blocks of 64 ions (one per warp, two ions per lane, packed FP32x2)
+//   segment s  : j in [s n / S, (s+1) n / S), staged into shared memory
+//   CTA g*S+s  : group g against segment s, and owner of the ions
+//                [g0 + s |g| / S, g0 + (s+1) |g| / S) of its group
+// A step: each warp leaves its (sum, compensation) pairs for (segment, ion) in global
+// scratch; the S CTAs of a group count their arrivals on the group's counter; each
+// owner merges its ions' S partials in segment order (Kahan), finishes the FP64 Verlet
+// update (trap, drag and noise were evaluated before the pair loop), writes the next
+// pair-stream entries and counts its CTA on the step counter; the next step starts once
+// every CTA has counted.  The owners' FP64 state stays in registers from step to step.
+// Every wait is bounded (2 s of %globaltimer) and gives up at once when another CTA has
+// flagged a timeout, so a launch always ends.
+//
+// Summation order depends on (n, W, S) only: j ascending inside 128-wide chunks of a
+// segment, chunks Kahan-added per warp, segments Kahan-merged in order.
+#include <cstdio>
+
+#include "iontrap_internal.cuh"
+
+namespace it {
+
+struct GpArgs {
+  unsigned* sync;  // [0]: step arrivals of all CTAs; [32 (1 + g)]: arrivals of group g (zero between launches)
+  long long K;     // steps in this launch
+  int S;           // segments = CTAs per group
+  int Lmax;        // entries per stream of the largest segment (shared-memory extent)
+};
+
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Release/acquire fence at GPU scope: orders this thread's (and, after a CTA barrier,
+// the CTA's) earlier accesses before a counter update, or a counter read before later
+// accesses.
+__device__ __forceinline__ void fence_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+// Wait until *ctr >= target (relaxed polling: the caller fences after a successful
+// wait).  Gives up (false) after kWaitLimitNs, setting the timeout flag, or at once when
+// the flag is already set by another CTA.
+__device__ __noinline__ bool gp_wait(const unsigned* ctr, unsigned target, int* err) {
+  if (ld_relaxed_u32(ctr) >= target) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  for (;;) {
+    if (ld_relaxed_u32(ctr) >= target) return true;
+    if (*(volatile int*)err & ERR_TIMEOUT) return false;
+    if (globaltimer_ns() - t0 > kWaitLimitNs) {
+      atomicOr(err, ERR_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+// Trap spring constant of component c (the c-th value trap_springs gives, same roundings).
+__device__ __forceinline__ double trap_spring_c(const TrapDev& tp, const SpeciesDev& sd, double cosv, int c) {
+  if (tp.flags & IONTRAP_TRAP_OFF) return 0.0;
+  const double rwz2 = __dmul_rn(sd.rho, tp.wz2);
+  const double rq4 = __dmul_rn(tp.q4, sd.rho);
+  const double qc2 = __dmul_rn(2.0 * tp.q, cosv);
+  const double ax = (c == 0) ? __dsub_rn(tp.a, qc2) : __dadd_rn(tp.a, qc2);
+  const double kr = __fma_rn(rq4, ax, -0.5 * rwz2);
+  return c == 2 ? rwz2 : kr;
+}
+
+template <int W>
+__global__ void __launch_bounds__(32 * W, 16 / W) k_step_f32_gp(const __grid_constant__ StepArgs A, const GpArgs P) {
+  constexpr int T = 32 * W;
+  constexpr int B = 64;  // ions per warp
+  // dynamic shared memory: segment hi[Lmax], lo[Lmax]; the owned ions' partials as
+  // floats sum[3][S][R] and comp[3][S][R] (R <= Rmax = ceil(64 W / S)); the RF phase
+  // cos(Omega t) at the force time of each of the K steps
+  extern __shared__ __align__(16) float4 s_dyn[];
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const long long n = A.n;
+  const int S = P.S;
+  const unsigned G = gridDim.x;
+  const int g = (int)blockIdx.x / S, s = (int)blockIdx.x % S;
+  const long long g0 = (long long)g * (W * B), g1 = min(g0 + (long long)(W * B), n);
+  const long long gs = g1 - g0;
+  const long long r0 = g0 + (s * gs) / S, r1 = g0 + ((s + 1) * gs) / S;
+  const int R = (int)(r1 - r0);
+  const long long js0 = (s * n) / S, js1 = ((s + 1) * n) / S;
+  const int L = (int)(js1 - js0);
+  const long long i0 = g0 + (long long)warp * B;
+  const int rmax = (64 * W + S - 1) / S;
+  float4* sh = s_dyn;
+  float4* sl = s_dyn + P.Lmax;
+  float* fsum = reinterpret_cast<float*>(s_dyn + 2 * P.Lmax);
+  float* fcmp = fsum + 3 * S * rmax;
+  double* scos = reinterpret_cast<double*>(fcmp + 3 * S * rmax);  // 24 S rmax bytes past fsum: 8-byte aligned
+  unsigned* ctr_step = P.sync;
+  unsigned* ctr_grp = P.sync + 32 * (1 + g);
+  const int poller = T - 1;
+  const float4* part = reinterpret_cast<const float4*>(A.part);
+  float4* wpart = reinterpret_cast<float4*>(A.part);
+  const TrapDev& tp = A.trap;
+  const long long ns0 = *A.step;
+  const bool forces = A.mode == MODE_FORCES;  // one force evaluation of the current positions (K = 1)
+  const bool rf = !(tp.flags & (IONTRAP_RF_OFF | IONTRAP_TRAP_OFF));
+  if (!forces)
+    for (long long k = tid; k < P.K; k += T) scos[k] = rf ? cos(tp.Omega * ((double)(ns0 + k + 1) * tp.dt)) : 0.0;
+
+  // owned items: thread k < 3R integrates component c = k / R of ion r0 + k % R, so the
+  // FP64 chain of the integration is spread over three warps with a third of the
+  // instructions each
+  const int oc = tid / max(R, 1), oq = tid - oc * max(R, 1);
+  const bool own = tid < 3 * R;
+  const long long ie = r0 + oq;
+  int spe = 0;
+  double xf = 0.0, vd = 0.0;
+  float z = 0.f;
+  if (own) spe = A.sp[ie];
+  if (own && !forces) {
+    const double vh = half_kick(A.v[oc * n + ie], A.a[oc * n + ie], tp.hdt);
+    vd = vh;
+    xf = drift(A.x[oc * n + ie], vh, tp.dt);
+  }
+  // the Langevin normal of a step, drawn ahead of time (FP32 Box-Muller, as accel_ext)
+  auto draw = [&](long long counter) {
+    if (own && !forces && A.spc[spe].sigma > 0.0) {
+      float zz[3];
+      normals3_f32(tp.seed, counter, ie, zz);
+      z = oc == 0 ? zz[0] : (oc == 1 ? zz[1] : zz[2]);
+    }
+  };
+  draw(ns0 + 1);
+  __syncthreads();
+
+  for (long long t = 0; t < P.K; ++t) {
+    const long long ns = ns0 + t;
+    const int rb = forces ? (int)(ns & 1) : (int)((ns + 1) & 1);
+    // positions x_{ns+1} are complete once every CTA has finished step t-1
+    bool bad = false;
+    if (t > 0 && tid == poller) {
+      bad = !gp_wait(ctr_step, G * (unsigned)t, A.err);
+      fence_gpu();
+    }
+    if (__syncthreads_or(bad)) break;
+
+    const float4* __restrict__ ghi = A.hi[rb];
+    const float4* __restrict__ glo = A.lo[rb];
+    for (int j = tid; j < L; j += T) {
+      sh[j] = __ldcg(ghi + js0 + j);
+      sl[j] = __ldcg(glo + js0 + j);
+    }
+    long long ii[2];
+    float2 nxh[1][3], nxl[1][3];
+    {
+      float4 h[2], l[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        ii[k] = i0 + k * 32 + lane;
+        h[k] = l[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (ii[k] < n) {
+          h[k] = __ldcg(ghi + ii[k]);
+          l[k] = __ldcg(glo + ii[k]);
+        }
+      }
+      nxh[0][0] = make_float2(-h[0].x, -h[1].x), nxh[0][1] = make_float2(-h[0].y, -h[1].y);
+      nxh[0][2] = make_float2(-h[0].z, -h[1].z);
+      nxl[0][0] = make_float2(-l[0].x, -l[1].x), nxl[0][1] = make_float2(-l[0].y, -l[1].y);
+      nxl[0][2] = make_float2(-l[0].z, -l[1].z);
+    }
+    __syncthreads();  // segment staged
+
+    if (i0 < n) {
+      float ks[2][3], kc[2][3];
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) ks[k][d] = kc[k][d] = 0.0f;
+      for (int c0 = 0; c0 < L; c0 += kSeg) {
+        const int jn = min(kSeg, L - c0);
+        const long long jc = js0 + c0;
+        const bool diag = (jc < i0 + B) && (i0 < jc + jn);
+        float2 acc[1][3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) acc[0][d] = make_float2(0.0f, 0.0f);
+        if (A.unitw) {
+          if (diag)
+            segment_f32x2<2, true, true>(sh + c0, sl + c0, jn, jc, nxh, nxl, ii, acc);
+          else
+            segment_f32x2<2, false, true>(sh + c0, sl + c0, jn, jc, nxh, nxl, ii, acc);
+        } else {
+          if (diag)
+            segment_f32x2<2, true>(sh + c0, sl + c0, jn, jc, nxh, nxl, ii, acc);
+          else
+            segment_f32x2<2, false>(sh + c0, sl + c0, jn, jc, nxh, nxl, ii, acc);
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            const float a = k ? acc[0][d].y : acc[0][d].x;
+            const float y = a - kc[k][d];
+            const float tt = ks[k][d] + y;
+            kc[k][d] = (tt - ks[k][d]) - y;
+            ks[k][d] = tt;
+          }
+      }
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+        if (ii[k] < n) {
+          const long long r = 2 * ((long long)s * n + ii[k]);
+          __stcg(wpart + r, make_float4(ks[k][0], ks[k][1], ks[k][2], 0.0f));
+          __stcg(wpart + r + 1, make_float4(kc[k][0], kc[k][1], kc[k][2], 0.0f));
+        }
+    }
+    __syncthreads();
+    if (tid == poller) {
+      fence_gpu();
+      atomicAdd(ctr_grp, 1u);
+      bad = !gp_wait(ctr_grp, (unsigned)S * (unsigned)(t + 1), A.err);
+      fence_gpu();
+    }
+    // while the group's CTAs arrive: the owned components' force-independent terms
+    // (trap, drag, kick; the roundings of accel_ext) and the next step's normals
+    double ext = 0.0;
+    if (own && !forces) {
+      const SpeciesDev& sd = A.spc[spe];
+      const double kc = trap_spring_c(tp, sd, scos[t], oc);
+      ext = __fma_rn(-tp.gamma, vd, __dmul_rn(-kc, xf));
+      if (sd.sigma > 0.0) ext = __fma_rn(sd.sigma, (double)z, ext);
+    }
+    if (t + 1 < P.K) draw(ns + 2);
+    if (__syncthreads_or(bad)) break;
+
+    // the owned ions' S records, fetched by the whole CTA in one round trip
+    for (int k = tid; k < R * S; k += T) {
+      const int p = k / R, q = k - p * R;
+      const long long r = 2 * ((long long)p * n + r0 + q);
+      const float4 a = __ldcg(part + r), b = __ldcg(part + r + 1);
+      fsum[(0 * S + p) * R + q] = a.x, fsum[(1 * S + p) * R + q] = a.y, fsum[(2 * S + p) * R + q] = a.z;
+      fcmp[(0 * S + p) * R + q] = b.x, fcmp[(1 * S + p) * R + q] = b.y, fcmp[(2 * S + p) * R + q] = b.z;
+    }
+    __syncthreads();
+    if (own) {  // merge in segment order (Kahan), then finish the step
+      float su = 0.f, cu = 0.f;
+      const float* ps = fsum + oc * S * R + oq;
+      const float* pc = fcmp + oc * S * R + oq;
+      constexpr int U = 8;
+      for (int p0 = 0; p0 < S; p0 += U) {
+        float a[U], b[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (p0 + u < S) a[u] = ps[(p0 + u) * R], b[u] = pc[(p0 + u) * R];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (p0 + u < S) kahan_merge(su, cu, a[u], b[u]);
+      }
+      const double Sd = (double)cu - (double)su;
+      const SpeciesDev& sd = A.spc[spe];
+      if (forces) {
+        A.out[oc * n + ie] = sd.coul * Sd;
+      } else {
+        const double acc = __fma_rn(sd.coul, Sd, ext);
+        const double vn = half_kick(vd, acc, tp.hdt);
+        const double vh = half_kick(vn, acc, tp.hdt);
+        const double xn = drift(xf, vh, tp.dt);
+        A.x[oc * n + ie] = xf;
+        A.v[oc * n + ie] = vn;
+        A.a[oc * n + ie] = acc;
+        // next pair-stream entry, component by component (hi = fl(xn), lo = fl(xn - hi))
+        const float h = __double2float_rn(xn);
+        const float l = __double2float_rn(xn - (double)h);
+        reinterpret_cast<float*>(A.hi[rb ^ 1] + ie)[oc] = h;
+        reinterpret_cast<float*>(A.lo[rb ^ 1] + ie)[oc] = l;
+        if (oc == 0) {
+          reinterpret_cast<float*>(A.hi[rb ^ 1] + ie)[3] = sd.w;
+          reinterpret_cast<float*>(A.lo[rb ^ 1] + ie)[3] = 0.0f;
+        }
+        if (!(isfinite(acc) && isfinite(vn) && isfinite(xn))) atomicOr(A.err, ERR_NONFINITE);
+        vd = vh;  // the next step's kick and drift, as a fresh start would compute them
+        xf = xn;
+      }
+    }
+    __syncthreads();
+    if (tid == poller) {
+      fence_gpu();
+      atomicAdd(ctr_step, 1u);
+    }
+  }
+
+  // once every CTA has counted its last step: clear the counters, advance the step index
+  if (blockIdx.x == 0 && tid == poller) {
+    gp_wait(ctr_step, G * (unsigned)P.K, A.err);
+    const int groups = (int)(G / (unsigned)S);
+    for (int q = 0; q < groups; ++q) P.sync[32 * (1 + q)] = 0u;
+    *ctr_step = 0u;
+    if (!forces) *A.step = ns0 + P.K;
+    __threadfence();
+  }
+}
+
+// Dynamic shared memory of a launch: the segment (2 Lmax float4), the owned ions'
+// partials (2 x 3 x S x ceil(64 W / S) floats, rounded up to 16 bytes) and K cosines.
+size_t gp_smem_bytes(int W, int S, int Lmax, long long K) {
+  const size_t rmax = (size_t)((64 * W + S - 1) / S);
+  const size_t recs = (6 * rmax * (size_t)S * sizeof(float) + 15) / 16 * 16;
+  return 2 * (size_t)Lmax * sizeof(float4) + recs + (size_t)K * sizeof(double);
+}
+
+const void* gp_kernel(int W) {
+  switch (W) {
+    case 8: return (const void*)k_step_f32_gp<8>;
+    case 16: return (const void*)k_step_f32_gp<16>;
+    default: return nullptr;
+  }
+}
+
+// Launch K steps of the grid-persistent form as one cooperative grid of G CTAs.
+cudaError_t launch_gp(const StepArgs& a, unsigned* sync, int W, int S, int G, int Lmax, long long K,
+                      cudaStream_t st) {
+  const void* fn = gp_kernel(W);
+  if (!fn) return cudaErrorInvalidValue;
+  GpArgs P{sync, K, S, Lmax};
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)G);
+  cfg.blockDim = dim3((unsigned)(32 * W));
+  cfg.dynamicSmemBytes = gp_smem_bytes(W, S, Lmax, K);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  StepArgs ac = a;
+  void* params[] = {&ac, &P};
+  return cudaLaunchKernelExC(&cfg, fn, params);
+}
+
+// Largest number of co-resident CTAs of the W-warp kernel with S segments of at most
+// Lmax entries and up to max_k steps per launch.  The kernel's dynamic shared-memory
+// limit is raised to the largest launch any handle may make (segments of max_lmax
+// entries), so handles coexist.
+int gp_max_ctas(int W, int S, int Lmax, int max_lmax, long long max_k, int sms) {
+  const void* fn = gp_kernel(W);
+  if (!fn || Lmax > max_lmax || S < 1) return 0;
+  const size_t smem = gp_smem_bytes(W, S, Lmax, max_k);
+  // ceil(64 W / S) S < 128 W
+  const size_t limit = 2 * (size_t)max_lmax * sizeof(float4) + 6 * 128 * (size_t)W * sizeof(float) + 16 +
+                       (size_t)max_k * sizeof(double);
+  if (smem > limit) return 0;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit) != cudaSuccess) return 0;
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, 32 * W, smem) != cudaSuccess) return 0;
+  return per * sms;
+}
+
+}  // namespace it

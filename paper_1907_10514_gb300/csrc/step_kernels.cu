@@ -82,49 +82,6 @@ __device__ __forceinline__ void finish_iblock(const StepArgs& A, long long ns) {
   }
 }
 
-__device__ __forceinline__ double force_time_cos(const StepArgs& A, long long ns) {
-  const long long nf = (A.mode == MODE_STEP) ? ns + 1 : ns;
-  if (A.trap.flags & (IONTRAP_RF_OFF | IONTRAP_TRAP_OFF)) return 0.0;
-  return cos(A.trap.Omega * ((double)nf * A.trap.dt));
-}
-
-// Split partials are stored as one 32-byte record per (split, ion):
-//   FP32 form: float[8] = (sum_x, sum_y, sum_z, 0, comp_x, comp_y, comp_z, 0)
-//   FP64 form: double[4] = (sum_x, sum_y, sum_z, 0)
-// at record index split * n + i.  The merge runs in split order: FP32 form by
-// compensated (Kahan) addition of the (sum, compensation) pairs -- the accumulators hold
-// the negated sum, hence the sign -- FP64 form by a plain FP64 sum.
-__device__ __forceinline__ void kahan_merge(float& s, float& cc, float ps, float pc) {
-  const float y = ps - cc;
-  const float t = s + y;
-  cc = ((t - s) - y) + pc;
-  s = t;
-}
-
-__device__ __forceinline__ void merge_f32(const float4* __restrict__ part, long long n, long long i, int nsplit,
-                                          double S[3]) {
-  float s[3] = {0.f, 0.f, 0.f}, cc[3] = {0.f, 0.f, 0.f};
-  constexpr int U = 4;
-  for (int p0 = 0; p0 < nsplit; p0 += U) {
-    float4 a[U], b[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (p0 + u < nsplit) {
-        a[u] = __ldcg(part + 2 * ((p0 + u) * n + i));
-        b[u] = __ldcg(part + 2 * ((p0 + u) * n + i) + 1);
-      }
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (p0 + u < nsplit) {
-        kahan_merge(s[0], cc[0], a[u].x, b[u].x);
-        kahan_merge(s[1], cc[1], a[u].y, b[u].y);
-        kahan_merge(s[2], cc[2], a[u].z, b[u].z);
-      }
-  }
-#pragma unroll
-  for (int c = 0; c < 3; ++c) S[c] = (double)cc[c] - (double)s[c];
-}
-
 __device__ __forceinline__ void merge_f64(const double4_32a* __restrict__ part, long long n, long long i,
                                           int nsplit, double S[3]) {
   double s[3] = {0.0, 0.0, 0.0};
@@ -203,10 +160,17 @@ __device__ __forceinline__ bool pair_sums(const StepArgs& A, float4 (&sh)[2][kCh
             nxl2[k][d] = make_float2(nxl[2 * k][d], nxl[2 * k + 1][d]);
             acc2[k][d] = make_float2(0.0f, 0.0f);
           }
-        if (diag)
-          segment_f32x2<I, true>(sh[b], sl[b], jn, jc, nxh2, nxl2, ii, acc2);
-        else
-          segment_f32x2<I, false>(sh[b], sl[b], jn, jc, nxh2, nxl2, ii, acc2);
+        if (A.unitw) {
+          if (diag)
+            segment_f32x2<I, true, true>(sh[b], sl[b], jn, jc, nxh2, nxl2, ii, acc2);
+          else
+            segment_f32x2<I, false, true>(sh[b], sl[b], jn, jc, nxh2, nxl2, ii, acc2);
+        } else {
+          if (diag)
+            segment_f32x2<I, true>(sh[b], sl[b], jn, jc, nxh2, nxl2, ii, acc2);
+          else
+            segment_f32x2<I, false>(sh[b], sl[b], jn, jc, nxh2, nxl2, ii, acc2);
+        }
 #pragma unroll
         for (int k = 0; k < I / 2; ++k)
 #pragma unroll
@@ -219,10 +183,17 @@ __device__ __forceinline__ bool pair_sums(const StepArgs& A, float4 (&sh)[2][kCh
         for (int k = 0; k < I; ++k)
 #pragma unroll
           for (int d = 0; d < 3; ++d) acc[k][d] = 0.0f;
-        if (diag)
-          segment_f32<I, true>(sh[b], sl[b], jn, jc, nxh, nxl, ii, acc);
-        else
-          segment_f32<I, false>(sh[b], sl[b], jn, jc, nxh, nxl, ii, acc);
+        if (A.unitw) {
+          if (diag)
+            segment_f32<I, true, true>(sh[b], sl[b], jn, jc, nxh, nxl, ii, acc);
+          else
+            segment_f32<I, false, true>(sh[b], sl[b], jn, jc, nxh, nxl, ii, acc);
+        } else {
+          if (diag)
+            segment_f32<I, true>(sh[b], sl[b], jn, jc, nxh, nxl, ii, acc);
+          else
+            segment_f32<I, false>(sh[b], sl[b], jn, jc, nxh, nxl, ii, acc);
+        }
       }
       // Kahan: value = ks - kc
 #pragma unroll
@@ -526,10 +497,17 @@ __global__ void __launch_bounds__(32 * W) k_step_f32_cw(const __grid_constant__ 
             nxl2[k2][d] = make_float2(nxl[2 * k2][d], nxl[2 * k2 + 1][d]);
             acc2[k2][d] = make_float2(0.0f, 0.0f);
           }
-        if (diag)
-          segment_f32x2<I, true>(csh, csl, jn, jc, nxh2, nxl2, ii, acc2);
-        else
-          segment_f32x2<I, false>(csh, csl, jn, jc, nxh2, nxl2, ii, acc2);
+        if (A.unitw) {
+          if (diag)
+            segment_f32x2<I, true, true>(csh, csl, jn, jc, nxh2, nxl2, ii, acc2);
+          else
+            segment_f32x2<I, false, true>(csh, csl, jn, jc, nxh2, nxl2, ii, acc2);
+        } else {
+          if (diag)
+            segment_f32x2<I, true>(csh, csl, jn, jc, nxh2, nxl2, ii, acc2);
+          else
+            segment_f32x2<I, false>(csh, csl, jn, jc, nxh2, nxl2, ii, acc2);
+        }
 #pragma unroll
         for (int k2 = 0; k2 < I / 2; ++k2)
 #pragma unroll
@@ -542,10 +520,17 @@ __global__ void __launch_bounds__(32 * W) k_step_f32_cw(const __grid_constant__ 
         for (int k2 = 0; k2 < I; ++k2)
 #pragma unroll
           for (int d = 0; d < 3; ++d) acc[k2][d] = 0.0f;
-        if (diag)
-          segment_f32<I, true>(csh, csl, jn, jc, nxh, nxl, ii, acc);
-        else
-          segment_f32<I, false>(csh, csl, jn, jc, nxh, nxl, ii, acc);
+        if (A.unitw) {
+          if (diag)
+            segment_f32<I, true, true>(csh, csl, jn, jc, nxh, nxl, ii, acc);
+          else
+            segment_f32<I, false, true>(csh, csl, jn, jc, nxh, nxl, ii, acc);
+        } else {
+          if (diag)
+            segment_f32<I, true>(csh, csl, jn, jc, nxh, nxl, ii, acc);
+          else
+            segment_f32<I, false>(csh, csl, jn, jc, nxh, nxl, ii, acc);
+        }
       }
 #pragma unroll
       for (int k2 = 0; k2 < I; ++k2)

@@ -88,15 +88,42 @@ def test_forces_match_oracle(it, n):
                                  (32, 1, 0, 376, 2), (64, 1, 0, 501, 2), (128, 4, 1, 1001, 2), (32, 2, 1, 3001, 2),
                                  (64, 1, 0, 501, 3), (128, 2, 1, 1001, 3), (128, 1, 0, 376, 3), (64, 2, 1, 3001, 3),
                                  (64, 2, 1, 200, 3), (64, 1, 0, 188, 3)])
-def test_forces_every_tile_config(it, cfg):
+@pytest.mark.parametrize("unit", [False, True], ids=["z_mixed", "z_unit"])
+def test_forces_every_tile_config(it, cfg, unit):
     n = 3001
-    w = _cloud(n, 5)
+    w = _cloud(n, 5, species=(iongen.CA40, iongen.NH3)) if unit else _cloud(n, 5)
     q, m, _ = _oracle_side(w)
     ref = oracle.coulomb_accel(w.x0, q, m)
     with _sim(it, w, it.IONTRAP_PREC_FP32) as sim:
         sim.set_config(*cfg)
         assert sim.config()[:5] == cfg
         assert rel_rms(sim.forces(), ref) < FP32_FORCE_TOL
+
+
+def test_unit_charge_path_is_bitwise_equal_to_general_path(it):
+    """Singly charged ions take the pair loop without the z_j product; listing an unused
+    doubly charged species forces the general loop on the same physics: same bits."""
+    n = 1500
+    w = _cloud(n, 21, species=(iongen.CA40, iongen.NH3))
+    w2 = iongen.Workload(w.name, list(w.species) + [iongen.Species(88.0, 2.0)], w.species_of_ion, w.x0, w.v0,
+                         w.trap, w.steps)
+    for prec in (it.IONTRAP_PREC_FP32, it.IONTRAP_PREC_FP64):
+        out = []
+        for ww in (w, w2):
+            with _sim(it, ww, prec) as sim:
+                f = sim.forces()
+                sim.step(20)
+                x, v, _, _ = sim.state()
+            out.append((f, x, v))
+        for a, b in zip(*out):
+            assert np.array_equal(a, b), prec
+    many = []
+    for ww in (w, w2):
+        sims = [_sim(it, ww, it.IONTRAP_PREC_FP32)]
+        it.iontrap_step_many([sims[0].handle], [20])
+        many.append(sims[0].state()[0])
+        sims[0].close()
+    assert np.array_equal(many[0], many[1])
 
 
 def test_forces_maximum_size_sampled(it):
@@ -392,6 +419,91 @@ def test_cluster_forms_trajectory_matches_oracle(it, cfg):
         sim.step(100)
         x, v, step, _ = sim.state()
     assert step == 100 and rel_rms(x, xo) < FP32_TRAJ_TOL and rel_rms(v, vo) < 10 * FP32_TRAJ_TOL
+
+
+# ------------------------------------------------------------------ grid-persistent form
+
+def _gp_cfg(n, W, S):
+    return (32 * W, 2, 1, -(-n // S), 4)
+
+
+@pytest.mark.parametrize("n,W,S,steps", [(700, 8, 7, 100), (1000, 8, 19, 100), (2049, 16, 50, 100),
+                                         (3000, 8, 25, 100), (4096, 16, 38, 100), (5000, 16, 30, 100),
+                                         (9000, 16, 16, 40)])
+def test_persistent_form_trajectory_matches_oracle(it, n, W, S, steps):
+    """The grid-persistent form (one cooperative launch for many steps, the owners' FP64
+    state in registers) against the oracle, on ragged ion counts and on group and
+    segment splits of every shape."""
+    w = _cloud(n, 600 + n)
+    q, m, p = _oracle_side(w)
+    xo, vo, _ = oracle.run(w.x0, w.v0, q, m, p, steps)
+    with _sim(it, w, 0) as sim:
+        sim.set_config(*_gp_cfg(n, W, S))
+        assert sim.config()[4] == 4
+        sim.step(steps)
+        x, v, step, _ = sim.state()
+    assert step == steps and rel_rms(x, xo) < FP32_TRAJ_TOL and rel_rms(v, vo) < 10 * FP32_TRAJ_TOL
+
+
+def test_persistent_form_bitwise_across_launches_and_restore(it):
+    """Splitting a run into launches (the owners reload their state at each launch) gives
+    the bits of one launch, a 1250-step call (two launches) included; a checkpoint
+    restored into a second handle continues bit for bit; iontrap_forces through the
+    persistent kernel agrees with the last-CTA form and with the oracle."""
+    n = 2500
+    w = _cloud(n, 31)
+    cfg = _gp_cfg(n, 16, 50)
+    with _sim(it, w, 0) as a, _sim(it, w, 0) as b, _sim(it, w, 0) as c:
+        for s in (a, b, c):
+            s.set_config(*cfg)
+        a.step(1250)
+        b.step(7)
+        b.step(600)
+        b.step(643)
+        for _ in range(50):
+            c.step(1)
+        c.step(1200)
+        xa, va, sa, _ = a.state()
+        for s in (b, c):
+            x, v, st, _ = s.state()
+            assert st == sa == 1250
+            assert np.array_equal(x, xa) and np.array_equal(v, va)
+        xk, vk, ak, sk = a.checkpoint()
+        with _sim(it, w, 0) as d:
+            d.set_config(*cfg)
+            d.restore(xk, vk, ak, sk)
+            a.step(100)
+            d.step(100)
+            xa, va, _, _ = a.state()
+            xd, vd, _, _ = d.state()
+            assert np.array_equal(xa, xd) and np.array_equal(va, vd)
+            f4 = d.forces()
+            xd = d.state()[0]
+            d.set_config(128, 2, 1, cfg[3], 1)
+            f1 = d.forces()
+    q, m, _ = _oracle_side(w)
+    ref = oracle.coulomb_accel(xd, q, m)
+    assert rel_rms(f4, f1) < 1e-6 and rel_rms(f4, ref) < FP32_FORCE_TOL
+
+
+def test_persistent_form_rejects_invalid_shapes(it):
+    w = _cloud(3000, 5)
+    with _sim(it, w, 0) as sim:
+        for cfg in [(128, 2, 1, 1500, 4),    # 4 warps: not a persistent shape
+                    (512, 1, 0, 100, 4),     # one ion per lane
+                    (512, 2, 1, 3000, 4),    # a single segment
+                    (512, 2, 1, 500, 4),     # 6 segments: 171 ions per CTA, 3 x 171 > 512 threads
+                    (512, 2, 1, 10, 4),      # 3 groups x 300 segments: more CTAs than fit
+                    (256, 2, 1, 0, 4)]:
+            with pytest.raises(it.IonTrapError):
+                sim.set_config(*cfg)
+        assert sim.config()[4] != 4
+    with _sim(it, w, it.IONTRAP_PREC_FP64) as sim:
+        with pytest.raises(it.IonTrapError):
+            sim.set_config(*_gp_cfg(3000, 16, 30))
+    with _sim(it, w, 0, flags=it.IONTRAP_COULOMB_OFF) as sim:
+        with pytest.raises(it.IonTrapError):
+            sim.set_config(*_gp_cfg(3000, 16, 30))
 
 
 def test_batched_then_single_continue_consistently(it):
