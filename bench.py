@@ -47,9 +47,17 @@ def ops_per_pair(species):
 FP32_LANES_PER_SM = 128
 MUFU_PER_SM = 16
 NOMINAL_SM_MHZ = 2070.0
-# DRAM bytes (read + write) per launch of the step kernel, from the ncu capture summarised
-# in profiles/step_f32_cw_mix_n4096.md; valid only for that launch configuration.
-PROFILED_TRAFFIC = {(128, 2, 1, 512, 3): 485376 + 0}
+# DRAM bytes (read + write) per timestep of the step kernel, from the ncu captures
+# summarised in profiles/; valid only for that launch configuration.
+PROFILED_TRAFFIC = {
+    # one launch per timestep (profiles/step_f32_cw_mix_n4096.md)
+    (128, 2, 1, 512, 3): (485376 + 0, "DRAM bytes per timestep launch (ncu, profiles/step_f32_cw_mix_n4096.md)"),
+    # grid-persistent form: a 20-timestep launch read 496 896 B and wrote 113 152 B
+    (512, 2, 1, 108, 4): ((496896 + 113152) / 20, "DRAM bytes per timestep, from a 20-timestep launch of the "
+                                                  "persistent kernel (ncu, profiles/step_f32_gp_mix_n4096.md)"),
+}
+# timesteps per cooperative launch of the grid-persistent form (include/iontrap.h)
+GP_STEPS_PER_LAUNCH = 1000
 
 
 def _dist():
@@ -304,15 +312,15 @@ def run_gpu(args):
                       "(bar 1e-5); trajectories: tests/test_gpu_parity.py",
         "e2e": {"value": e2e_value, "unit": "ion-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": args.steps * nsteps,
+        "gpu_launches": args.steps * (-(-nsteps // GP_STEPS_PER_LAUNCH) if cfg[4] == 4 else nsteps),
         "roofline": {"bound": "alu", "achieved": achieved_gpairs, "peak": peak_gpairs,
                      "unit": "Gpair/s", "frac": achieved_gpairs / peak_gpairs,
-                     "traffic": PROFILED_TRAFFIC.get(tuple(cfg[:5])),
-                     "traffic_unit": "DRAM bytes per launch (ncu, profiles/step_f32_cw_mix_n4096.md)",
+                     "traffic": PROFILED_TRAFFIC.get(tuple(cfg[:5]), (None, None))[0],
+                     "traffic_unit": PROFILED_TRAFFIC.get(tuple(cfg[:5]), (None, "not profiled for this tile"))[1],
                      "basis": f"{sms} SMs x {NOMINAL_SM_MHZ:.0f} MHz x {FP32_LANES_PER_SM} FP32 lanes / "
                               f"{opp} FP32 instr per ordered pair (MUFU roof "
-                              f"{MUFU_PER_SM}/clk/SM not binding); achieved = N(N-1) per launch / "
-                              "mean launch time over the timed region",
+                              f"{MUFU_PER_SM}/clk/SM not binding); achieved = N(N-1) per timestep / "
+                              "mean time per timestep over the timed region",
                      "peak_source": "derived from SM count, nominal max SM clock and FP32 lane count",
                      "hbm_peak_gbs_measured": peaks.get("hbm_gbs")},
         "clocks": clk.summary(),

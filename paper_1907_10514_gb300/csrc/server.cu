@@ -26,6 +26,10 @@
 
 #include "iontrap.h"
 
+namespace it {
+int use_nonpersistent_default(iontrap_t* h);  // iontrap_api.cu
+}
+
 namespace {
 
 struct Event {
@@ -183,6 +187,7 @@ int iontrap_server_poll(iontrap_server_t* s, int64_t* completed_ids, int64_t cap
     if (!r->status)
       r->status = iontrap_create(r->species.data(), (int)r->species.size(), r->soi.data(), r->x0.data(),
                                  r->has_v0 ? r->v0.data() : nullptr, r->n, &r->p, 0, (void*)st, &r->h);
+    if (!r->status && !r->batched) r->status = it::use_nonpersistent_default(r->h);
     if (r->status) {  // rejected (unstable trap, bad input, no memory): completes at once
       if (r->own) cudaStreamDestroy(r->own);
       r->own = nullptr;

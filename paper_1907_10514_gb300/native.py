@@ -96,6 +96,8 @@ SIGNATURES = {
                                        ctypes.c_int, _dp]),
     "iontrap_get_config": (ctypes.c_int, [_vp, ctypes.POINTER(iontrap_config)]),
     "iontrap_set_config": (ctypes.c_int, [_vp, ctypes.POINTER(iontrap_config)]),
+    "iontrap_default_config": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.c_uint32, ctypes.c_int,
+                                              ctypes.POINTER(iontrap_config)]),
     "iontrap_forces_noalloc": (ctypes.c_int, [ctypes.POINTER(iontrap_species), ctypes.c_int, _vp, _vp,
                                               ctypes.c_int64, _vp, _vp]),
     "iontrap_device_bytes": (ctypes.c_int, [_vp, _i64p]),
@@ -278,6 +280,15 @@ def iontrap_get_config(h):
     """Returns (threads, ions_per_thread, packed, jsplit, fused, pdl, graph)."""
     c = iontrap_config()
     _check(_lib.iontrap_get_config(h, ctypes.byref(c)), "iontrap_get_config")
+    return c.threads, c.ions_per_thread, c.packed, c.jsplit, c.fused, c.pdl, c.graph
+
+
+def iontrap_default_config(n: int, precision: int = IONTRAP_PREC_FP32, flags: int = 0,
+                           allow_persistent: int = 1):
+    """Returns (threads, ions_per_thread, packed, jsplit, fused, pdl, graph)."""
+    c = iontrap_config()
+    _check(_lib.iontrap_default_config(int(n), int(precision), int(flags), int(allow_persistent), ctypes.byref(c)),
+           "iontrap_default_config")
     return c.threads, c.ions_per_thread, c.packed, c.jsplit, c.fused, c.pdl, c.graph
 
 
