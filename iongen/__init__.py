@@ -71,6 +71,16 @@ class Trap:
 
 
 @dataclasses.dataclass
+class Cooling:
+    """Cooling of one species (Sec. 3, "Cooling the motion of ions"): its Langevin
+    bath (rate 1/dampingTime in 1/s, temperature in K; gamma 0 = no bath) and its
+    laser-cooling vector in 1/s (zero vector = no laser).  Plain data."""
+    gamma: float = 0.0
+    T_bath: float = 0.0
+    laser: tuple = (0.0, 0.0, 0.0)
+
+
+@dataclasses.dataclass
 class Workload:
     name: str
     species: List[Species]

@@ -10,6 +10,8 @@ Functions follow the paper:
   * ``trap_accel``     -- linear Paul trap field, Eq. 1 in the Mathieu form of Eq. 3
   * ``normals``        -- Langevin kicks (Sec. 3, "Cooling the motion of ions") from
                           Philox-4x64-10 + Box-Muller
+  * ``cooling_arrays`` -- per-species baths and laser cooling (Sec. 3, langevinBath
+                          on a group, laserCool) as per-ion arrays for ``accel``/``run``
   * ``run``            -- velocity-Verlet time evolution (Sec. 6 "Integration", "nve")
   * ``energy``         -- Eq. 4 energy for a static trap
   * ``stable``         -- discrete-Verlet Floquet stability of a single ion (|tr M| < 2)
@@ -81,6 +83,10 @@ def lib():
                                    ctypes.c_double, dp]
         L.oracle_run.argtypes = [ctypes.c_int64, dp, dp, dp, dp, dp, pp, ctypes.c_int64,
                                  ctypes.c_int64, ctypes.c_int, dp]
+        L.oracle_accel_cool.argtypes = [ctypes.c_int64, dp, dp, dp, dp, pp, ctypes.c_int64,
+                                        ctypes.c_double, dp, dp, dp, dp]
+        L.oracle_run_cool.argtypes = [ctypes.c_int64, dp, dp, dp, dp, dp, pp, ctypes.c_int64,
+                                      ctypes.c_int64, ctypes.c_int, dp, dp, dp, dp]
         L.oracle_energy.restype = ctypes.c_double
         L.oracle_energy.argtypes = [ctypes.c_int64, dp, dp, dp, dp, pp]
         _lib = L
@@ -172,23 +178,51 @@ def trap_accel(p: _Params, qm: float, r, t: float) -> np.ndarray:
     return out
 
 
-def accel(x, udrag, charge, mass, p: _Params, counter: int, t: float) -> np.ndarray:
+def cooling_arrays(species_of_ion, coolings):
+    """Per-ion cooling arrays (gamma[n], T_bath[n], laser[3][n]) from one cooling
+    description per species (objects with ``gamma``, ``T_bath`` and ``laser``): a bath or
+    laser applied to a species applies to every ion of it (Sec. 3, langevinBath(T,
+    dampingTime, group) and laserCool(species, gamma))."""
+    sp = np.asarray(species_of_ion, dtype=np.int64)
+    g = np.array([float(c.gamma) for c in coolings])
+    T = np.array([float(c.T_bath) for c in coolings])
+    L = np.array([[float(u) for u in c.laser] for c in coolings]).reshape(-1, 3)
+    return _c64(g[sp]), _c64(T[sp]), _c64(L[sp].T)
+
+
+def _cool_ptrs(cooling):
+    if cooling is None:
+        return None, None, None, ()
+    g, T, L = (_c64(a) for a in cooling)
+    return _dp(g), _dp(T), _dp(L), (g, T, L)
+
+
+def accel(x, udrag, charge, mass, p: _Params, counter: int, t: float, cooling=None) -> np.ndarray:
+    """Acceleration of every ion; ``cooling`` = (gamma[n], T_bath[n], laser[3][n]) per
+    ion (see ``cooling_arrays``), or None for the bath of ``p`` and no laser."""
     x, udrag = _c64(x), _c64(udrag)
     acc = np.empty_like(x)
-    lib().oracle_accel(x.shape[1], _dp(x), _dp(udrag), _dp(_c64(charge)), _dp(_c64(mass)),
-                       ctypes.byref(p), int(counter), float(t), _dp(acc))
+    gp, tp, lp, keep = _cool_ptrs(cooling)
+    lib().oracle_accel_cool(x.shape[1], _dp(x), _dp(udrag), _dp(_c64(charge)), _dp(_c64(mass)),
+                            ctypes.byref(p), int(counter), float(t), gp, tp, lp, _dp(acc))
+    del keep
     return acc
 
 
-def run(x0, v0, charge, mass, p: _Params, nsteps: int, step0: int = 0, a0=None):
+def run(x0, v0, charge, mass, p: _Params, nsteps: int, step0: int = 0, a0=None, cooling=None):
     """Velocity-Verlet evolution.  Returns (x, v, a) after ``nsteps`` steps.  With
-    ``a0`` None the initial acceleration is evaluated first."""
+    ``a0`` None the initial acceleration is evaluated first (at t = step0 dt, drag on
+    v0, noise counter step0) -- which is also how the forces change between two runs
+    (interleaved evolve, Sec. 3 "Time evolution").  ``cooling`` as for ``accel``."""
     x, v = _c64(x0).copy(), _c64(v0).copy()
     n = x.shape[1]
     a = np.zeros_like(x) if a0 is None else _c64(a0).copy()
     work = np.empty_like(x)
-    lib().oracle_run(n, _dp(x), _dp(v), _dp(a), _dp(_c64(charge)), _dp(_c64(mass)),
-                     ctypes.byref(p), int(step0), int(nsteps), int(a0 is None), _dp(work))
+    gp, tp, lp, keep = _cool_ptrs(cooling)
+    lib().oracle_run_cool(n, _dp(x), _dp(v), _dp(a), _dp(_c64(charge)), _dp(_c64(mass)),
+                          ctypes.byref(p), int(step0), int(nsteps), int(a0 is None), gp, tp, lp,
+                          _dp(work))
+    del keep
     return x, v, a
 
 

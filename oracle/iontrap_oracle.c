@@ -12,8 +12,14 @@
  *                                              of the pair term), direct sum, Sec. 6
  *                                              "Interactions" (brute force, no cutoff)
  *         + trap_i(x_i, t)                     Eq. 1 in the Mathieu a/q form of Eq. 3
- *         - gamma u_i + sigma_i xi_i(n)        Langevin bath, Sec. 3 "Cooling the
- *                                              motion of ions" (gamma = 1/dampingTime)
+ *         - gamma_i u_i + sigma_i xi_i(n)      Langevin bath, Sec. 3 "Cooling the
+ *                                              motion of ions" (gamma = 1/dampingTime;
+ *                                              a bath may act on a group of ions only,
+ *                                              so gamma_i and T_i are per ion)
+ *         - |g_i| (g^_i . u_i) g^_i            laser cooling laserCool(species, g),
+ *                                              Sec. 3 "Cooling the motion of ions": a
+ *                                              viscous force along the beam direction
+ *                                              g^ = g/|g| at rate |g| (1/s), no kicks
  *
  *   trap_i for an ion whose charge/mass is rho times that of the reference species:
  *     x: -(Omega^2/4)(rho a - 2 rho q cos Omega t) x + (rho omega_z^2 / 2) x
@@ -22,7 +28,7 @@
  *   (q_x = -q_y = q, Eq. 3; a and q scale with Q/M, Eq. 3; the static axial field
  *    confines along z and defocuses radially by half its strength, Eq. 1 and 3.)
  *
- *   sigma_i = sqrt(2 gamma k_B T / (M_i dt)); xi = three standard normals drawn by
+ *   sigma_i = sqrt(2 gamma_i k_B T_i / (M_i dt)); xi = three standard normals drawn by
  *   Box-Muller from Philox-4x64-10 (Salmon et al., SC'11) with key (seed, 0) and
  *   counter (n, i, 0, 0), on the uniforms (top 23 bits + 1/2) 2^-23.
  *
@@ -213,9 +219,17 @@ void oracle_trap_accel(const oracle_params *p, double qm, const double r[3], dou
 }
 
 /* ------------------------------------------------------------- full acceleration */
-void oracle_accel(int64_t n, const double *x, const double *udrag, const double *charge,
-                  const double *mass, const oracle_params *p, int64_t counter, double t,
-                  double *acc)
+/* Per-ion cooling (any pointer may be NULL):
+ *   gamma[n], T_bath[n]  Langevin rate (1/s) and bath temperature (K) of each ion's bath;
+ *                        NULL: every ion in the bath of p (p->gamma, p->T_bath)
+ *   laser[3][n]          laser-cooling vector g of each ion (1/s, SoA; zero vector = no
+ *                        laser); NULL: no laser cooling
+ * A bath restricted to a group (langevinBath(T, dampingTime, group)) is a group whose
+ * ions carry that bath's (gamma, T) and the others (0, 0). */
+void oracle_accel_cool(int64_t n, const double *x, const double *udrag, const double *charge,
+                       const double *mass, const oracle_params *p, int64_t counter, double t,
+                       const double *gamma, const double *T_bath, const double *laser,
+                       double *acc)
 {
     if (p->flags & ORC_COULOMB_OFF) {
         for (int64_t k = 0; k < 3 * n; ++k) acc[k] = 0.0;
@@ -225,27 +239,54 @@ void oracle_accel(int64_t n, const double *x, const double *udrag, const double 
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         double r[3] = {x[i], x[n + i], x[2 * n + i]};
+        double u[3] = {udrag[i], udrag[n + i], udrag[2 * n + i]};
         double tr[3];
         oracle_trap_accel(p, charge[i] / mass[i], r, t, tr);
-        double sigma = sqrt(2.0 * p->gamma * ORC_KB * p->T_bath / (mass[i] * p->dt));
+        double g_i = gamma ? gamma[i] : p->gamma;
+        double T_i = gamma ? T_bath[i] : p->T_bath;
+        double sigma = sqrt(2.0 * g_i * ORC_KB * T_i / (mass[i] * p->dt));
         double xi[3] = {0.0, 0.0, 0.0};
         if (sigma > 0.0) oracle_normals(p->seed, counter, i, xi);
+        /* laser: -|g| (g^ . u) g^ with g^ = g / |g| */
+        double las[3] = {0.0, 0.0, 0.0};
+        if (laser) {
+            double g[3] = {laser[i], laser[n + i], laser[2 * n + i]};
+            double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+            if (gn > 0.0) {
+                double khat[3] = {g[0] / gn, g[1] / gn, g[2] / gn};
+                double proj = khat[0] * u[0] + khat[1] * u[1] + khat[2] * u[2];
+                for (int c = 0; c < 3; ++c) las[c] = -gn * proj * khat[c];
+            }
+        }
         for (int c = 0; c < 3; ++c) {
-            double lang = -p->gamma * udrag[c * n + i] + sigma * xi[c];
-            acc[c * n + i] += tr[c] + lang;
+            double lang = -g_i * u[c] + sigma * xi[c];
+            acc[c * n + i] += tr[c] + lang + las[c];
         }
     }
+}
+
+void oracle_accel(int64_t n, const double *x, const double *udrag, const double *charge,
+                  const double *mass, const oracle_params *p, int64_t counter, double t,
+                  double *acc)
+{
+    oracle_accel_cool(n, x, udrag, charge, mass, p, counter, t, NULL, NULL, NULL, acc);
 }
 
 /* ------------------------------------------------------------ velocity Verlet run */
 /* Advances (x, v, a) in place by nsteps from step index step0.  With init != 0 it
  * first evaluates a_0 at (x_0, t = step0 dt) with v_0 as the drag velocity. */
-void oracle_run(int64_t n, double *x, double *v, double *a, const double *charge,
-                const double *mass, const oracle_params *p, int64_t step0, int64_t nsteps,
-                int init, double *work /* 3n doubles of scratch */)
+/* Changing the forces between two runs (interleaved evolve, Sec. 3 "Time evolution")
+ * is a second call with the new parameters and init != 0: a_n is re-evaluated under the
+ * new forces at (x_n, t = n dt), with v_n as the drag velocity and noise counter n. */
+void oracle_run_cool(int64_t n, double *x, double *v, double *a, const double *charge,
+                     const double *mass, const oracle_params *p, int64_t step0, int64_t nsteps,
+                     int init, const double *gamma, const double *T_bath, const double *laser,
+                     double *work /* 3n doubles of scratch */)
 {
     const double dt = p->dt;
-    if (init) oracle_accel(n, x, v, charge, mass, p, step0, (double)step0 * dt, a);
+    if (init)
+        oracle_accel_cool(n, x, v, charge, mass, p, step0, (double)step0 * dt, gamma, T_bath,
+                          laser, a);
     for (int64_t s = 0; s < nsteps; ++s) {
         int64_t step = step0 + s;
         double *vh = work;
@@ -253,9 +294,17 @@ void oracle_run(int64_t n, double *x, double *v, double *a, const double *charge
             vh[k] = v[k] + 0.5 * dt * a[k];
             x[k] = x[k] + dt * vh[k];
         }
-        oracle_accel(n, x, vh, charge, mass, p, step + 1, (double)(step + 1) * dt, a);
+        oracle_accel_cool(n, x, vh, charge, mass, p, step + 1, (double)(step + 1) * dt, gamma,
+                          T_bath, laser, a);
         for (int64_t k = 0; k < 3 * n; ++k) v[k] = vh[k] + 0.5 * dt * a[k];
     }
+}
+
+void oracle_run(int64_t n, double *x, double *v, double *a, const double *charge,
+                const double *mass, const oracle_params *p, int64_t step0, int64_t nsteps,
+                int init, double *work /* 3n doubles of scratch */)
+{
+    oracle_run_cool(n, x, v, a, charge, mass, p, step0, nsteps, init, NULL, NULL, NULL, work);
 }
 
 /* ------------------------------------------------------------------------ energy */
