@@ -7,25 +7,31 @@
  *   - species defined by charge (units of e) and mass (amu)   Sec. 3 "Adding ions"
  *   - ions placed at given coordinates, ids = index order      Sec. 3 "Adding ions"
  *   - linear Paul trap, full RF field, Mathieu a/q form         Eq. 1, Eq. 3, Sec. 3 "Forces and fields"
- *   - Langevin bath langevinBath(T, dampingTime)                Sec. 3 "Cooling the motion of ions"
+ *   - Langevin bath langevinBath(T, dampingTime[, group])       Sec. 3 "Cooling the motion of ions"
+ *   - laser cooling laserCool(species, gamma)                    Sec. 3 "Cooling the motion of ions"
+ *   - forces changed between evolve calls                        Sec. 3 "Time evolution"
  *   - all-pairs Coulomb interaction, no cutoff                  Eq. 4, Sec. 6 "Interactions"
  *   - evolve(N): N steps of the "nve" integrator                Sec. 3 "Time evolution", Sec. 6 "Integration"
  *   - positions and velocities read back in id order            Sec. 3 "Writing/reading data"
- *   - a simulation's parameters are immutable once it runs      Sec. 3 "Execution"
+ *   - parameters change only between evolve calls              Sec. 3 "Time evolution", "Execution"
  *
  * One step (index n -> n+1), for every ion i with charge number z_i and mass M_i:
  *   v_half  = v_n + dt/2 a_n
  *   x_{n+1} = x_n + dt v_half
  *   a_{n+1} = (k_e e^2 z_i / M_i) sum_{j != i} z_j (x_i - x_j) / |x_i - x_j|^3
- *           + trap_i(x_{n+1}, t_{n+1}) - gamma v_half + sigma_i xi_i(n+1)
+ *           + trap_i(x_{n+1}, t_{n+1}) - gamma_s v_half + sigma_i xi_i(n+1)
+ *           - |g_s| (g^_s . v_half) g^_s
  *   v_{n+1} = v_half + dt/2 a_{n+1}
  * with, for an ion whose charge/mass is rho times that of species 0 (c = cos Omega t):
  *   trap_x = -(Omega^2/4) rho (a - 2 q c) x + (rho omega_z^2 / 2) x
  *   trap_y = -(Omega^2/4) rho (a + 2 q c) y + (rho omega_z^2 / 2) y
  *   trap_z = -rho omega_z^2 z
- *   sigma_i = sqrt(2 gamma k_B T / (M_i dt)),  xi = 3 normals from Philox-4x64-10
+ *   sigma_i = sqrt(2 gamma_s k_B T_s / (M_i dt)),  xi = 3 normals from Philox-4x64-10
  *   (key (seed, 0), counter (n+1, i, 0, 0)) by Box-Muller on the uniforms
  *   (top 23 bits of each 64-bit word + 1/2) 2^-23.
+ * where (gamma_s, T_s) is the Langevin bath and g_s the laser-cooling vector of ion i's
+ * species s (g^ = g/|g|; by default every species is in the bath of iontrap_params and
+ * none is laser-cooled, see iontrap_set_params).
  * a_{n0} is evaluated at create time from (x_{n0}, t = n0 dt) with v_{n0} as drag.
  *
  * Layout: every per-ion array is SoA, [3][n] doubles (x block, then y, then z), in
@@ -112,6 +118,34 @@ int iontrap_create(const iontrap_species *species, int n_species,
  * 100 steps plus single launches).  Returns the handle's sticky status. */
 int iontrap_step(iontrap_t *h, int64_t n_steps);
 
+/* Cooling of one species (Sec. 3 "Cooling the motion of ions").  A Langevin bath
+ * langevinBath(T, dampingTime, group) with the group one species: drag -gamma v and
+ * Gaussian kicks of variance 2 gamma k_B T / (M dt) per component and step.  Laser cooling
+ * laserCool(species, g): a viscous force along the beam, acceleration -|g| (g^.v) g^ with
+ * g^ = g/|g|, no kicks (the paper writes the force as -M (g.v) g; its examples give g as a
+ * rate in 1/s times a direction, which is the reading taken here).  v is the half-step
+ * velocity, as for the bath.  To give a group of ions of one kind a bath of its own,
+ * declare it as a separate species with the same mass and charge. */
+typedef struct {
+    double gamma;     /* bath rate 1/dampingTime, 1/s (0 = no bath) */
+    double T_bath;    /* bath temperature, K */
+    double laser[3];  /* laser-cooling vector g, 1/s (zero vector = no laser cooling) */
+} iontrap_cooling;
+
+/* Change the forces between evolve calls (Sec. 3 "Time evolution": interleaving evolve
+ * with commands that add or remove forces and fields; Sec. 4 Example 2 removes a bath and
+ * laser-cools one species).  From the current state n on, the trap is that of p (Omega,
+ * a, q, omega_z, IONTRAP_RF_OFF / IONTRAP_TRAP_OFF) and species s has the bath and laser of
+ * cooling[s] (cooling[n_species], or NULL: every species in the bath (p->gamma, p->T_bath),
+ * no laser).  The state keeps x_n and v_n; a_n is evaluated again under the new forces
+ * exactly as iontrap_create evaluates it (at t = n dt, drag on v_n, noise counter n), so the
+ * handle continues bit for bit like a handle created from (x_n, v_n) at step0 = n with the
+ * new forces.  dt, seed, precision and IONTRAP_COULOMB_OFF cannot change (EINVAL).
+ * EINVAL on non-finite or negative bath values, EUNSTABLE for a trap that cannot hold a
+ * species (unless IONTRAP_ALLOW_UNSTABLE).  Synchronous: waits for the handle's queued
+ * work first.  Handles advanced by iontrap_step_many use the new forces as well. */
+int iontrap_set_params(iontrap_t *h, const iontrap_params *p, const iontrap_cooling *cooling);
+
 /* Wait for the handle's stream and report device-side failures (ENONFINITE,
  * ETIMEOUT, ECUDA). */
 int iontrap_sync(iontrap_t *h);
@@ -152,6 +186,25 @@ int iontrap_step_many(iontrap_t *const *hs, const int64_t *n_steps, int count);
 
 /* Free the handle's device memory, graph and owned stream.  NULL is a no-op. */
 void iontrap_destroy(iontrap_t *h);
+
+/* The linear Paul trap given by its voltages and geometry, linearPT(V0, U0, R0, Z0,
+ * kappa, Omega) of Sec. 3 "Forces and fields": the field of Eq. 1 expressed through the
+ * Mathieu parameters of Eq. 3 for species0 (charge Q, mass M):
+ *   q = 2 Q V0 / (M R0^2 Omega^2),   omega_z^2 = 2 Q kappa U0 / (M Z0^2),   a = 0.
+ * Eq. 3's a_x = -4 Q kappa U0 / (M Z0^2 Omega^2) is the radial defocusing of the axial dc
+ * field, which this library's trap already applies as +omega_z^2/2 (iontrap_params.a is an
+ * extra dc term on top of it), so a is set to 0.  The dc field is taken as confining along
+ * z: Eq. 1 prints kappa U0/Z0^2 (2z, -x, -y), which pushes a positive ion away from the
+ * centre along z, while Eq. 3 gives a_z > 0 (confinement) for Q kappa U0 > 0.
+ *   V0, U0    ac amplitude and dc (endcap) voltage, V
+ *   R0, Z0    radial and axial characteristic lengths, m (> 0)
+ *   kappa     geometric factor of the dc field
+ *   Omega     RF angular frequency, rad/s (> 0)
+ * Writes p->Omega, p->a, p->q and p->omega_z and leaves the other fields as they are.
+ * EINVAL on non-finite or non-positive lengths / Omega / mass, or Q kappa U0 < 0 (the dc
+ * field would not confine along z).  Host only. */
+int iontrap_linear_pt(double V0, double U0, double R0, double Z0, double kappa, double Omega,
+                      const iontrap_species *species0, iontrap_params *p);
 
 /* Static description of a status code. */
 const char *iontrap_strerror(int status);

@@ -12,6 +12,7 @@ Functions follow the paper:
                           Philox-4x64-10 + Box-Muller
   * ``cooling_arrays`` -- per-species baths and laser cooling (Sec. 3, langevinBath
                           on a group, laserCool) as per-ion arrays for ``accel``/``run``
+  * ``linear_pt``      -- Mathieu parameters of a trap given by voltages (Eq. 3)
   * ``run``            -- velocity-Verlet time evolution (Sec. 6 "Integration", "nve")
   * ``energy``         -- Eq. 4 energy for a static trap
   * ``stable``         -- discrete-Verlet Floquet stability of a single ion (|tr M| < 2)
@@ -230,6 +231,19 @@ def energy(x, v, charge, mass, p: _Params) -> float:
     x, v = _c64(x), _c64(v)
     return float(lib().oracle_energy(x.shape[1], _dp(x), _dp(v), _dp(_c64(charge)),
                                      _dp(_c64(mass)), ctypes.byref(p)))
+
+
+def linear_pt(V0: float, U0: float, R0: float, Z0: float, kappa: float, Omega: float,
+              charge_c: float, mass_kg: float):
+    """Trap parameters (Omega, a, q, omega_z) of the oracle's trap for a linear Paul trap
+    given by voltages and geometry (linearPT, Sec. 3 "Forces and fields").  Eq. 3:
+    q_x = 2 Q V0 / (M R0^2 Omega^2) and a_z = 8 Q kappa U0 / (M Z0^2 Omega^2); the static
+    axial frequency follows from a_z as omega_z = (Omega/2) sqrt(a_z).  The radial a_x =
+    -a_z/2 of Eq. 3 is the axial field's defocusing, which the trap of this oracle already
+    contains through omega_z, so the extra a is 0."""
+    q = 2.0 * charge_c * V0 / (mass_kg * R0 ** 2 * Omega ** 2)
+    a_z = 8.0 * charge_c * kappa * U0 / (mass_kg * Z0 ** 2 * Omega ** 2)
+    return Omega, 0.0, q, Omega / 2.0 * math.sqrt(a_z)
 
 
 # ------------------------------------------------------------------- stability

@@ -58,6 +58,7 @@ struct GpShape {
 struct iontrap {
   int64_t n = 0;
   int nspecies = 0;
+  iontrap_species species[IONTRAP_MAX_SPECIES]{};
   iontrap_params p{};
   int f64 = 0;
   int device = 0;
@@ -349,6 +350,42 @@ size_t smem_of(const iontrap* h) {
   return (size_t)h->jsplit * 32;
 }
 
+// The per-species constants and the trap of a handle's step arguments, from the trap and
+// default bath of p and, when cool is not null, one bath and laser per species.
+void fill_forces(iontrap* h, const iontrap_params* p, const iontrap_cooling* cool) {
+  const double dt = h->p.dt;
+  const double ke = 1.0 / (4.0 * kPi * kEps0);
+  const double qm0 = h->species[0].charge_e / h->species[0].mass_amu;
+  StepArgs& A = h->args;
+  int laser = 0;
+  for (int s = 0; s < h->nspecies; ++s) {
+    const double M = h->species[s].mass_amu * kAmu, z = h->species[s].charge_e;
+    const double g = cool ? cool[s].gamma : p->gamma, T = cool ? cool[s].T_bath : p->T_bath;
+    SpeciesDev& d = A.spc[s];
+    d.coul = ke * kE * kE * z / M;
+    d.rho = (z / h->species[s].mass_amu) / qm0;
+    d.gamma = g;
+    d.sigma = std::sqrt(2.0 * g * kKB * T / (M * dt));
+    const double* L = cool ? cool[s].laser : nullptr;
+    const double ln = L ? std::sqrt(L[0] * L[0] + L[1] * L[1] + L[2] * L[2]) : 0.0;
+    d.lrate = ln;
+    for (int c = 0; c < 3; ++c) d.kdir[c] = ln > 0.0 ? L[c] / ln : 0.0;
+    if (ln > 0.0) laser = 1;
+    d.w = (float)z;
+    d.pad = 0.f;
+  }
+  A.trap.dt = dt;
+  A.trap.hdt = 0.5 * dt;
+  A.trap.Omega = p->Omega;
+  A.trap.q4 = p->Omega * p->Omega / 4.0;
+  A.trap.a = p->a;
+  A.trap.q = p->q;
+  A.trap.wz2 = p->omega_z * p->omega_z;
+  A.trap.seed = p->seed;
+  A.trap.flags = p->flags;
+  A.trap.laser = laser;
+}
+
 void destroy_graph(iontrap* h) {
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->graph) cudaGraphDestroy(h->graph);
@@ -439,7 +476,6 @@ cudaError_t launch_mode(iontrap* h, int mode, double* out) {
   StepArgs a = h->args;
   a.mode = mode;
   a.out = out;
-  void* params[] = {&a};
   return launch_step_on(h, a, h->stream);
 }
 
@@ -539,6 +575,23 @@ const char* iontrap_strerror(int status) {
   }
 }
 
+int iontrap_linear_pt(double V0, double U0, double R0, double Z0, double kappa, double Omega,
+                      const iontrap_species* species0, iontrap_params* p) {
+  if (!species0 || !p) return IONTRAP_EINVAL;
+  const double vals[] = {V0, U0, R0, Z0, kappa, Omega, species0->mass_amu, species0->charge_e};
+  for (double v : vals)
+    if (!std::isfinite(v)) return IONTRAP_EINVAL;
+  if (!(R0 > 0) || !(Z0 > 0) || !(Omega > 0) || !(species0->mass_amu > 0)) return IONTRAP_EINVAL;
+  const double qm = species0->charge_e * kE / (species0->mass_amu * kAmu);  // Q/M, C/kg
+  const double wz2 = 2.0 * qm * kappa * U0 / (Z0 * Z0);
+  if (wz2 < 0) return IONTRAP_EINVAL;
+  p->Omega = Omega;
+  p->a = 0.0;
+  p->q = 2.0 * qm * V0 / (R0 * R0 * Omega * Omega);
+  p->omega_z = std::sqrt(wz2);
+  return IONTRAP_OK;
+}
+
 int iontrap_stable(const iontrap_species* species, int n_species, const iontrap_params* p, int* is_stable) {
   if (!is_stable) return IONTRAP_EINVAL;
   const int st = check_params(species, n_species, p);
@@ -619,29 +672,10 @@ int iontrap_create(const iontrap_species* species, int n_species, const uint8_t*
     }
   }
 
-  // species table
-  const double dt = h->p.dt;
-  const double ke = 1.0 / (4.0 * kPi * kEps0);
-  const double qm0 = species[0].charge_e / species[0].mass_amu;
+  // species table, trap and bath
+  for (int s = 0; s < n_species; ++s) h->species[s] = species[s];
+  fill_forces(h, p, nullptr);
   StepArgs& A = h->args;
-  for (int s = 0; s < n_species; ++s) {
-    const double M = species[s].mass_amu * kAmu, z = species[s].charge_e;
-    A.spc[s].coul = ke * kE * kE * z / M;
-    A.spc[s].rho = (z / species[s].mass_amu) / qm0;
-    A.spc[s].sigma = std::sqrt(2.0 * p->gamma * kKB * p->T_bath / (M * dt));
-    A.spc[s].w = (float)z;
-    A.spc[s].pad = 0.f;
-  }
-  A.trap.dt = dt;
-  A.trap.hdt = 0.5 * dt;
-  A.trap.Omega = p->Omega;
-  A.trap.q4 = p->Omega * p->Omega / 4.0;
-  A.trap.a = p->a;
-  A.trap.q = p->q;
-  A.trap.wz2 = p->omega_z * p->omega_z;
-  A.trap.gamma = p->gamma;
-  A.trap.seed = p->seed;
-  A.trap.flags = p->flags;
   A.n = n;
   A.unitw = 1;  // every species singly charged (+1 e): exact to drop the z_j factor
   for (int s = 0; s < n_species; ++s)
@@ -743,6 +777,42 @@ int iontrap_step(iontrap_t* h, int64_t n_steps) {
     h->step += 1;
   }
   return h->status;
+}
+
+int iontrap_set_params(iontrap_t* h, const iontrap_params* p, const iontrap_cooling* cooling) {
+  if (!h || !p) return IONTRAP_EINVAL;
+  if (h->status) return h->status;
+  int st = check_params(h->species, h->nspecies, p);
+  if (st) return st;
+  if (effective_dt(p) != h->p.dt || p->seed != h->p.seed || p->precision != h->p.precision ||
+      ((p->flags ^ h->p.flags) & IONTRAP_COULOMB_OFF))
+    return IONTRAP_EINVAL;
+  if (cooling)
+    for (int s = 0; s < h->nspecies; ++s) {
+      const iontrap_cooling& c = cooling[s];
+      const double vals[] = {c.gamma, c.T_bath, c.laser[0], c.laser[1], c.laser[2]};
+      for (double v : vals)
+        if (!std::isfinite(v)) return IONTRAP_EINVAL;
+      if (c.gamma < 0 || c.T_bath < 0) return IONTRAP_EINVAL;
+    }
+  if (!(p->flags & IONTRAP_ALLOW_UNSTABLE)) {
+    int ok = 0;
+    iontrap_stable(h->species, h->nspecies, p, &ok);
+    if (!ok) return IONTRAP_EUNSTABLE;
+  }
+  DeviceGuard g(h->device);
+  cudaError_t e = cudaStreamSynchronize(h->stream);  // no graph of the old forces in flight
+  if (e != cudaSuccess) return cuda_status(h, e);
+  const double dt = h->p.dt;
+  h->p = *p;
+  h->p.dt = dt;
+  fill_forces(h, p, cooling);
+  destroy_graph(h);
+  // a_n under the new forces, as iontrap_create evaluates it at step0 = n
+  e = launch_prep(h, (int)(h->step & 1));
+  if (e == cudaSuccess) e = launch_mode(h, MODE_INIT, nullptr);
+  if (e != cudaSuccess) return cuda_status(h, e);
+  return iontrap_sync(h);
 }
 
 int iontrap_sync(iontrap_t* h) {

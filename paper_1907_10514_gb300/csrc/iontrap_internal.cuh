@@ -29,7 +29,10 @@ enum ErrBits : int { ERR_NONFINITE = 1, ERR_TIMEOUT = 2 };
 struct SpeciesDev {
   double coul;   // k_e e^2 z / M: Coulomb acceleration per unit of sum_j z_j d/r^3
   double rho;    // (z/M) / (z_0/M_0): scales a, q and omega_z^2 of species 0
+  double gamma;  // Langevin rate of this species' bath (1/dampingTime), 1/s
   double sigma;  // sqrt(2 gamma k_B T / (M dt)): std. dev. of the Langevin kick acceleration
+  double lrate;  // laser-cooling rate |g|, 1/s (0: no laser on this species)
+  double kdir[3];  // laser direction g / |g|
   float w;       // z as float, the source weight in the FP32 pair stream
   float pad;
 };
@@ -38,10 +41,9 @@ struct TrapDev {
   double dt, hdt;      // step and half step
   double Omega, q4;    // RF angular frequency and Omega^2/4
   double a, q, wz2;    // Mathieu a, q and omega_z^2 of species 0
-  double gamma;        // Langevin rate
   unsigned long long seed;
   unsigned flags;
-  int pad;
+  int laser;           // some species is laser-cooled
 };
 
 // Arguments of one force+integrate launch.  All per-ion arrays are SoA [3][n].
@@ -365,19 +367,32 @@ __device__ __forceinline__ void trap_springs(const TrapDev& tp, const SpeciesDev
 
 // Acceleration of one ion at force time, FP64 in both forms, split in two so that the
 // part that does not depend on the Coulomb sum can be evaluated before the sum is known:
-//   ext = -k xf - gamma vd + sigma xi(seed, counter, id)   (accel_ext)
-//   acc = k_e e^2 z/M S + ext                             (accel_total)
-// with k the spring constants of the ion's species and S = sum_j z_j d/r^3.  Explicit
+//   ext = -k xf - gamma vd - lrate (kdir.vd) kdir + sigma xi(seed, counter, id)  (accel_ext)
+//   acc = k_e e^2 z/M S + ext                                                  (accel_total)
+// with k the spring constants, gamma and sigma the bath and (lrate, kdir) the laser of the
+// ion's species, and S = sum_j z_j d/r^3.  Explicit
 // roundings (no FMA contraction left to the compiler): every kernel produces the same
 // bits.  The trajectories of these clouds amplify FP32-sized perturbations of the RF trap
 // term by ~1e4 within 100 steps, so no term is evaluated in FP32.  F64 selects FP64
 // Box-Muller noise.
 // The deterministic part (trap springs and drag) and the kick sigma*xi, separately so
 // that a kernel can draw the normals ahead of time.
-__device__ __forceinline__ void accel_ext_det(const TrapDev& tp, const double k[3], const double xf[3],
+// Laser-cooling drag of one ion (laserCool, Sec. 3 "Cooling the motion of ions"): the
+// rate times the drag velocity's projection on the beam direction, -lrate (k.vd) k.
+__device__ __forceinline__ double laser_proj(const SpeciesDev& sd, const double vd[3]) {
+  const double kv = __fma_rn(sd.kdir[2], vd[2], __fma_rn(sd.kdir[1], vd[1], __dmul_rn(sd.kdir[0], vd[0])));
+  return __dmul_rn(sd.lrate, kv);
+}
+
+__device__ __forceinline__ void accel_ext_det(const SpeciesDev& sd, const double k[3], const double xf[3],
                                               const double vd[3], double ext[3]) {
 #pragma unroll
-  for (int c = 0; c < 3; ++c) ext[c] = __fma_rn(-tp.gamma, vd[c], __dmul_rn(-k[c], xf[c]));
+  for (int c = 0; c < 3; ++c) ext[c] = __fma_rn(-sd.gamma, vd[c], __dmul_rn(-k[c], xf[c]));
+  if (sd.lrate != 0.0) {
+    const double lp = laser_proj(sd, vd);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ext[c] = __fma_rn(-lp, sd.kdir[c], ext[c]);
+  }
 }
 
 __device__ __forceinline__ void accel_add_kick(const SpeciesDev& sd, const double z[3], double ext[3]) {
@@ -389,7 +404,7 @@ template <bool F64>
 __device__ __forceinline__ void accel_ext(const TrapDev& tp, const SpeciesDev& sd, const double k[3],
                                           const double xf[3], const double vd[3], long long counter, long long id,
                                           double ext[3]) {
-  accel_ext_det(tp, k, xf, vd, ext);
+  accel_ext_det(sd, k, xf, vd, ext);
   if (sd.sigma > 0.0) {
     double z[3];
     if constexpr (F64) {

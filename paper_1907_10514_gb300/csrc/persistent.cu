@@ -76,7 +76,8 @@ __global__ void __launch_bounds__(32 * W, 16 / W) k_step_f32_gp(const __grid_con
   constexpr int B = 64;  // ions per warp
   // dynamic shared memory: segment hi[Lmax], lo[Lmax]; the owned ions' partials as
   // floats sum[3][S][R] and comp[3][S][R] (R <= Rmax = ceil(64 W / S)); the RF phase
-  // cos(Omega t) at the force time of each of the K steps
+  // cos(Omega t) at the force time of each of the K steps; the owned ions' drag
+  // velocities [3][R] (laser cooling needs all three components of an ion)
   extern __shared__ __align__(16) float4 s_dyn[];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -97,6 +98,7 @@ __global__ void __launch_bounds__(32 * W, 16 / W) k_step_f32_gp(const __grid_con
   float* fsum = reinterpret_cast<float*>(s_dyn + 2 * P.Lmax);
   float* fcmp = fsum + 3 * S * rmax;
   double* scos = reinterpret_cast<double*>(fcmp + 3 * S * rmax);  // 24 S rmax bytes past fsum: 8-byte aligned
+  double* svd = scos + P.K;
   unsigned* ctr_step = P.sync;
   unsigned* ctr_grp = P.sync + 32 * (1 + g);
   const int poller = T - 1;
@@ -223,16 +225,26 @@ __global__ void __launch_bounds__(32 * W, 16 / W) k_step_f32_gp(const __grid_con
       fence_gpu();
     }
     // while the group's CTAs arrive: the owned components' force-independent terms
-    // (trap, drag, kick; the roundings of accel_ext) and the next step's normals
+    // (trap, drag, laser, kick; the operations and order of accel_ext) and the next
+    // step's normals
     double ext = 0.0;
+    const float zk = z;
     if (own && !forces) {
       const SpeciesDev& sd = A.spc[spe];
       const double kc = trap_spring_c(tp, sd, scos[t], oc);
-      ext = __fma_rn(-tp.gamma, vd, __dmul_rn(-kc, xf));
-      if (sd.sigma > 0.0) ext = __fma_rn(sd.sigma, (double)z, ext);
+      ext = __fma_rn(-sd.gamma, vd, __dmul_rn(-kc, xf));
+      if (tp.laser) svd[oc * R + oq] = vd;
     }
     if (t + 1 < P.K) draw(ns + 2);
     if (__syncthreads_or(bad)) break;
+    if (own && !forces) {
+      const SpeciesDev& sd = A.spc[spe];
+      if (tp.laser && sd.lrate != 0.0) {
+        const double v3[3] = {svd[oq], svd[R + oq], svd[2 * R + oq]};
+        ext = __fma_rn(-laser_proj(sd, v3), sd.kdir[oc], ext);
+      }
+      if (sd.sigma > 0.0) ext = __fma_rn(sd.sigma, (double)zk, ext);
+    }
 
     // the owned ions' S records, fetched by the whole CTA in one round trip
     for (int k = tid; k < R * S; k += T) {
@@ -302,11 +314,12 @@ __global__ void __launch_bounds__(32 * W, 16 / W) k_step_f32_gp(const __grid_con
 }
 
 // Dynamic shared memory of a launch: the segment (2 Lmax float4), the owned ions'
-// partials (2 x 3 x S x ceil(64 W / S) floats, rounded up to 16 bytes) and K cosines.
+// partials (2 x 3 x S x ceil(64 W / S) floats, rounded up to 16 bytes), K cosines and
+// the owned ions' drag velocities (3 x ceil(64 W / S) doubles).
 size_t gp_smem_bytes(int W, int S, int Lmax, long long K) {
   const size_t rmax = (size_t)((64 * W + S - 1) / S);
   const size_t recs = (6 * rmax * (size_t)S * sizeof(float) + 15) / 16 * 16;
-  return 2 * (size_t)Lmax * sizeof(float4) + recs + (size_t)K * sizeof(double);
+  return 2 * (size_t)Lmax * sizeof(float4) + recs + (size_t)K * sizeof(double) + 3 * rmax * sizeof(double);
 }
 
 const void* gp_kernel(int W) {
@@ -346,9 +359,9 @@ int gp_max_ctas(int W, int S, int Lmax, int max_lmax, long long max_k, int sms) 
   const void* fn = gp_kernel(W);
   if (!fn || Lmax > max_lmax || S < 1) return 0;
   const size_t smem = gp_smem_bytes(W, S, Lmax, max_k);
-  // ceil(64 W / S) S < 128 W
+  // ceil(64 W / S) S < 128 W; ceil(64 W / S) <= 64 W
   const size_t limit = 2 * (size_t)max_lmax * sizeof(float4) + 6 * 128 * (size_t)W * sizeof(float) + 16 +
-                       (size_t)max_k * sizeof(double);
+                       (size_t)max_k * sizeof(double) + 3 * 64 * (size_t)W * sizeof(double);
   if (smem > limit) return 0;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit) != cudaSuccess) return 0;
   int per = 0;

@@ -48,6 +48,10 @@ class iontrap_params(ctypes.Structure):
                 ("precision", ctypes.c_int32)]
 
 
+class iontrap_cooling(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("T_bath", ctypes.c_double), ("laser", ctypes.c_double * 3)]
+
+
 class iontrap_config(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("ions_per_thread", ctypes.c_int32),
                 ("packed", ctypes.c_int32), ("jsplit", ctypes.c_int32), ("fused", ctypes.c_int32),
@@ -83,6 +87,7 @@ SIGNATURES = {
                                       ctypes.POINTER(_vp)]),
     "iontrap_step": (ctypes.c_int, [_vp, ctypes.c_int64]),
     "iontrap_sync": (ctypes.c_int, [_vp]),
+    "iontrap_set_params": (ctypes.c_int, [_vp, ctypes.POINTER(iontrap_params), ctypes.POINTER(iontrap_cooling)]),
     "iontrap_state": (ctypes.c_int, [_vp, _dp, _dp, _i64p, _dp]),
     "iontrap_forces": (ctypes.c_int, [_vp, _dp]),
     "iontrap_checkpoint": (ctypes.c_int, [_vp, _dp, _dp, _dp, _i64p]),
@@ -92,6 +97,9 @@ SIGNATURES = {
     "iontrap_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "iontrap_stable": (ctypes.c_int, [ctypes.POINTER(iontrap_species), ctypes.c_int,
                                       ctypes.POINTER(iontrap_params), _ip]),
+    "iontrap_linear_pt": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, ctypes.POINTER(iontrap_species),
+                                         ctypes.POINTER(iontrap_params)]),
     "iontrap_normals": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int64, _i64p, ctypes.c_int64,
                                        ctypes.c_int, _dp]),
     "iontrap_get_config": (ctypes.c_int, [_vp, ctypes.POINTER(iontrap_config)]),
@@ -216,6 +224,25 @@ def iontrap_step(h, n_steps: int) -> None:
     _check(_lib.iontrap_step(h, int(n_steps)), "iontrap_step")
 
 
+def _cooling_array(cooling) -> Optional[ctypes.Array]:
+    """One iontrap_cooling per species from objects with gamma, T_bath and laser
+    attributes (or (gamma, T_bath, laser) tuples); None passes NULL."""
+    if cooling is None:
+        return None
+    arr = (iontrap_cooling * len(cooling))()
+    for k, c in enumerate(cooling):
+        g, T, L = (c.gamma, c.T_bath, c.laser) if hasattr(c, "gamma") else c
+        arr[k].gamma, arr[k].T_bath = float(g), float(T)
+        for d in range(3):
+            arr[k].laser[d] = float(L[d])
+    return arr
+
+
+def iontrap_set_params(h, params: iontrap_params, cooling=None) -> None:
+    """Change the trap and the per-species cooling between evolve calls."""
+    _check(_lib.iontrap_set_params(h, ctypes.byref(params), _cooling_array(cooling)), "iontrap_set_params")
+
+
 def iontrap_sync(h) -> None:
     _check(_lib.iontrap_sync(h), "iontrap_sync")
 
@@ -266,6 +293,16 @@ def iontrap_stable(species: Sequence, params: iontrap_params) -> bool:
     _check(_lib.iontrap_stable(_species_array(species), len(species), ctypes.byref(params),
                                ctypes.byref(ok)), "iontrap_stable")
     return bool(ok.value)
+
+
+def iontrap_linear_pt(V0: float, U0: float, R0: float, Z0: float, kappa: float, Omega: float, species0,
+                      params: Optional[iontrap_params] = None) -> iontrap_params:
+    """Fill Omega, a, q, omega_z of ``params`` (a new one if None) from the voltages
+    and geometry of a linear Paul trap; returns the params."""
+    p = params if params is not None else iontrap_params()
+    _check(_lib.iontrap_linear_pt(float(V0), float(U0), float(R0), float(Z0), float(kappa), float(Omega),
+                                  _species_array([species0]), ctypes.byref(p)), "iontrap_linear_pt")
+    return p
 
 
 def iontrap_normals(seed: int, counter: int, ids, precision: int = IONTRAP_PREC_FP32) -> np.ndarray:
@@ -424,6 +461,9 @@ class Simulation:
 
     def sync(self) -> None:
         iontrap_sync(self.handle)
+
+    def set_params(self, params, cooling=None) -> None:
+        iontrap_set_params(self.handle, params, cooling)
 
     def state(self):
         return iontrap_state(self.handle, self.n)

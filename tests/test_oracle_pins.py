@@ -169,9 +169,8 @@ def test_trap_matches_voltage_form_of_eq1():
     opposite sign."""
     Q, M = E, M_CA
     V0, R0, U0, Z0, kappa = 300.0, 0.9e-3, 7.0, 2.75e-3, 0.3
-    q = 2 * Q * V0 / (M * R0 ** 2 * OMEGA_RF ** 2)
-    a_z = 8 * Q * kappa * U0 / (M * Z0 ** 2 * OMEGA_RF ** 2)
-    wz = math.sqrt(a_z * OMEGA_RF ** 2 / 4)
+    Om, a0, q, wz = oracle.linear_pt(V0, U0, R0, Z0, kappa, OMEGA_RF, Q, M)
+    assert Om == OMEGA_RF and a0 == 0.0
     tr = _trap(q=q, omega_z=wz, a=0.0)
     p = oracle.params(tr, Q / M)
     rng = np.random.default_rng(3)
