@@ -356,6 +356,24 @@ def extra_measurements(it, torch, stream, sms, args):
     out["fp64_form_mix_n4096"] = {"ion_steps_per_s": n * k / (ms / 1e3),
                                   "pair_interactions_per_s": n * (n - 1) * k / (ms / 1e3),
                                   "us_per_timestep": 1e3 * ms / k, "timesteps": k}
+    # the same workload with species-selective cooling (Sec. 3): Ca+ laser-cooled along x on
+    # top of its bath, NH3+ in a bath of its own; forces changed through iontrap_set_params
+    pc = it.make_params(w.trap, precision=it.IONTRAP_PREC_FP32)
+    cool = [(w.trap.gamma, w.trap.T_bath, (1e5, 0.0, 0.0)), (2e5, 2e-3, (0.0, 0.0, 0.0))]
+    with it.Simulation(w.species, w.species_of_ion, w.x0, w.v0, pc, stream=stream) as s:
+        s.set_params(pc, cool)
+        s.step(100)
+        s.sync()
+        k = 1000
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(k)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        out["mix_n4096_species_cooling"] = {"ion_steps_per_s": n * k / (ms / 1e3), "us_per_timestep": 1e3 * ms / k,
+                                            "timesteps": k, "tile": list(s.config()),
+                                            "cooling": "Ca+: bath 1e5/s 1 mK + laser (1e5, 0, 0)/s; NH3+: bath 2e5/s 2 mK"}
     wc = iongen.crystal_n32768()
     nc = wc.n
     pc = it.make_params(wc.trap, precision=it.IONTRAP_PREC_FP32)
