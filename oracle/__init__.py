@@ -13,6 +13,11 @@ Functions follow the paper:
   * ``cooling_arrays`` -- per-species baths and laser cooling (Sec. 3, langevinBath
                           on a group, laserCool) as per-ion arrays for ``accel``/``run``
   * ``linear_pt``      -- Mathieu parameters of a trap given by voltages (Eq. 3)
+  * ``pseudo_springs`` -- the pseudopotential of the trap (Eq. 2); ``springs_arrays``
+                          a pseudopotential trap given by per-species frequencies
+  * ``minimize``       -- damped minimisation of the static potential (Sec. 3)
+  * ``hessian``        -- mass-weighted Hessian whose eigenvalues are the squared
+                          normal-mode frequencies (Sec. 5 "Normal modes of motion")
   * ``run``            -- velocity-Verlet time evolution (Sec. 6 "Integration", "nve")
   * ``energy``         -- Eq. 4 energy for a static trap
   * ``stable``         -- discrete-Verlet Floquet stability of a single ion (|tr M| < 2)
@@ -41,6 +46,7 @@ _lib = None
 RF_OFF = 1
 COULOMB_OFF = 2
 TRAP_OFF = 4
+PSEUDO = 16  # the trap is its Eq. 2 pseudopotential (static springs)
 
 
 class _Params(ctypes.Structure):
@@ -84,12 +90,16 @@ def lib():
                                    ctypes.c_double, dp]
         L.oracle_run.argtypes = [ctypes.c_int64, dp, dp, dp, dp, dp, pp, ctypes.c_int64,
                                  ctypes.c_int64, ctypes.c_int, dp]
-        L.oracle_accel_cool.argtypes = [ctypes.c_int64, dp, dp, dp, dp, pp, ctypes.c_int64,
-                                        ctypes.c_double, dp, dp, dp, dp]
-        L.oracle_run_cool.argtypes = [ctypes.c_int64, dp, dp, dp, dp, dp, pp, ctypes.c_int64,
-                                      ctypes.c_int64, ctypes.c_int, dp, dp, dp, dp]
+        L.oracle_accel_ex.argtypes = [ctypes.c_int64, dp, dp, dp, dp, pp, ctypes.c_int64,
+                                      ctypes.c_double, dp, dp, dp, dp, dp]
+        L.oracle_run_ex.argtypes = [ctypes.c_int64, dp, dp, dp, dp, dp, pp, ctypes.c_int64,
+                                    ctypes.c_int64, ctypes.c_int, dp, dp, dp, dp, dp]
         L.oracle_energy.restype = ctypes.c_double
         L.oracle_energy.argtypes = [ctypes.c_int64, dp, dp, dp, dp, pp]
+        L.oracle_energy_ex.restype = ctypes.c_double
+        L.oracle_energy_ex.argtypes = [ctypes.c_int64, dp, dp, dp, dp, pp, dp]
+        L.oracle_pseudo_springs.argtypes = [pp, ctypes.c_double, dp]
+        L.oracle_hessian.argtypes = [ctypes.c_int64, dp, dp, dp, pp, dp, dp]
         _lib = L
     return _lib
 
@@ -198,39 +208,119 @@ def _cool_ptrs(cooling):
     return _dp(g), _dp(T), _dp(L), (g, T, L)
 
 
-def accel(x, udrag, charge, mass, p: _Params, counter: int, t: float, cooling=None) -> np.ndarray:
+def _opt(a):
+    if a is None:
+        return None, None
+    a = _c64(a)
+    return _dp(a), a
+
+
+def pseudo_springs(p: _Params, qm: float) -> np.ndarray:
+    """Spring constants (1/s^2) of the Eq. 2 pseudopotential for charge/mass qm."""
+    k = np.empty(3)
+    lib().oracle_pseudo_springs(ctypes.byref(p), float(qm), _dp(k))
+    return k
+
+
+def springs_arrays(species_of_ion, omegas) -> np.ndarray:
+    """Per-ion spring constants [3][n] from secular angular frequencies (wx, wy, wz)
+    given per species -- a pseudopotential trap per species (linearPseudoPT, Sec. 3)."""
+    w = np.asarray(omegas, dtype=np.float64).reshape(-1, 3)
+    sp = np.asarray(species_of_ion, dtype=np.int64)
+    return _c64((w[sp] ** 2).T)
+
+
+def accel(x, udrag, charge, mass, p: _Params, counter: int, t: float, cooling=None,
+          springs=None) -> np.ndarray:
     """Acceleration of every ion; ``cooling`` = (gamma[n], T_bath[n], laser[3][n]) per
-    ion (see ``cooling_arrays``), or None for the bath of ``p`` and no laser."""
+    ion (see ``cooling_arrays``), or None for the bath of ``p`` and no laser; ``springs``
+    = per-ion static springs [3][n] replacing the trap (see ``springs_arrays``)."""
     x, udrag = _c64(x), _c64(udrag)
     acc = np.empty_like(x)
     gp, tp, lp, keep = _cool_ptrs(cooling)
-    lib().oracle_accel_cool(x.shape[1], _dp(x), _dp(udrag), _dp(_c64(charge)), _dp(_c64(mass)),
-                            ctypes.byref(p), int(counter), float(t), gp, tp, lp, _dp(acc))
-    del keep
+    sp_, keep2 = _opt(springs)
+    lib().oracle_accel_ex(x.shape[1], _dp(x), _dp(udrag), _dp(_c64(charge)), _dp(_c64(mass)),
+                          ctypes.byref(p), int(counter), float(t), gp, tp, lp, sp_, _dp(acc))
+    del keep, keep2
     return acc
 
 
-def run(x0, v0, charge, mass, p: _Params, nsteps: int, step0: int = 0, a0=None, cooling=None):
+def run(x0, v0, charge, mass, p: _Params, nsteps: int, step0: int = 0, a0=None, cooling=None,
+        springs=None):
     """Velocity-Verlet evolution.  Returns (x, v, a) after ``nsteps`` steps.  With
     ``a0`` None the initial acceleration is evaluated first (at t = step0 dt, drag on
     v0, noise counter step0) -- which is also how the forces change between two runs
-    (interleaved evolve, Sec. 3 "Time evolution").  ``cooling`` as for ``accel``."""
+    (interleaved evolve, Sec. 3 "Time evolution").  ``cooling`` and ``springs`` as for
+    ``accel``."""
     x, v = _c64(x0).copy(), _c64(v0).copy()
     n = x.shape[1]
     a = np.zeros_like(x) if a0 is None else _c64(a0).copy()
     work = np.empty_like(x)
     gp, tp, lp, keep = _cool_ptrs(cooling)
-    lib().oracle_run_cool(n, _dp(x), _dp(v), _dp(a), _dp(_c64(charge)), _dp(_c64(mass)),
-                          ctypes.byref(p), int(step0), int(nsteps), int(a0 is None), gp, tp, lp,
-                          _dp(work))
-    del keep
+    sp_, keep2 = _opt(springs)
+    lib().oracle_run_ex(n, _dp(x), _dp(v), _dp(a), _dp(_c64(charge)), _dp(_c64(mass)),
+                        ctypes.byref(p), int(step0), int(nsteps), int(a0 is None), gp, tp, lp, sp_,
+                        _dp(work))
+    del keep, keep2
     return x, v, a
 
 
-def energy(x, v, charge, mass, p: _Params) -> float:
+def minimize(x0, charge, mass, p: _Params, dt: float, dmax: float, ftol: float, max_steps: int,
+             springs=None):
+    """Damped dynamics toward the minimum of the static potential (Sec. 3
+    "Minimisation": the equations of motion are damped to extract energy, and the distance
+    an ion may move in one step is limited).  The trap must be static (the pseudopotential
+    of Eq. 2, ``springs``, or RF off); no bath acts.  Starting at rest, every step:
+      1. a = acceleration at x (trap + Coulomb), F_i = M_i a_i; stop if |F| < ftol
+         (2-norm over all ions and components);
+      2. the velocity keeps only its component along the force, v = (v.F / F.F) F, and is
+         set to zero when v.F <= 0 (moving uphill);
+      3. v += dt a; the displacement d = dt v is scaled (with v) by
+         min(1, dmax / max_i |d_i|), so no ion moves more than dmax; x += d.
+    Returns (x, steps taken, |F| at the last evaluation)."""
+    x = _c64(x0).copy()
+    mass = _c64(mass)
+    v = np.zeros_like(x)
+    zero = np.zeros_like(x)
+    fn = math.inf
+    for k in range(int(max_steps)):
+        a = accel(x, zero, charge, mass, p, 0, 0.0, springs=springs)
+        F = mass[None, :] * a
+        FF = float((F * F).sum())
+        fn = math.sqrt(FF)
+        if fn < ftol:
+            return x, k, fn
+        vF = float((v * F).sum())
+        v = (vF / FF) * F if vF > 0.0 else np.zeros_like(x)
+        v = v + dt * a
+        d = dt * v
+        dm = float(np.sqrt((d * d).sum(axis=0)).max())
+        s = min(1.0, dmax / dm) if dm > 0.0 else 1.0
+        v = s * v
+        x = x + s * d
+    return x, int(max_steps), fn
+
+
+def hessian(x, charge, mass, p: _Params, springs=None) -> np.ndarray:
+    """Mass-weighted Hessian (3n x 3n, row/column 3i+a) of the static potential at x:
+    trap springs (``springs`` or the Eq. 2 pseudopotential of ``p``) plus the Coulomb pair
+    energy.  Its eigenvalues are the squared normal-mode angular frequencies (Sec. 5)."""
+    x = _c64(x)
+    n = x.shape[1]
+    H = np.empty((3 * n, 3 * n))
+    sp_, keep = _opt(springs)
+    lib().oracle_hessian(n, _dp(x), _dp(_c64(charge)), _dp(_c64(mass)), ctypes.byref(p), sp_, _dp(H))
+    del keep
+    return H
+
+
+def energy(x, v, charge, mass, p: _Params, springs=None) -> float:
     x, v = _c64(x), _c64(v)
-    return float(lib().oracle_energy(x.shape[1], _dp(x), _dp(v), _dp(_c64(charge)),
-                                     _dp(_c64(mass)), ctypes.byref(p)))
+    sp_, keep = _opt(springs)
+    e = float(lib().oracle_energy_ex(x.shape[1], _dp(x), _dp(v), _dp(_c64(charge)),
+                                     _dp(_c64(mass)), ctypes.byref(p), sp_))
+    del keep
+    return e
 
 
 def linear_pt(V0: float, U0: float, R0: float, Z0: float, kappa: float, Omega: float,

@@ -60,6 +60,7 @@ static const double ORC_PI = 3.14159265358979323846;
 #define ORC_RF_OFF 1u
 #define ORC_COULOMB_OFF 2u
 #define ORC_TRAP_OFF 4u
+#define ORC_PSEUDO 16u   /* the trap is its Eq. 2 pseudopotential: static springs */
 
 typedef struct {
     double Omega;    /* RF angular frequency, rad/s */
@@ -199,12 +200,36 @@ void oracle_coulomb_accel(int64_t n, const double *x, const double *charge,
 }
 
 /* ---------------------------------------------------------------------- trap term */
-/* Linear Paul trap acceleration (Eq. 1 with the Mathieu parameters of Eq. 3). */
+/* Spring constants (1/s^2) of the pseudopotential of the trap for an ion of
+ * charge/mass qm (Eq. 2): omega_m^2 = (Omega^2/4)(a_m + q_m^2/2) along x and y, with
+ * q_m = rho q and a_m = rho a - 2 rho omega_z^2 / Omega^2 (the species' own dc a plus the
+ * axial field's radial defocusing, Eq. 3: a_x = -a_z/2), and rho omega_z^2 along z. */
+void oracle_pseudo_springs(const oracle_params *p, double qm, double k[3])
+{
+    double rho = qm / p->qm_ref;
+    double O2 = p->Omega * p->Omega;
+    double wz2 = rho * p->omega_z * p->omega_z;
+    double a_m = rho * p->a - 2.0 * wz2 / O2;
+    double q_m = rho * p->q;
+    double kr = O2 / 4.0 * (a_m + 0.5 * q_m * q_m);
+    k[0] = kr;
+    k[1] = kr;
+    k[2] = wz2;
+}
+
+/* Linear Paul trap acceleration (Eq. 1 with the Mathieu parameters of Eq. 3), or its
+ * pseudopotential (Eq. 2) when ORC_PSEUDO is set. */
 void oracle_trap_accel(const oracle_params *p, double qm, const double r[3], double t,
                        double acc[3])
 {
     if (p->flags & ORC_TRAP_OFF) {
         acc[0] = acc[1] = acc[2] = 0.0;
+        return;
+    }
+    if (p->flags & ORC_PSEUDO) {
+        double k[3];
+        oracle_pseudo_springs(p, qm, k);
+        for (int c = 0; c < 3; ++c) acc[c] = -k[c] * r[c];
         return;
     }
     double rho = qm / p->qm_ref;
@@ -226,10 +251,13 @@ void oracle_trap_accel(const oracle_params *p, double qm, const double r[3], dou
  *                        laser); NULL: no laser cooling
  * A bath restricted to a group (langevinBath(T, dampingTime, group)) is a group whose
  * ions carry that bath's (gamma, T) and the others (0, 0). */
-void oracle_accel_cool(int64_t n, const double *x, const double *udrag, const double *charge,
-                       const double *mass, const oracle_params *p, int64_t counter, double t,
-                       const double *gamma, const double *T_bath, const double *laser,
-                       double *acc)
+/* springs[3][n] (may be NULL): static spring constants k of each ion (1/s^2, SoA),
+ * acceleration -k_c x_c, replacing the trap of p (a pseudopotential trap given by its
+ * frequencies, linearPseudoPT, Sec. 3 "Forces and fields"). */
+void oracle_accel_ex(int64_t n, const double *x, const double *udrag, const double *charge,
+                     const double *mass, const oracle_params *p, int64_t counter, double t,
+                     const double *gamma, const double *T_bath, const double *laser,
+                     const double *springs, double *acc)
 {
     if (p->flags & ORC_COULOMB_OFF) {
         for (int64_t k = 0; k < 3 * n; ++k) acc[k] = 0.0;
@@ -241,7 +269,10 @@ void oracle_accel_cool(int64_t n, const double *x, const double *udrag, const do
         double r[3] = {x[i], x[n + i], x[2 * n + i]};
         double u[3] = {udrag[i], udrag[n + i], udrag[2 * n + i]};
         double tr[3];
-        oracle_trap_accel(p, charge[i] / mass[i], r, t, tr);
+        if (springs)
+            for (int c = 0; c < 3; ++c) tr[c] = -springs[c * n + i] * r[c];
+        else
+            oracle_trap_accel(p, charge[i] / mass[i], r, t, tr);
         double g_i = gamma ? gamma[i] : p->gamma;
         double T_i = gamma ? T_bath[i] : p->T_bath;
         double sigma = sqrt(2.0 * g_i * ORC_KB * T_i / (mass[i] * p->dt));
@@ -269,7 +300,7 @@ void oracle_accel(int64_t n, const double *x, const double *udrag, const double 
                   const double *mass, const oracle_params *p, int64_t counter, double t,
                   double *acc)
 {
-    oracle_accel_cool(n, x, udrag, charge, mass, p, counter, t, NULL, NULL, NULL, acc);
+    oracle_accel_ex(n, x, udrag, charge, mass, p, counter, t, NULL, NULL, NULL, NULL, acc);
 }
 
 /* ------------------------------------------------------------ velocity Verlet run */
@@ -278,15 +309,15 @@ void oracle_accel(int64_t n, const double *x, const double *udrag, const double 
 /* Changing the forces between two runs (interleaved evolve, Sec. 3 "Time evolution")
  * is a second call with the new parameters and init != 0: a_n is re-evaluated under the
  * new forces at (x_n, t = n dt), with v_n as the drag velocity and noise counter n. */
-void oracle_run_cool(int64_t n, double *x, double *v, double *a, const double *charge,
-                     const double *mass, const oracle_params *p, int64_t step0, int64_t nsteps,
-                     int init, const double *gamma, const double *T_bath, const double *laser,
-                     double *work /* 3n doubles of scratch */)
+void oracle_run_ex(int64_t n, double *x, double *v, double *a, const double *charge,
+                   const double *mass, const oracle_params *p, int64_t step0, int64_t nsteps,
+                   int init, const double *gamma, const double *T_bath, const double *laser,
+                   const double *springs, double *work /* 3n doubles of scratch */)
 {
     const double dt = p->dt;
     if (init)
-        oracle_accel_cool(n, x, v, charge, mass, p, step0, (double)step0 * dt, gamma, T_bath,
-                          laser, a);
+        oracle_accel_ex(n, x, v, charge, mass, p, step0, (double)step0 * dt, gamma, T_bath,
+                        laser, springs, a);
     for (int64_t s = 0; s < nsteps; ++s) {
         int64_t step = step0 + s;
         double *vh = work;
@@ -294,8 +325,8 @@ void oracle_run_cool(int64_t n, double *x, double *v, double *a, const double *c
             vh[k] = v[k] + 0.5 * dt * a[k];
             x[k] = x[k] + dt * vh[k];
         }
-        oracle_accel_cool(n, x, vh, charge, mass, p, step + 1, (double)(step + 1) * dt, gamma,
-                          T_bath, laser, a);
+        oracle_accel_ex(n, x, vh, charge, mass, p, step + 1, (double)(step + 1) * dt, gamma,
+                        T_bath, laser, springs, a);
         for (int64_t k = 0; k < 3 * n; ++k) v[k] = vh[k] + 0.5 * dt * a[k];
     }
 }
@@ -304,14 +335,15 @@ void oracle_run(int64_t n, double *x, double *v, double *a, const double *charge
                 const double *mass, const oracle_params *p, int64_t step0, int64_t nsteps,
                 int init, double *work /* 3n doubles of scratch */)
 {
-    oracle_run_cool(n, x, v, a, charge, mass, p, step0, nsteps, init, NULL, NULL, NULL, work);
+    oracle_run_ex(n, x, v, a, charge, mass, p, step0, nsteps, init, NULL, NULL, NULL, NULL, work);
 }
 
 /* ------------------------------------------------------------------------ energy */
-/* Total energy for a static trap (RF off): kinetic + trap potential + Coulomb pair
- * potential (Eq. 4, each unordered pair once). */
-double oracle_energy(int64_t n, const double *x, const double *v, const double *charge,
-                     const double *mass, const oracle_params *p)
+/* Total energy for a static trap (RF off, the pseudopotential of Eq. 2, or the static
+ * springs[3][n] when given): kinetic + trap potential + Coulomb pair potential (Eq. 4,
+ * each unordered pair once). */
+double oracle_energy_ex(int64_t n, const double *x, const double *v, const double *charge,
+                        const double *mass, const oracle_params *p, const double *springs)
 {
     const double ke = 1.0 / (4.0 * ORC_PI * ORC_EPS0);
     double kin = 0.0, trap = 0.0, coul = 0.0;
@@ -319,7 +351,14 @@ double oracle_energy(int64_t n, const double *x, const double *v, const double *
         double v2 = 0.0;
         for (int c = 0; c < 3; ++c) v2 += v[c * n + i] * v[c * n + i];
         kin += 0.5 * mass[i] * v2;
-        if (!(p->flags & ORC_TRAP_OFF)) {
+        if (springs || (p->flags & ORC_PSEUDO)) {
+            double k[3];
+            if (springs)
+                for (int c = 0; c < 3; ++c) k[c] = springs[c * n + i];
+            else
+                oracle_pseudo_springs(p, charge[i] / mass[i], k);
+            for (int c = 0; c < 3; ++c) trap += 0.5 * mass[i] * k[c] * x[c * n + i] * x[c * n + i];
+        } else if (!(p->flags & ORC_TRAP_OFF)) {
             double rho = (charge[i] / mass[i]) / p->qm_ref;
             double wz2 = rho * p->omega_z * p->omega_z;
             double kr = p->Omega * p->Omega / 4.0 * rho * p->a - 0.5 * wz2;
@@ -335,4 +374,57 @@ double oracle_energy(int64_t n, const double *x, const double *v, const double *
             }
     }
     return kin + trap + coul;
+}
+
+double oracle_energy(int64_t n, const double *x, const double *v, const double *charge,
+                     const double *mass, const oracle_params *p)
+{
+    return oracle_energy_ex(n, x, v, charge, mass, p, NULL);
+}
+
+/* ----------------------------------------------------------------------- Hessian */
+/* Mass-weighted Hessian of the static potential (trap springs + Coulomb pair energy of
+ * Eq. 4) at positions x: H[(3i+a)(3n) + 3j+b] = d^2 V / dx_ia dx_jb / sqrt(M_i M_j).
+ * Its eigenvalues are the squared normal-mode frequencies (Sec. 5 "Normal modes of
+ * motion").  Pair block (i != j), r = x_i - x_j:
+ *   d^2 (k_e Q_i Q_j / |r|) / dx_ia dx_jb = k_e Q_i Q_j (delta_ab / r^3 - 3 r_a r_b / r^5)
+ * and the diagonal block is minus the sum of the pair blocks of row i plus M_i k_a delta_ab
+ * (the pair energy depends on x_i - x_j only).  springs[3][n] as for oracle_accel_ex, or
+ * NULL for the pseudopotential of p (Eq. 2). */
+void oracle_hessian(int64_t n, const double *x, const double *charge, const double *mass,
+                    const oracle_params *p, const double *springs, double *H)
+{
+    const double ke = 1.0 / (4.0 * ORC_PI * ORC_EPS0);
+    const int64_t m = 3 * n;
+    for (int64_t k = 0; k < m * m; ++k) H[k] = 0.0;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double diag[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double r[3], r2 = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                r[c] = x[c * n + i] - x[c * n + j];
+                r2 += r[c] * r[c];
+            }
+            double rr = sqrt(r2);
+            double r3 = r2 * rr, r5 = r3 * r2;
+            double kq = ke * charge[i] * charge[j];
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    double hab = kq * ((a == b ? 1.0 : 0.0) / r3 - 3.0 * r[a] * r[b] / r5);
+                    H[(3 * i + a) * m + 3 * j + b] = hab / sqrt(mass[i] * mass[j]);
+                    diag[a][b] -= hab;
+                }
+        }
+        double k[3];
+        if (springs)
+            for (int c = 0; c < 3; ++c) k[c] = springs[c * n + i];
+        else
+            oracle_pseudo_springs(p, charge[i] / mass[i], k);
+        for (int a = 0; a < 3; ++a) {
+            diag[a][a] += mass[i] * k[a];
+            for (int b = 0; b < 3; ++b) H[(3 * i + a) * m + 3 * i + b] = diag[a][b] / mass[i];
+        }
+    }
 }
