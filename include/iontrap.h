@@ -70,6 +70,11 @@ extern "C" {
 #define IONTRAP_COULOMB_OFF 2u       /* non-interacting ions */
 #define IONTRAP_TRAP_OFF 4u          /* free ions: no trap field at all */
 #define IONTRAP_ALLOW_UNSTABLE 8u    /* skip the stability check at create */
+#define IONTRAP_PSEUDO 16u           /* pseudopotential trap (Eq. 2): static springs per species,
+                                        (Omega^2/4)(a_s + q_s^2/2) radially with a_s = rho a -
+                                        2 rho omega_z^2/Omega^2, q_s = rho q, and rho omega_z^2
+                                        axially; or the frequencies of
+                                        iontrap_set_pseudo_frequencies */
 
 /* iontrap_params.precision */
 #define IONTRAP_PREC_FP32 0  /* FP32 pair forces with compensated accumulation; FP64 state,
@@ -145,6 +150,47 @@ typedef struct {
  * species (unless IONTRAP_ALLOW_UNSTABLE).  Synchronous: waits for the handle's queued
  * work first.  Handles advanced by iontrap_step_many use the new forces as well. */
 int iontrap_set_params(iontrap_t *h, const iontrap_params *p, const iontrap_cooling *cooling);
+
+/* Pseudopotential trap given by its secular frequencies, one set per species
+ * (linearPseudoPT, Sec. 3 "Forces and fields": the pseudopotential frequencies depend on
+ * Q/M, so each species gets its own).  omega[3 n_species] = (wx, wy, wz) of each species,
+ * rad/s: the trap acceleration of an ion of species s is (-wx^2 x, -wy^2 y, -wz^2 z).  NULL
+ * returns to the Eq. 2 pseudopotential of the handle's Mathieu parameters.  The handle must
+ * carry IONTRAP_PSEUDO (EINVAL otherwise); a_n is evaluated again as by
+ * iontrap_set_params.  EINVAL for non-finite or non-positive frequencies, EUNSTABLE when
+ * w dt >= 2 on some axis (unless IONTRAP_ALLOW_UNSTABLE).  Synchronous. */
+int iontrap_set_pseudo_frequencies(iontrap_t *h, const double *omega);
+
+/* Minimisation (Sec. 3 "Minimisation"): damped dynamics that drives the ions to a minimum
+ * of the static potential -- the trap (IONTRAP_PSEUDO, or a static trap: IONTRAP_RF_OFF;
+ * EINVAL with the RF field on, whose minimum under damping is not the crystal's, as Sec. 3
+ * explains) plus the Coulomb pair energy -- with no bath and no laser.  Starting at rest,
+ * each iteration:
+ *   1. a = Coulomb (the handle's pair kernel, in its precision form) + trap, F_i = M_i a_i;
+ *      stop when |F| = sqrt(sum_i |F_i|^2) < ftol (newtons)
+ *   2. v = (v.F / F.F) F when v.F > 0 (sums over all ions), else v = 0
+ *   3. v += dt a; d = dt v; d and v are scaled by min(1, dmax / max_i |d_i|), so no ion
+ *      moves more than dmax (m) in one iteration; x += d
+ *   max_iters  iterations at most (>= 0)
+ *   dt         iteration time step, s (0 = the handle's dt); keep omega dt well below 1
+ *              for the stiffest trap axis
+ * On return x_n is the last position, v_n = 0, a_n is evaluated again under the handle's
+ * forces, and the step index is unchanged (minimisation is not time evolution).
+ * *iters (may be NULL) receives the iterations that moved the ions and *fnorm (may be
+ * NULL) |F| at the final positions.  Synchronous. */
+int iontrap_minimize(iontrap_t *h, int64_t max_iters, double dt, double dmax, double ftol, int64_t *iters,
+                     double *fnorm);
+
+/* Mass-weighted Hessian of the static potential at the current positions (Sec. 5
+ * "Normal modes of motion": the normal-mode frequencies are the square roots of its
+ * eigenvalues), FP64, computed on the device:
+ *   H[(3i+a) 3n + 3j+b] = d^2 V / dx_ia dx_jb / sqrt(M_i M_j),
+ *   V = sum_i M_i (kx x_i^2 + ky y_i^2 + kz z_i^2)/2 + sum_{i<j} k_e Q_i Q_j / |x_i - x_j|
+ * with k the trap springs of i's species (the pseudopotential, or the static RF-off trap).
+ * H[9 n^2] is a host array, row-major, symmetric.  EINVAL with the RF field on,
+ * IONTRAP_ETOOLARGE for n > 8192, ENOMEM if the 9 n^2 doubles cannot be allocated on the
+ * device.  Synchronous. */
+int iontrap_hessian(iontrap_t *h, double *H);
 
 /* Wait for the handle's stream and report device-side failures (ENONFINITE,
  * ETIMEOUT, ECUDA). */

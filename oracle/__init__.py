@@ -283,6 +283,8 @@ def minimize(x0, charge, mass, p: _Params, dt: float, dmax: float, ftol: float, 
     v = np.zeros_like(x)
     zero = np.zeros_like(x)
     fn = math.inf
+    p = _Params.from_buffer_copy(p)
+    p.gamma, p.T_bath = 0.0, 0.0  # no bath acts during minimisation
     for k in range(int(max_steps)):
         a = accel(x, zero, charge, mass, p, 0, 0.0, springs=springs)
         F = mass[None, :] * a

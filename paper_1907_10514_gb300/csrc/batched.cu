@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kBThreads)
       const TrapDev& tp = e.trap;
       const long long nf = s_n0[tid] + k + 1;
       const double cosv =
-          (tp.flags & (IONTRAP_RF_OFF | IONTRAP_TRAP_OFF)) ? 0.0 : cos(tp.Omega * ((double)nf * tp.dt));
+          (tp.flags & (IONTRAP_RF_OFF | IONTRAP_TRAP_OFF | IONTRAP_PSEUDO)) ? 0.0 : cos(tp.Omega * ((double)nf * tp.dt));
       for (int sp = 0; sp < e.nspecies; ++sp) trap_springs(tp, e.spc[sp], cosv, s_springs[tid][sp]);
     }
     __syncthreads();

@@ -14,6 +14,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <limits>
 #include <vector>
 
 #include "iontrap_internal.cuh"
@@ -31,6 +32,12 @@ const void* restore_kernel();
 cudaError_t launch_normals(unsigned long long seed, long long counter, const long long* d_ids, long long m,
                            int f64, double* d_z, cudaStream_t st);
 // persistent.cu
+cudaError_t launch_min_iteration(const StepArgs& s, const double* coul, void* scratch, double dt, double dmax,
+                                 double ftol, int f64, int b, cudaStream_t st);
+size_t min_scratch_bytes(long long n);
+size_t min_state_bytes();
+void min_progress(const void* host_state, long long* iters, double* fnorm, int* converged);
+cudaError_t launch_hessian(const StepArgs& s, double* d_H, cudaStream_t st);
 cudaError_t launch_gp(const StepArgs& a, unsigned* sync, int W, int S, int G, int Lmax, long long K,
                       cudaStream_t st);
 int gp_max_ctas(int W, int S, int Lmax, int max_lmax, long long max_k, int sms);
@@ -60,6 +67,12 @@ struct iontrap {
   int nspecies = 0;
   iontrap_species species[IONTRAP_MAX_SPECIES]{};
   iontrap_params p{};
+  // pseudopotential trap given by per-species secular angular frequencies (rad/s), used
+  // instead of Eq. 2 when pseudo_given (IONTRAP_PSEUDO only)
+  double pseudo_w[IONTRAP_MAX_SPECIES][3]{};
+  int pseudo_given = 0;
+  iontrap_cooling cooling[IONTRAP_MAX_SPECIES]{};  // per-species cooling set by iontrap_set_params
+  int cooling_given = 0;
   int f64 = 0;
   int device = 0;
   int sms = 0;
@@ -186,14 +199,42 @@ int check_params(const iontrap_species* sp, int ns, const iontrap_params* p) {
   if (p->dt == 0 && !(p->Omega > 0)) return IONTRAP_EINVAL;
   if (!(p->flags & (IONTRAP_RF_OFF | IONTRAP_TRAP_OFF)) && !(p->Omega > 0)) return IONTRAP_EINVAL;
   if (p->precision != IONTRAP_PREC_FP32 && p->precision != IONTRAP_PREC_FP64) return IONTRAP_EINVAL;
-  if (p->flags & ~(IONTRAP_RF_OFF | IONTRAP_COULOMB_OFF | IONTRAP_TRAP_OFF | IONTRAP_ALLOW_UNSTABLE))
+  if (p->flags & ~(IONTRAP_RF_OFF | IONTRAP_COULOMB_OFF | IONTRAP_TRAP_OFF | IONTRAP_ALLOW_UNSTABLE | IONTRAP_PSEUDO))
     return IONTRAP_EINVAL;
   return IONTRAP_OK;
+}
+
+// Spring constants (1/s^2) of the pseudopotential of Eq. 2 for a species whose
+// charge/mass is rho times that of species 0: (Omega^2/4)(a_m + q_m^2/2) along x and y
+// with q_m = rho q and a_m = rho a - 2 rho omega_z^2/Omega^2 (the axial field's radial
+// defocusing is Eq. 3's a_x = -a_z/2), rho omega_z^2 along z.
+void pseudo_springs(const iontrap_params* p, double rho, double k[3]) {
+  const double O2 = p->Omega * p->Omega;
+  const double wz2 = rho * p->omega_z * p->omega_z;
+  const double a_m = rho * p->a - 2.0 * wz2 / O2;
+  const double q_m = rho * p->q;
+  const double kr = O2 / 4.0 * (a_m + 0.5 * q_m * q_m);
+  k[0] = kr;
+  k[1] = kr;
+  k[2] = wz2;
+}
+
+// Static springs hold an ion under kick-drift-kick when 0 < k dt^2 < 4 on every axis.
+bool springs_stable(const double k[3], double dt) {
+  for (int c = 0; c < 3; ++c)
+    if (!(k[c] > 0.0) || !(k[c] * dt * dt < 4.0)) return false;
+  return true;
 }
 
 bool species_stable(const iontrap_params* p, double rho) {
   if (p->flags & IONTRAP_TRAP_OFF) return true;
   const double dt = effective_dt(p);
+  if (p->flags & IONTRAP_PSEUDO) {
+    if (rho == 0.0) return true;
+    double k[3];
+    pseudo_springs(p, rho, k);
+    return springs_stable(k, dt);
+  }
   const double wz2 = rho * p->omega_z * p->omega_z;
   if (rho == 0.0) return true;  // neutral: no trap force at all
   if (!(wz2 > 0) || !(std::fabs(2.0 - dt * dt * wz2) < 2.0)) return false;
@@ -371,6 +412,13 @@ void fill_forces(iontrap* h, const iontrap_params* p, const iontrap_cooling* coo
     d.lrate = ln;
     for (int c = 0; c < 3; ++c) d.kdir[c] = ln > 0.0 ? L[c] / ln : 0.0;
     if (ln > 0.0) laser = 1;
+    if (h->pseudo_given) {
+      for (int c = 0; c < 3; ++c) d.ks[c] = h->pseudo_w[s][c] * h->pseudo_w[s][c];
+    } else {
+      pseudo_springs(p, d.rho, d.ks);
+    }
+    d.mass = M;
+    d.z = z;
     d.w = (float)z;
     d.pad = 0.f;
   }
@@ -533,6 +581,14 @@ int prepare_kernels() {
   if (allow_large_clusters() != cudaSuccess) return IONTRAP_ECUDA;
   done = 1;
   return IONTRAP_OK;
+}
+
+// a_n again under the handle's current forces at its current state (as creation does).
+int reevaluate(iontrap* h) {
+  cudaError_t e = launch_prep(h, (int)(h->step & 1));
+  if (e == cudaSuccess) e = launch_mode(h, MODE_INIT, nullptr);
+  if (e != cudaSuccess) return cuda_status(h, e);
+  return iontrap_sync(h);
 }
 
 void free_all(iontrap* h) {
@@ -806,13 +862,128 @@ int iontrap_set_params(iontrap_t* h, const iontrap_params* p, const iontrap_cool
   const double dt = h->p.dt;
   h->p = *p;
   h->p.dt = dt;
+  h->cooling_given = cooling != nullptr;
+  for (int s = 0; s < h->nspecies && cooling; ++s) h->cooling[s] = cooling[s];
+  if (!(p->flags & IONTRAP_PSEUDO)) h->pseudo_given = 0;
   fill_forces(h, p, cooling);
   destroy_graph(h);
   // a_n under the new forces, as iontrap_create evaluates it at step0 = n
-  e = launch_prep(h, (int)(h->step & 1));
-  if (e == cudaSuccess) e = launch_mode(h, MODE_INIT, nullptr);
+  return reevaluate(h);
+}
+
+int iontrap_set_pseudo_frequencies(iontrap_t* h, const double* omega) {
+  if (!h) return IONTRAP_EINVAL;
+  if (h->status) return h->status;
+  if (!(h->p.flags & IONTRAP_PSEUDO)) return IONTRAP_EINVAL;
+  if (omega) {
+    for (int s = 0; s < 3 * h->nspecies; ++s)
+      if (!std::isfinite(omega[s]) || !(omega[s] > 0)) return IONTRAP_EINVAL;
+    if (!(h->p.flags & IONTRAP_ALLOW_UNSTABLE))
+      for (int s = 0; s < h->nspecies; ++s) {
+        const double k[3] = {omega[3 * s] * omega[3 * s], omega[3 * s + 1] * omega[3 * s + 1],
+                             omega[3 * s + 2] * omega[3 * s + 2]};
+        if (!springs_stable(k, h->p.dt)) return IONTRAP_EUNSTABLE;
+      }
+  } else if (!(h->p.flags & IONTRAP_ALLOW_UNSTABLE)) {
+    int ok = 0;
+    iontrap_stable(h->species, h->nspecies, &h->p, &ok);
+    if (!ok) return IONTRAP_EUNSTABLE;
+  }
+  DeviceGuard g(h->device);
+  cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_status(h, e);
-  return iontrap_sync(h);
+  h->pseudo_given = omega != nullptr;
+  for (int s = 0; s < h->nspecies && omega; ++s)
+    for (int c = 0; c < 3; ++c) h->pseudo_w[s][c] = omega[3 * s + c];
+  fill_forces(h, &h->p, h->cooling_given ? h->cooling : nullptr);
+  destroy_graph(h);
+  return reevaluate(h);
+}
+
+int iontrap_minimize(iontrap_t* h, int64_t max_iters, double dt, double dmax, double ftol, int64_t* iters,
+                     double* fnorm) {
+  if (!h || max_iters < 0 || !std::isfinite(dt) || dt < 0 || !std::isfinite(dmax) || !(dmax > 0) ||
+      !std::isfinite(ftol) || ftol < 0)
+    return IONTRAP_EINVAL;
+  if (h->status) return h->status;
+  if (!(h->p.flags & (IONTRAP_PSEUDO | IONTRAP_RF_OFF | IONTRAP_TRAP_OFF))) return IONTRAP_EINVAL;
+  int st = iontrap_sync(h);
+  if (st) return st;
+  DeviceGuard g(h->device);
+  const size_t vec = 3 * (size_t)h->n * sizeof(double);
+  if (!h->d_out && cudaMalloc(&h->d_out, vec) != cudaSuccess) return IONTRAP_ENOMEM;
+  void* scratch = nullptr;
+  if (cudaMalloc(&scratch, min_scratch_bytes(h->n)) != cudaSuccess) return IONTRAP_ENOMEM;
+  const double step_dt = dt > 0 ? dt : h->p.dt;
+  const int b = (int)(h->step & 1);  // the pair stream of parity n holds x_n
+  std::vector<unsigned char> hs(min_state_bytes());
+  long long done = 0;
+  double fn = 0.0;
+  int conv = 0;
+  cudaError_t e = cudaMemsetAsync(scratch, 0, min_scratch_bytes(h->n), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_v, 0, vec, h->stream);  // from rest
+  if (e == cudaSuccess && (h->p.flags & IONTRAP_COULOMB_OFF)) e = cudaMemsetAsync(h->d_out, 0, vec, h->stream);
+  if (e == cudaSuccess) e = launch_prep(h, b);
+  constexpr int64_t kChunk = 64;
+  for (int64_t launched = 0; e == cudaSuccess && launched < max_iters;) {
+    // up to kChunk iterations, then a look at the device state
+    const int64_t k = std::min<int64_t>(kChunk, max_iters - launched);
+    for (int64_t q = 0; q < k && e == cudaSuccess; ++q) {
+      if (!(h->p.flags & IONTRAP_COULOMB_OFF)) e = launch_mode(h, MODE_FORCES, h->d_out);
+      if (e == cudaSuccess)
+        e = launch_min_iteration(h->args, h->d_out, scratch, step_dt, dmax, ftol, h->f64, b, h->stream);
+    }
+    launched += k;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), scratch, hs.size(), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) break;
+    min_progress(hs.data(), &done, &fn, &conv);
+    if (conv) break;
+  }
+  if (e == cudaSuccess && !conv) {
+    // |F| at the final positions (the force kernel of one more iteration; it moves
+    // nothing when converged, and otherwise the count of moves is already max_iters)
+    if (!(h->p.flags & IONTRAP_COULOMB_OFF)) e = launch_mode(h, MODE_FORCES, h->d_out);
+    if (e == cudaSuccess)
+      e = launch_min_iteration(h->args, h->d_out, scratch, step_dt, dmax, std::numeric_limits<double>::infinity(),
+                               h->f64, b, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), scratch, hs.size(), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) {
+      long long d2;
+      int c2;
+      min_progress(hs.data(), &d2, &fn, &c2);
+    }
+  }
+  cudaFree(scratch);
+  if (e != cudaSuccess) return cuda_status(h, e);
+  if (iters) *iters = done;
+  if (fnorm) *fnorm = fn;
+  // the minimum at rest: v = 0, a_n evaluated under the handle's forces
+  e = cudaMemsetAsync(h->d_v, 0, vec, h->stream);
+  if (e != cudaSuccess) return cuda_status(h, e);
+  return reevaluate(h);
+}
+
+int iontrap_hessian(iontrap_t* h, double* H) {
+  if (!h || !H) return IONTRAP_EINVAL;
+  if (h->n > 8192) return IONTRAP_ETOOLARGE;
+  if (!(h->p.flags & (IONTRAP_PSEUDO | IONTRAP_RF_OFF | IONTRAP_TRAP_OFF))) return IONTRAP_EINVAL;
+  int st = iontrap_sync(h);
+  if (st) return st;
+  DeviceGuard g(h->device);
+  const size_t bytes = 9 * (size_t)h->n * (size_t)h->n * sizeof(double);
+  double* d_H = nullptr;
+  if (cudaMalloc(&d_H, bytes) != cudaSuccess) return IONTRAP_ENOMEM;
+  StepArgs a = h->args;
+  if (h->p.flags & IONTRAP_COULOMB_OFF)
+    for (int s = 0; s < IONTRAP_MAX_SPECIES; ++s) a.spc[s].z = 0.0;
+  cudaError_t e = launch_hessian(a, d_H, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(H, d_H, bytes, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(d_H);
+  if (e != cudaSuccess) return cuda_status(h, e);
+  return h->status;
 }
 
 int iontrap_sync(iontrap_t* h) {

@@ -33,6 +33,9 @@ struct SpeciesDev {
   double sigma;  // sqrt(2 gamma k_B T / (M dt)): std. dev. of the Langevin kick acceleration
   double lrate;  // laser-cooling rate |g|, 1/s (0: no laser on this species)
   double kdir[3];  // laser direction g / |g|
+  double ks[3];  // static spring constants of the pseudopotential trap (IONTRAP_PSEUDO), 1/s^2
+  double mass;   // kg
+  double z;      // charge number
   float w;       // z as float, the source weight in the FP32 pair stream
   float pad;
 };
@@ -226,7 +229,7 @@ __device__ __forceinline__ void segment_f32x2(const float4* __restrict__ sh, con
 // RF phase at the force time of a launch in the given mode.
 __device__ __forceinline__ double force_time_cos(const StepArgs& A, long long ns) {
   const long long nf = (A.mode == MODE_STEP) ? ns + 1 : ns;
-  if (A.trap.flags & (IONTRAP_RF_OFF | IONTRAP_TRAP_OFF)) return 0.0;
+  if (A.trap.flags & (IONTRAP_RF_OFF | IONTRAP_TRAP_OFF | IONTRAP_PSEUDO)) return 0.0;
   return cos(A.trap.Omega * ((double)nf * A.trap.dt));
 }
 
@@ -355,6 +358,10 @@ __device__ __forceinline__ void write_pair(const StepArgs& A, int b, long long i
 __device__ __forceinline__ void trap_springs(const TrapDev& tp, const SpeciesDev& sd, double cosv, double k[3]) {
   if (tp.flags & IONTRAP_TRAP_OFF) {
     k[0] = k[1] = k[2] = 0.0;
+    return;
+  }
+  if (tp.flags & IONTRAP_PSEUDO) {  // static pseudopotential springs (Eq. 2 or given frequencies)
+    k[0] = sd.ks[0], k[1] = sd.ks[1], k[2] = sd.ks[2];
     return;
   }
   const double rwz2 = __dmul_rn(sd.rho, tp.wz2);

@@ -62,6 +62,7 @@ __device__ __noinline__ bool gp_wait(const unsigned* ctr, unsigned target, int* 
 // Trap spring constant of component c (the c-th value trap_springs gives, same roundings).
 __device__ __forceinline__ double trap_spring_c(const TrapDev& tp, const SpeciesDev& sd, double cosv, int c) {
   if (tp.flags & IONTRAP_TRAP_OFF) return 0.0;
+  if (tp.flags & IONTRAP_PSEUDO) return sd.ks[c];
   const double rwz2 = __dmul_rn(sd.rho, tp.wz2);
   const double rq4 = __dmul_rn(tp.q4, sd.rho);
   const double qc2 = __dmul_rn(2.0 * tp.q, cosv);
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(32 * W, 16 / W) k_step_f32_gp(const __grid_con
   const TrapDev& tp = A.trap;
   const long long ns0 = *A.step;
   const bool forces = A.mode == MODE_FORCES;  // one force evaluation of the current positions (K = 1)
-  const bool rf = !(tp.flags & (IONTRAP_RF_OFF | IONTRAP_TRAP_OFF));
+  const bool rf = !(tp.flags & (IONTRAP_RF_OFF | IONTRAP_TRAP_OFF | IONTRAP_PSEUDO));
   if (!forces)
     for (long long k = tid; k < P.K; k += T) scos[k] = rf ? cos(tp.Omega * ((double)(ns0 + k + 1) * tp.dt)) : 0.0;
 

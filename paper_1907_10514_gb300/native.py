@@ -29,6 +29,7 @@ IONTRAP_RF_OFF = 1
 IONTRAP_COULOMB_OFF = 2
 IONTRAP_TRAP_OFF = 4
 IONTRAP_ALLOW_UNSTABLE = 8
+IONTRAP_PSEUDO = 16
 
 IONTRAP_PREC_FP32 = 0
 IONTRAP_PREC_FP64 = 1
@@ -87,6 +88,10 @@ SIGNATURES = {
                                       ctypes.POINTER(_vp)]),
     "iontrap_step": (ctypes.c_int, [_vp, ctypes.c_int64]),
     "iontrap_sync": (ctypes.c_int, [_vp]),
+    "iontrap_set_pseudo_frequencies": (ctypes.c_int, [_vp, _dp]),
+    "iontrap_minimize": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                        _i64p, _dp]),
+    "iontrap_hessian": (ctypes.c_int, [_vp, _dp]),
     "iontrap_set_params": (ctypes.c_int, [_vp, ctypes.POINTER(iontrap_params), ctypes.POINTER(iontrap_cooling)]),
     "iontrap_state": (ctypes.c_int, [_vp, _dp, _dp, _i64p, _dp]),
     "iontrap_forces": (ctypes.c_int, [_vp, _dp]),
@@ -241,6 +246,30 @@ def _cooling_array(cooling) -> Optional[ctypes.Array]:
 def iontrap_set_params(h, params: iontrap_params, cooling=None) -> None:
     """Change the trap and the per-species cooling between evolve calls."""
     _check(_lib.iontrap_set_params(h, ctypes.byref(params), _cooling_array(cooling)), "iontrap_set_params")
+
+
+def iontrap_set_pseudo_frequencies(h, omega=None) -> None:
+    """Per-species secular angular frequencies (n_species x 3, rad/s) of the
+    pseudopotential trap, or None for Eq. 2."""
+    w = None if omega is None else _f64(omega).reshape(-1)
+    _check(_lib.iontrap_set_pseudo_frequencies(h, None if w is None else _ptr(w)),
+           "iontrap_set_pseudo_frequencies")
+
+
+def iontrap_minimize(h, max_iters: int, dmax: float, ftol: float, dt: float = 0.0):
+    """Damped minimisation of the static potential; returns (iterations, |F|)."""
+    it_ = ctypes.c_int64()
+    fn = ctypes.c_double()
+    _check(_lib.iontrap_minimize(h, int(max_iters), float(dt), float(dmax), float(ftol), ctypes.byref(it_),
+                                 ctypes.byref(fn)), "iontrap_minimize")
+    return it_.value, fn.value
+
+
+def iontrap_hessian(h, n: int) -> np.ndarray:
+    """Mass-weighted Hessian (3n x 3n) of the static potential at the current state."""
+    H = np.empty((3 * n, 3 * n))
+    _check(_lib.iontrap_hessian(h, _ptr(H)), "iontrap_hessian")
+    return H
 
 
 def iontrap_sync(h) -> None:
@@ -464,6 +493,15 @@ class Simulation:
 
     def set_params(self, params, cooling=None) -> None:
         iontrap_set_params(self.handle, params, cooling)
+
+    def set_pseudo_frequencies(self, omega=None) -> None:
+        iontrap_set_pseudo_frequencies(self.handle, omega)
+
+    def minimize(self, max_iters: int, dmax: float, ftol: float, dt: float = 0.0):
+        return iontrap_minimize(self.handle, max_iters, dmax, ftol, dt)
+
+    def hessian(self) -> np.ndarray:
+        return iontrap_hessian(self.handle, self.n)
 
     def state(self):
         return iontrap_state(self.handle, self.n)
