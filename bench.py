@@ -374,6 +374,7 @@ def extra_measurements(it, torch, stream, sms, args):
         out["mix_n4096_species_cooling"] = {"ion_steps_per_s": n * k / (ms / 1e3), "us_per_timestep": 1e3 * ms / k,
                                             "timesteps": k, "tile": list(s.config()),
                                             "cooling": "Ca+: bath 1e5/s 1 mK + laser (1e5, 0, 0)/s; NH3+: bath 2e5/s 2 mK"}
+    out.update(modes_measurements(it, stream))
     wc = iongen.crystal_n32768()
     nc = wc.n
     pc = it.make_params(wc.trap, precision=it.IONTRAP_PREC_FP32)
@@ -404,6 +405,44 @@ def extra_measurements(it, torch, stream, sms, args):
                              "roofline_frac": gp / peak, "achieved_gpair_s": gp, "peak_gpair_s": peak,
                              "force_rel_rms_vs_oracle_max": max(errs),
                              "error_sample": "256 ions at steps 0, 142, ..., 999 of a 1000-step run"}
+    return out
+
+
+def modes_measurements(it, stream):
+    """The minimiser on a 1024-ion Ca+ crystal in a pseudopotential trap (Sec. 3
+    "Minimisation") and the device Hessian of a 2048-ion crystal (Sec. 5 "Normal modes")."""
+    import iongen
+    out = {}
+    n = 1024
+    w0 = 2 * math.pi * 0.3e6
+    freqs = [(1.2 * w0, 1.3 * w0, w0)]
+    trap = iongen.Trap(Omega=iongen.OMEGA_RF, a=0.0, q=0.3, omega_z=2 * math.pi * 0.2e6, gamma=0.0, T_bath=0.0,
+                       dt=iongen.rf_period_dt(iongen.OMEGA_RF), seed=5)
+    x0 = iongen.gaussian_positions(n, 60e-6, seed=5)
+    sp = np.zeros(n, np.uint8)
+    e, eps0, amu = 1.602176634e-19, 8.8541878128e-12, 1.66053906660e-27
+    m = iongen.CA40.mass_amu * amu
+    l = (e * e / (4 * math.pi * eps0 * m * w0 ** 2)) ** (1 / 3)
+    fscale = m * w0 ** 2 * l
+    p = it.make_params(trap, flags=it.IONTRAP_PSEUDO)
+    with it.Simulation([iongen.CA40], sp, x0, None, p, stream=stream) as s:
+        s.set_pseudo_frequencies(freqs)
+        t0 = time.perf_counter()
+        iters, fn = s.minimize(20000, 0.05 * l, 1e-4 * fscale * math.sqrt(n), dt=5 * trap.dt)
+        wall = time.perf_counter() - t0
+    out["minimize_crystal_n1024"] = {"iterations": iters, "seconds": wall, "us_per_iteration": 1e6 * wall / max(iters, 1),
+                                     "force_norm_over_scale": fn / fscale,
+                                     "note": "FP32 pair kernel + 3 reduction/update kernels per iteration, "
+                                             "host check every 64 iterations"}
+    nh = 2048
+    xh = iongen.gaussian_positions(nh, 80e-6, seed=6)
+    with it.Simulation([iongen.CA40], np.zeros(nh, np.uint8), xh, None, p, stream=stream) as s:
+        s.hessian()
+        t0 = time.perf_counter()
+        s.hessian()
+        wall = time.perf_counter() - t0
+    out["hessian_n2048"] = {"seconds": wall, "bytes": 9 * nh * nh * 8,
+                            "note": "FP64 device kernels + device-to-host copy of the 3n x 3n matrix"}
     return out
 
 
