@@ -192,6 +192,33 @@ int iontrap_minimize(iontrap_t *h, int64_t max_iters, double dt, double dmax, do
  * device.  Synchronous. */
 int iontrap_hessian(iontrap_t *h, double *H);
 
+/* iontrap_step_record fields */
+#define IONTRAP_REC_X 1u     /* positions x_s */
+#define IONTRAP_REC_V 2u     /* velocities v_s */
+#define IONTRAP_REC_VAVG 4u  /* velocities averaged over the last avg_steps steps */
+
+/* evolve(N) with dump and timeAvg (Sec. 3 "Writing/reading data"): enqueue n_steps steps
+ * and, after every `every` steps (the dump interval), write a record of the state s
+ * reached to d_out.  A record holds, in this order, the fields requested:
+ *   IONTRAP_REC_X     x_s [3n]
+ *   IONTRAP_REC_V     v_s [3n]
+ *   IONTRAP_REC_VAVG  (1/W) sum_{m=s-W+1..s} v_m [3n], W = avg_steps, the time average of
+ *                     the velocity over the W steps ending at s (timeAvg; W = 20 steps is
+ *                     one RF period at dt = T_RF/20: the secular velocity)
+ * each [3][n] SoA in id order, so record k (0-based, state step0 + (k+1) every) starts at
+ * d_out + k F 3n with F the number of fields.  d_out is a DEVICE array of
+ * (n_steps / every) F 3n doubles owned by the caller; it must stay valid until the
+ * stream reaches the last record (iontrap_sync).  The average uses
+ * sum v_m = [(x_s - x_{s-W}) + (x_{s+1} - x_{s-W+1})] / (2 dt), exact for kick-drift-kick
+ * Verlet (v_m is the mean of its two half-step velocities), so the step kernels do no
+ * extra work; a snapshot of x_{s-W} is taken W steps before each record (the handle
+ * holds 6n doubles for it).  EINVAL when every < 1, n_steps is not a multiple of every,
+ * fields is empty or unknown, or avg_steps is not in [1, every] with IONTRAP_REC_VAVG.
+ * Asynchronous like iontrap_step; forms and results are those of iontrap_step (the
+ * steps are enqueued in chunks between records). */
+int iontrap_step_record(iontrap_t *h, int64_t n_steps, int64_t every, uint32_t fields, int64_t avg_steps,
+                        double *d_out);
+
 /* Wait for the handle's stream and report device-side failures (ENONFINITE,
  * ETIMEOUT, ECUDA). */
 int iontrap_sync(iontrap_t *h);

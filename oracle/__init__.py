@@ -15,6 +15,8 @@ Functions follow the paper:
   * ``linear_pt``      -- Mathieu parameters of a trap given by voltages (Eq. 3)
   * ``pseudo_springs`` -- the pseudopotential of the trap (Eq. 2); ``springs_arrays``
                           a pseudopotential trap given by per-species frequencies
+  * ``record``         -- dump and timeAvg (Sec. 3 "Writing/reading data"): strided
+                          states and windowed velocity averages, summed step by step
   * ``minimize``       -- damped minimisation of the static potential (Sec. 3)
   * ``hessian``        -- mass-weighted Hessian whose eigenvalues are the squared
                           normal-mode frequencies (Sec. 5 "Normal modes of motion")
@@ -263,6 +265,34 @@ def run(x0, v0, charge, mass, p: _Params, nsteps: int, step0: int = 0, a0=None, 
                         _dp(work))
     del keep, keep2
     return x, v, a
+
+
+def record(x0, v0, charge, mass, p: _Params, nsteps: int, every: int, avg_steps: int, step0: int = 0,
+           a0=None, cooling=None, springs=None):
+    """Evolve like ``run`` and record, after every ``every`` steps (dump, Sec. 3
+    "Writing/reading data"), the positions, the velocities and the time average of the
+    full-step velocities over the last ``avg_steps`` steps (timeAvg), summed step by step.
+    Returns (X, V, VAVG), each (nsteps // every, 3, n), and the final (x, v, a)."""
+    x, v = _c64(x0).copy(), _c64(v0).copy()
+    a = a0
+    X, V, VA = [], [], []
+    step = step0
+    for _ in range(int(nsteps) // int(every)):
+        if every > avg_steps:
+            x, v, a = run(x, v, charge, mass, p, every - avg_steps, step0=step, a0=a, cooling=cooling,
+                          springs=springs)
+            step += every - avg_steps
+        elif a is None:
+            x, v, a = run(x, v, charge, mass, p, 0, step0=step, cooling=cooling, springs=springs)
+        vsum = np.zeros_like(x)
+        for _k in range(int(avg_steps)):
+            x, v, a = run(x, v, charge, mass, p, 1, step0=step, a0=a, cooling=cooling, springs=springs)
+            step += 1
+            vsum += v
+        X.append(x.copy())
+        V.append(v.copy())
+        VA.append(vsum / avg_steps)
+    return np.array(X), np.array(V), np.array(VA), (x, v, a)
 
 
 def minimize(x0, charge, mass, p: _Params, dt: float, dmax: float, ftol: float, max_steps: int,

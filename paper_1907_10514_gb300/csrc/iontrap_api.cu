@@ -38,6 +38,10 @@ size_t min_scratch_bytes(long long n);
 size_t min_state_bytes();
 void min_progress(const void* host_state, long long* iters, double* fnorm, int* converged);
 cudaError_t launch_hessian(const StepArgs& s, double* d_H, cudaStream_t st);
+cudaError_t launch_snapshot(long long n, const double* x, const double* v, const double* a, double* snap, double dt,
+                            cudaStream_t st);
+cudaError_t launch_record(long long n, const double* x, const double* v, const double* a, const double* snap,
+                          double* out, unsigned fields, long long W, double dt, cudaStream_t st);
 cudaError_t launch_gp(const StepArgs& a, unsigned* sync, int W, int S, int G, int Lmax, long long K,
                       cudaStream_t st);
 int gp_max_ctas(int W, int S, int Lmax, int max_lmax, long long max_k, int sms);
@@ -94,6 +98,7 @@ struct iontrap {
   int T = 128, I = 1, packed = 0, jsplit = 128, fused = 1, pdl = 0, use_graph = 1;
   GpShape gp{};                 // fused = 4
   unsigned* d_gsync = nullptr;  // fused = 4: step and group counters (zero between launches)
+  double* d_snap = nullptr;     // iontrap_step_record: x_{s-W}, x_{s-W+1} [2][3][n]
   StepArgs args{};
   // graph of kGraphSteps chained steps
   cudaGraph_t graph = nullptr;
@@ -594,7 +599,7 @@ int reevaluate(iontrap* h) {
 void free_all(iontrap* h) {
   destroy_graph(h);
   void* ptrs[] = {h->d_x, h->d_v, h->d_a, h->d_out, h->d_sp, h->d_pair[0], h->d_pair[1],
-                  h->d_part, h->d_cnt, h->d_done, h->d_step, h->d_err, h->d_gsync};
+                  h->d_part, h->d_cnt, h->d_done, h->d_step, h->d_err, h->d_gsync, h->d_snap};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -983,6 +988,35 @@ int iontrap_hessian(iontrap_t* h, double* H) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   cudaFree(d_H);
   if (e != cudaSuccess) return cuda_status(h, e);
+  return h->status;
+}
+
+int iontrap_step_record(iontrap_t* h, int64_t n_steps, int64_t every, uint32_t fields, int64_t avg_steps,
+                        double* d_out) {
+  if (!h || !d_out || n_steps < 0 || every < 1 || n_steps % every != 0) return IONTRAP_EINVAL;
+  const uint32_t known = IONTRAP_REC_X | IONTRAP_REC_V | IONTRAP_REC_VAVG;
+  if (fields == 0 || (fields & ~known)) return IONTRAP_EINVAL;
+  const bool avg = fields & IONTRAP_REC_VAVG;
+  if (avg && (avg_steps < 1 || avg_steps > every)) return IONTRAP_EINVAL;
+  if (h->status) return h->status;
+  DeviceGuard g(h->device);
+  const size_t n3 = 3 * (size_t)h->n;
+  if (avg && !h->d_snap && cudaMalloc(&h->d_snap, 2 * n3 * sizeof(double)) != cudaSuccess) return IONTRAP_ENOMEM;
+  const int nf = ((fields & IONTRAP_REC_X) ? 1 : 0) + ((fields & IONTRAP_REC_V) ? 1 : 0) + (avg ? 1 : 0);
+  for (int64_t k = 0; k < n_steps / every; ++k) {
+    int st;
+    if (avg) {
+      if (every > avg_steps && (st = iontrap_step(h, every - avg_steps))) return st;
+      cudaError_t e = launch_snapshot(h->n, h->d_x, h->d_v, h->d_a, h->d_snap, h->p.dt, h->stream);
+      if (e != cudaSuccess) return cuda_status(h, e);
+      if ((st = iontrap_step(h, avg_steps))) return st;
+    } else if ((st = iontrap_step(h, every))) {
+      return st;
+    }
+    cudaError_t e = launch_record(h->n, h->d_x, h->d_v, h->d_a, h->d_snap, d_out + (size_t)k * nf * n3, fields,
+                                  avg ? avg_steps : 0, h->p.dt, h->stream);
+    if (e != cudaSuccess) return cuda_status(h, e);
+  }
   return h->status;
 }
 
@@ -1383,7 +1417,7 @@ int iontrap_device_bytes(const iontrap_t* h, int64_t* bytes) {
   if (!h || !bytes) return IONTRAP_EINVAL;
   const int64_t vec = 3 * h->n * (int64_t)sizeof(double);
   const int64_t pair = h->n * (int64_t)(h->f64 ? sizeof(double4_32a) : 2 * sizeof(float4));
-  *bytes = 3 * vec + (h->d_out ? vec : 0) + h->n + 2 * pair + (int64_t)h->part_bytes +
+  *bytes = 3 * vec + (h->d_out ? vec : 0) + (h->d_snap ? 2 * vec : 0) + h->n + 2 * pair + (int64_t)h->part_bytes +
            (int64_t)h->cnt_len * (int64_t)sizeof(unsigned) + 64 + (h->d_gsync ? (int64_t)kGpSyncBytes : 0);
   return IONTRAP_OK;
 }

@@ -31,6 +31,10 @@ IONTRAP_TRAP_OFF = 4
 IONTRAP_ALLOW_UNSTABLE = 8
 IONTRAP_PSEUDO = 16
 
+IONTRAP_REC_X = 1
+IONTRAP_REC_V = 2
+IONTRAP_REC_VAVG = 4
+
 IONTRAP_PREC_FP32 = 0
 IONTRAP_PREC_FP64 = 1
 
@@ -92,6 +96,7 @@ SIGNATURES = {
     "iontrap_minimize": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                         _i64p, _dp]),
     "iontrap_hessian": (ctypes.c_int, [_vp, _dp]),
+    "iontrap_step_record": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint32, ctypes.c_int64, _vp]),
     "iontrap_set_params": (ctypes.c_int, [_vp, ctypes.POINTER(iontrap_params), ctypes.POINTER(iontrap_cooling)]),
     "iontrap_state": (ctypes.c_int, [_vp, _dp, _dp, _i64p, _dp]),
     "iontrap_forces": (ctypes.c_int, [_vp, _dp]),
@@ -270,6 +275,13 @@ def iontrap_hessian(h, n: int) -> np.ndarray:
     H = np.empty((3 * n, 3 * n))
     _check(_lib.iontrap_hessian(h, _ptr(H)), "iontrap_hessian")
     return H
+
+
+def iontrap_step_record(h, n_steps: int, every: int, fields: int, avg_steps: int, d_out: int) -> None:
+    """Enqueue n_steps steps with a record every ``every`` steps written to the device
+    array at address d_out ((n_steps // every) x fields x 3 x n doubles)."""
+    _check(_lib.iontrap_step_record(h, int(n_steps), int(every), int(fields), int(avg_steps), ctypes.c_void_p(d_out)),
+           "iontrap_step_record")
 
 
 def iontrap_sync(h) -> None:
@@ -502,6 +514,10 @@ class Simulation:
 
     def hessian(self) -> np.ndarray:
         return iontrap_hessian(self.handle, self.n)
+
+    def step_record(self, n_steps: int, every: int, fields: int, avg_steps: int, d_out: int) -> "Simulation":
+        iontrap_step_record(self.handle, n_steps, every, fields, avg_steps, d_out)
+        return self
 
     def state(self):
         return iontrap_state(self.handle, self.n)

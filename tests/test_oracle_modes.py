@@ -234,3 +234,36 @@ def test_kicked_chain_spectrum_peaks_at_hessian_frequencies():
              and spec[i] > 0.02 * spec.max()]
     for w in (1.0, math.sqrt(3), math.sqrt(29 / 5)):
         assert min(abs(f - w) for f in peaks) < 1.5 * res, (w, peaks)
+
+
+# ------------------------------------------------------------------ dump / timeAvg
+
+def test_record_time_average_of_uniform_motion_and_harmonic_motion():
+    """Sec. 3 'Writing/reading data' (timeAvg): a free ion's averaged velocity is its
+    velocity; on a static spring k the kick-drift-kick trajectory is x_m = A cos(m th + ph)
+    with cos th = 1 - k dt^2/2 and its full-step velocity (x_{m+1} - x_{m-1})/(2 dt), whose
+    window mean has a closed form (geometric sums) that the recorded average must match."""
+    sp = np.zeros(1, np.uint8)
+    q_, m_ = np.array([E]), np.array([M_CA])
+    pfree = _p(oracle.TRAP_OFF)
+    X, V, VA, _ = oracle.record(np.zeros((3, 1)), np.array([[0.3], [-0.2], [0.7]]), q_, m_, pfree, 60, 20, 20)
+    np.testing.assert_allclose(VA[:, :, 0], np.tile([0.3, -0.2, 0.7], (3, 1)), rtol=1e-14)
+    k = 4.0e12
+    springs = np.full((3, 1), k)
+    x0 = np.array([[2e-6], [-1e-6], [3e-6]])
+    v0 = np.array([[0.5], [0.2], [-0.1]])
+    every, W, K = 30, 20, 4
+    X, V, VA, _ = oracle.record(x0, v0, q_, m_, _p(0), every * K, every, W, springs=springs)
+    th = math.acos(1 - k * DT ** 2 / 2)
+    # x_m = A cos(m th) + B sin(m th): x_0 given, x_1 = x_0 + dt (v_0 + dt/2 a_0), a_0 = -k x_0
+    x1 = x0[:, 0] + DT * (v0[:, 0] - DT / 2 * k * x0[:, 0])
+    A = x0[:, 0]
+    B = (x1 - A * math.cos(th)) / math.sin(th)
+
+    def xm(m):
+        return A * math.cos(m * th) + B * math.sin(m * th)
+    for r in range(K):
+        s = (r + 1) * every
+        expect = sum((xm(mm + 1) - xm(mm - 1)) / (2 * DT) for mm in range(s - W + 1, s + 1)) / W
+        np.testing.assert_allclose(VA[r, :, 0], expect, rtol=1e-9, atol=1e-12)
+        np.testing.assert_allclose(X[r, :, 0], xm(s), rtol=1e-9, atol=1e-18)
