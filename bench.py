@@ -52,6 +52,9 @@ NOMINAL_SM_MHZ = 2070.0
 PROFILED_TRAFFIC = {
     # one launch per timestep (profiles/step_f32_cw_mix_n4096.md)
     (128, 2, 1, 512, 3): (485376 + 0, "DRAM bytes per timestep launch (ncu, profiles/step_f32_cw_mix_n4096.md)"),
+    # row-persistent form: a 20-timestep launch read 489 472 B and wrote 2 816 B
+    (512, 1, 1, 32, 5): ((489472 + 2816) / 20, "DRAM bytes per timestep, from a 20-timestep launch of the "
+                                               "row-persistent kernel (ncu, profiles/step_f32_rp_mix_n4096.md)"),
     # grid-persistent form: a 20-timestep launch read 496 896 B and wrote 113 152 B
     (512, 2, 1, 108, 4): ((496896 + 113152) / 20, "DRAM bytes per timestep, from a 20-timestep launch of the "
                                                   "persistent kernel (ncu, profiles/step_f32_gp_mix_n4096.md)"),
@@ -312,7 +315,7 @@ def run_gpu(args):
                       "(bar 1e-5); trajectories: tests/test_gpu_parity.py",
         "e2e": {"value": e2e_value, "unit": "ion-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": args.steps * (-(-nsteps // GP_STEPS_PER_LAUNCH) if cfg[4] == 4 else nsteps),
+        "gpu_launches": args.steps * (-(-nsteps // GP_STEPS_PER_LAUNCH) if cfg[4] >= 4 else nsteps),
         "roofline": {"bound": "alu", "achieved": achieved_gpairs, "peak": peak_gpairs,
                      "unit": "Gpair/s", "frac": achieved_gpairs / peak_gpairs,
                      "traffic": PROFILED_TRAFFIC.get(tuple(cfg[:5]), (None, None))[0],

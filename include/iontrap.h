@@ -320,6 +320,14 @@ typedef struct {
                                     each CTA sums a group of 2*threads ions against one
                                     segment and integrates an equal share of its group; no
                                     CUDA graph, pdl ignored; not with IONTRAP_COULOMB_OFF.
+                                 5: row-persistent: one cooperative launch runs up to 1000
+                                    steps (threads = 256 or 512, ions_per_thread = 1,
+                                    packed = 1, jsplit = R <= 32 ions per CTA, ceil(n / R)
+                                    CTAs resident at once); each CTA sums its R ions over
+                                    every j, its warps splitting the j-range, merges the warp
+                                    partials in shared memory and integrates; one grid-wide
+                                    counter per step; creation and iontrap_forces use form 1
+                                    over 512-ion j-ranges; not with IONTRAP_COULOMB_OFF.
                                  The FP64 form supports 1 only. */
     int32_t pdl;              /* 1: consecutive step kernels use programmatic dependent launch
                                  (default 0: measured slower on GB300 for these grids) */
@@ -412,7 +420,7 @@ int iontrap_forces_noalloc(const iontrap_species *species, int n_species, const 
                            const double *d_x, int64_t n, double *d_acc, void *cuda_stream);
 
 /* Profiling hook: run ONE step with per-CTA phase timestamps (%globaltimer, ns) and copy
- * them to marks[cap] (EINVAL in the grid-persistent form 4).  Layout: 4 marks per force-kernel CTA, CTA id = y*grid.x + x
+ * them to marks[cap] (EINVAL in the persistent forms 4 and 5).  Layout: 4 marks per force-kernel CTA, CTA id = y*grid.x + x
  * (start after the grid dependency wait, end of the pair loop, start of the fused
  * epilogue or 0, end of the fused epilogue or 0), then 2 per epilogue-kernel CTA (start,
  * end) when the configuration is not fused.  *n_force and *n_epi receive the counts.

@@ -45,6 +45,9 @@ cudaError_t launch_record(long long n, const double* x, const double* v, const d
 cudaError_t launch_gp(const StepArgs& a, unsigned* sync, int W, int S, int G, int Lmax, long long K,
                       cudaStream_t st);
 int gp_max_ctas(int W, int S, int Lmax, int max_lmax, long long max_k, int sms);
+cudaError_t launch_rp(const StepArgs& a, unsigned* sync, int W, int R, int G, int JW, long long K, cudaStream_t st);
+int rp_max_ctas(int W, int JW, int max_jw, long long max_k, int sms);
+size_t rp_smem_bytes(int W, int JW, long long K);
 }  // namespace it
 
 using namespace it;
@@ -65,6 +68,12 @@ static constexpr size_t kGpSyncBytes = 32 * (1 + kGpMaxGroups) * sizeof(unsigned
 struct GpShape {
   int W = 0, S = 0, G = 0, Lmax = 0;
 };
+
+// row-persistent form (fused = 5): W warps, R ions per CTA, G CTAs, JW j per warp
+struct RpShape {
+  int W = 0, R = 0, G = 0, JW = 0;
+};
+static constexpr int64_t kRpInitJsplit = 512;  // j-range per CTA of its creation-time / force evaluation
 
 struct iontrap {
   int64_t n = 0;
@@ -97,6 +106,7 @@ struct iontrap {
   // launch configuration
   int T = 128, I = 1, packed = 0, jsplit = 128, fused = 1, pdl = 0, use_graph = 1;
   GpShape gp{};                 // fused = 4
+  RpShape rp{};                 // fused = 5
   unsigned* d_gsync = nullptr;  // fused = 4: step and group counters (zero between launches)
   double* d_snap = nullptr;     // iontrap_step_record: x_{s-W}, x_{s-W+1} [2][3][n]
   StepArgs args{};
@@ -308,6 +318,26 @@ bool tuned_config(int64_t n, int f64, int dev, iontrap_config* c) {
 // blocks keep the FP64 epilogue of the last CTA short, large ones reuse each staged j
 // over more ions.  The number of j-splits S makes the grid a multiple of the SM count
 // (equal work per SM) with at least two CTAs per SM where n allows.
+// The largest j-range per warp (a multiple of 4) whose launch fits in 227 KB of shared memory.
+int rp_max_jw(int W) {
+  const size_t fixed = rp_smem_bytes(W, 0, kGpMaxSteps);
+  return (int)(((227 * 1024 - fixed) / (28 * (size_t)W)) & ~(size_t)3);
+}
+
+bool rp_shape(int64_t n, int f64, unsigned flags, int sms, int T, int I, int packed, int64_t R, RpShape* out) {
+  if (f64 || (flags & IONTRAP_COULOMB_OFF) || (T != 256 && T != 512) || I != 1 || packed != 1 || R < 1 || R > 32 ||
+      R > n)
+    return false;
+  const int W = T / 32;
+  // a multiple of 4 j per warp: the pair loop reads four j per 16-byte shared load, and
+  // every warp's 7 arrays of JW floats then start on 16-byte boundaries
+  const int64_t JW = (cdiv(n, W) + 3) / 4 * 4, G = cdiv(n, R);
+  if (JW < 2 || JW > rp_max_jw(W)) return false;
+  if (G > rp_max_ctas(W, (int)JW, rp_max_jw(W), kGpMaxSteps, sms)) return false;
+  out->W = W, out->R = (int)R, out->G = (int)G, out->JW = (int)JW;
+  return true;
+}
+
 void default_config(int64_t n, int f64, int sms, int* T, int* I, int* packed, int* jsplit, int* fused,
                     int allow_persistent = 1) {
   *fused = 1;
@@ -362,6 +392,18 @@ void default_config(int64_t n, int f64, int sms, int* T, int* I, int* packed, in
       *jsplit = (int)cdiv(n, S);
     }
   }
+  // n <= 32 x SMs: the row-persistent form (32 ions per CTA) measured fastest of all
+  // (us/step on GB300 against the choice above: n = 256: 3.7 vs 10.8; 1024: 6.2 vs 13.4;
+  // 2048: 9.1 vs 9.7; 4096: 15.0 vs 17.3; 4864: 17.7 vs 22.7)
+  if (!f64 && allow_persistent && n <= 32 * (int64_t)sms) {
+    const int W = n < 512 ? 8 : 16;
+    const int64_t R = std::min<int64_t>(32, n);
+    RpShape rs;
+    if (rp_shape(n, 0, 0, sms, 32 * W, 1, 1, R, &rs)) {
+      *T = 32 * W, *I = 1, *packed = 1, *fused = 5;
+      *jsplit = (int)R;
+    }
+  }
 }
 
 int set_status(iontrap* h, int st) {
@@ -376,6 +418,7 @@ int cuda_status(iontrap* h, cudaError_t e) {
 
 int64_t splits_of(const iontrap* h) {
   if (h->p.flags & IONTRAP_COULOMB_OFF) return 1;
+  if (h->fused == 5) return cdiv(h->n, kRpInitJsplit);
   return cdiv(h->n, h->jsplit);
 }
 
@@ -383,7 +426,7 @@ int64_t splits_of(const iontrap* h) {
 // all hold the same 32*I ions, and the grid-persistent form (fused = 4) whose initial
 // evaluation at creation uses the last-CTA form with 128 x 2 ions
 int64_t iblock_ions(const iontrap* h) {
-  if (h->fused == 4) return 256;
+  if (h->fused >= 4) return 256;
   return h->fused == 3 ? 32 * (int64_t)h->I : (int64_t)h->T * h->I;
 }
 
@@ -468,8 +511,13 @@ int alloc_scratch(iontrap* h) {
   }
   if (cudaMemsetAsync(h->d_cnt, 0, h->cnt_len * sizeof(unsigned), h->stream) != cudaSuccess)
     return IONTRAP_ECUDA;
-  if (h->fused == 4) {
-    if (!gp_shape(h->n, h->f64, h->p.flags, h->sms, h->T, h->I, h->packed, h->jsplit, &h->gp)) return IONTRAP_EINVAL;
+  if (h->fused == 4 || h->fused == 5) {
+    if (h->fused == 4 &&
+        !gp_shape(h->n, h->f64, h->p.flags, h->sms, h->T, h->I, h->packed, h->jsplit, &h->gp))
+      return IONTRAP_EINVAL;
+    if (h->fused == 5 &&
+        !rp_shape(h->n, h->f64, h->p.flags, h->sms, h->T, h->I, h->packed, h->jsplit, &h->rp))
+      return IONTRAP_EINVAL;
     if (!h->d_gsync) {
       if (cudaMalloc(&h->d_gsync, kGpSyncBytes) != cudaSuccess) return IONTRAP_ENOMEM;
       if (cudaMemsetAsync(h->d_gsync, 0, kGpSyncBytes, h->stream) != cudaSuccess) return IONTRAP_ECUDA;
@@ -477,7 +525,9 @@ int alloc_scratch(iontrap* h) {
   }
   h->args.part = h->d_part;
   h->args.cnt = h->d_cnt;
-  h->args.jsplit = (h->p.flags & IONTRAP_COULOMB_OFF) ? (int)std::min<int64_t>(h->n, 1 << 30) : h->jsplit;
+  h->args.jsplit = (h->p.flags & IONTRAP_COULOMB_OFF) ? (int)std::min<int64_t>(h->n, 1 << 30)
+                   : h->fused == 5                   ? (int)std::min<int64_t>(h->n, kRpInitJsplit)
+                                                     : h->jsplit;
   h->args.nsplit = (int)splits;
   return IONTRAP_OK;
 }
@@ -485,8 +535,11 @@ int alloc_scratch(iontrap* h) {
 // Launch one step kernel with programmatic dependent launch, so that consecutive steps
 // overlap one grid's launch with the previous grid's tail.
 cudaError_t launch_step_on(iontrap* h, StepArgs& a, cudaStream_t st) {
-  if (h->fused == 4) {
-    if (a.mode != MODE_INIT) return launch_gp(a, h->d_gsync, h->gp.W, h->gp.S, h->gp.G, h->gp.Lmax, 1, st);
+  if (h->fused == 5 && a.mode == MODE_STEP)
+    return launch_rp(a, h->d_gsync, h->rp.W, h->rp.R, h->rp.G, h->rp.JW, 1, st);
+  if (h->fused == 4 || h->fused == 5) {
+    if (h->fused == 4 && a.mode != MODE_INIT)
+      return launch_gp(a, h->d_gsync, h->gp.W, h->gp.S, h->gp.G, h->gp.Lmax, 1, st);
     // the initial evaluation (at creation or after restore): the last-CTA form over the same j-segments
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)cdiv(h->n, 256), (unsigned)splits_of(h), 1);
@@ -612,7 +665,7 @@ namespace it {
 // Give a handle the default configuration without the grid-persistent form (for callers
 // that run many simulations side by side on separate streams).
 int use_nonpersistent_default(iontrap* h) {
-  if (!h || h->fused != 4) return IONTRAP_OK;
+  if (!h || h->fused < 4) return IONTRAP_OK;
   iontrap_config c{};
   const int st = iontrap_default_config(h->n, h->f64 ? IONTRAP_PREC_FP64 : IONTRAP_PREC_FP32, h->p.flags, 0, &c);
   return st ? st : iontrap_set_config(h, &c);
@@ -718,10 +771,16 @@ int iontrap_create(const iontrap_species* species, int n_species, const uint8_t*
     iontrap_config tc{};
     GpShape gs;
     const bool tuned = tuned_config(n, h->f64, h->device, &tc);
+    RpShape rs;
     if (tuned && tc.fused == 4) {
       if (gp_shape(n, h->f64, p->flags, h->sms, tc.threads, tc.ions_per_thread, tc.packed, tc.jsplit, &gs)) {
         h->T = tc.threads, h->I = tc.ions_per_thread, h->packed = tc.packed, h->jsplit = tc.jsplit;
         h->fused = 4, h->pdl = 0, h->use_graph = 0;
+      }
+    } else if (tuned && tc.fused == 5) {
+      if (rp_shape(n, h->f64, p->flags, h->sms, tc.threads, tc.ions_per_thread, tc.packed, tc.jsplit, &rs)) {
+        h->T = tc.threads, h->I = tc.ions_per_thread, h->packed = tc.packed, h->jsplit = tc.jsplit;
+        h->fused = 5, h->pdl = 0, h->use_graph = 0;
       }
     } else if (tuned && step_kernel(h->f64, tc.threads, tc.ions_per_thread, tc.packed, tc.fused) &&
         tc.jsplit >= 1 && tc.jsplit <= n && (!h->f64 || tc.jsplit <= kMaxJsplitF64) &&
@@ -809,13 +868,14 @@ int iontrap_step(iontrap_t* h, int64_t n_steps) {
   if (!h || n_steps < 0) return IONTRAP_EINVAL;
   if (h->status) return h->status;
   DeviceGuard g(h->device);
-  if (h->fused == 4) {  // grid-persistent form: up to kGpMaxSteps steps per cooperative launch
+  if (h->fused == 4 || h->fused == 5) {  // persistent forms: up to kGpMaxSteps steps per cooperative launch
     StepArgs a = h->args;
     a.mode = MODE_STEP;
     a.out = nullptr;
     while (n_steps > 0) {
       const int64_t k = std::min<int64_t>(n_steps, kGpMaxSteps);
-      cudaError_t e = launch_gp(a, h->d_gsync, h->gp.W, h->gp.S, h->gp.G, h->gp.Lmax, k, h->stream);
+      cudaError_t e = h->fused == 4 ? launch_gp(a, h->d_gsync, h->gp.W, h->gp.S, h->gp.G, h->gp.Lmax, k, h->stream)
+                                    : launch_rp(a, h->d_gsync, h->rp.W, h->rp.R, h->rp.G, h->rp.JW, k, h->stream);
       if (e != cudaSuccess) return cuda_status(h, e);
       n_steps -= k;
       h->step += k;
@@ -1105,7 +1165,7 @@ int iontrap_restore(iontrap_t* h, const double* x, const double* v, const double
 }
 
 int iontrap_trace_step(iontrap_t* h, unsigned long long* marks, int64_t cap, int64_t* n_force, int64_t* n_epi) {
-  if (!h || !marks || cap < 1 || h->fused == 4) return IONTRAP_EINVAL;
+  if (!h || !marks || cap < 1 || h->fused >= 4) return IONTRAP_EINVAL;
   int st = iontrap_sync(h);
   if (st) return st;
   DeviceGuard g(h->device);
@@ -1249,17 +1309,19 @@ int iontrap_estimate_bytes(int64_t n, int precision, int64_t* bytes) {
   default_config(n, f64, sms, &T, &I, &P, &J, &F);
   iontrap_config tc{};
   GpShape gs;
+  RpShape rs;
   if (tuned_config(n, f64, dev, &tc) &&
       (step_kernel(f64, tc.threads, tc.ions_per_thread, tc.packed, tc.fused) ||
-       (tc.fused == 4 && gp_shape(n, f64, 0, sms, tc.threads, tc.ions_per_thread, tc.packed, tc.jsplit, &gs)))) {
+       (tc.fused == 4 && gp_shape(n, f64, 0, sms, tc.threads, tc.ions_per_thread, tc.packed, tc.jsplit, &gs)) ||
+       (tc.fused == 5 && rp_shape(n, f64, 0, sms, tc.threads, tc.ions_per_thread, tc.packed, tc.jsplit, &rs)))) {
     T = tc.threads, I = tc.ions_per_thread, J = tc.jsplit, F = tc.fused;
   }
-  const int64_t splits = cdiv(n, J);
-  const int64_t iblocks = F == 4 ? cdiv(n, 256) : cdiv(n, (F == 3 ? 32 : (int64_t)T) * I);
+  const int64_t splits = F == 5 ? cdiv(n, kRpInitJsplit) : cdiv(n, J);
+  const int64_t iblocks = F >= 4 ? cdiv(n, 256) : cdiv(n, (F == 3 ? 32 : (int64_t)T) * I);
   const int64_t vec = 3 * n * (int64_t)sizeof(double);
   const int64_t pair = n * (int64_t)(f64 ? sizeof(double4_32a) : 2 * sizeof(float4));
   *bytes = 3 * vec + n + 2 * pair + splits * n * 32 + iblocks * (int64_t)sizeof(unsigned) + 64 +
-           (F == 4 ? (int64_t)kGpSyncBytes : 0);
+           (F >= 4 ? (int64_t)kGpSyncBytes : 0);
   return IONTRAP_OK;
 }
 
@@ -1332,6 +1394,13 @@ int iontrap_autotune(iontrap_t* h, double trial_us, iontrap_config* best, double
         iontrap_config c{32 * W, 2, 1, (int32_t)cdiv(n, S), 4, 0, 0};
         GpShape gs;
         if (gp_shape(n, 0, h->p.flags, h->sms, c.threads, 2, 1, c.jsplit, &gs)) cands.push_back(c);
+      }
+    // row-persistent shapes: the ions spread over every SM, or 32 per CTA
+    for (int W : {8, 16})
+      for (int64_t R : {cdiv(n, h->sms), (int64_t)32}) {
+        iontrap_config c{32 * W, 1, 1, (int32_t)R, 5, 0, 0};
+        RpShape rs;
+        if (rp_shape(n, 0, h->p.flags, h->sms, c.threads, 1, 1, R, &rs)) cands.push_back(c);
       }
   }
   cudaEvent_t e0, e1;
@@ -1453,8 +1522,12 @@ int iontrap_get_config(const iontrap_t* h, iontrap_config* c) {
 int iontrap_set_config(iontrap_t* h, const iontrap_config* c) {
   if (!h || !c) return IONTRAP_EINVAL;
   GpShape gs;
+  RpShape rs;
   if (c->fused == 4) {
     if (!gp_shape(h->n, h->f64, h->p.flags, h->sms, c->threads, c->ions_per_thread, c->packed, c->jsplit, &gs))
+      return IONTRAP_EINVAL;
+  } else if (c->fused == 5) {
+    if (!rp_shape(h->n, h->f64, h->p.flags, h->sms, c->threads, c->ions_per_thread, c->packed, c->jsplit, &rs))
       return IONTRAP_EINVAL;
   } else if (!step_kernel(h->f64, c->threads, c->ions_per_thread, c->packed, c->fused)) {
     return IONTRAP_EINVAL;

@@ -370,4 +370,303 @@ int gp_max_ctas(int W, int S, int Lmax, int max_lmax, long long max_k, int sms) 
   return per * sms;
 }
 
+// ------------------------------------------------------------------ row-persistent form (fused = 5)
+// One cooperative launch advances K steps.  CTA g owns the ions [g R, min((g+1) R, n))
+// (R <= 32, one per lane) and sums their Coulomb term over every j itself: warp w takes the
+// j-range [w JW, (w+1) JW), stages it into shared memory as structure-of-arrays floats,
+// and runs the pair loop two j at a time on packed FP32x2 instructions with the lane's ion
+// in both halves (so no per-j register shuffling); the W warp partials (sum, compensation)
+// merge in warp order in shared memory, and one thread per owned ion component integrates
+// it exactly as the grid-persistent form does.  One grid-wide step counter per step; no
+// partial sum leaves the SM.  The next step's force-independent terms are evaluated right
+// after the CTA has counted itself, while the others finish.
+//
+// Summation order depends on (n, W) only: per warp, j ascending in 128-j chunks summed as
+// even and odd j (the two halves added), chunks Kahan-added; warps Kahan-merged in order.
+// Each (i, j) term is the same FP32 value as in the other forms.
+
+struct RpArgs {
+  unsigned* sync;  // [0]: step arrivals of all CTAs (zero between launches)
+  long long K;     // steps in this launch
+  int R;           // ions per CTA (<= 32)
+  int JW;          // j entries per warp (a multiple of 4; the range past n is padded)
+};
+
+// Pair terms of one lane's ion against qn (even) staged j of a warp's SoA arrays (stride
+// JW between x_hi, y_hi, z_hi, x_lo, y_lo, z_lo, z), two j per instruction.  Padding
+// entries sit at 1e30 m: r^2 overflows to infinity, rsqrt gives 0, the term is exactly 0.
+template <bool DIAG, bool UNITW>
+__device__ __forceinline__ void rp_pair2(float2 hx, float2 hy, float2 hz, float2 lx, float2 ly, float2 lz, float2 w,
+                                         long long j, long long i, const float2 (&nh)[3], const float2 (&nl)[3],
+                                         float2 (&acc)[3]) {
+  const float2 dx = __fadd2_rn(__fadd2_rn(hx, nh[0]), __fadd2_rn(lx, nl[0]));
+  const float2 dy = __fadd2_rn(__fadd2_rn(hy, nh[1]), __fadd2_rn(ly, nl[1]));
+  const float2 dz = __fadd2_rn(__fadd2_rn(hz, nh[2]), __fadd2_rn(lz, nl[2]));
+  const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+  float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+  if (DIAG) {
+    ri.x = (j == i) ? 0.0f : ri.x;
+    ri.y = (j + 1 == i) ? 0.0f : ri.y;
+  }
+  const float2 ri2 = __fmul2_rn(ri, ri);
+  const float2 s = UNITW ? __fmul2_rn(ri, ri2) : __fmul2_rn(__fmul2_rn(w, ri), ri2);
+  acc[0] = __ffma2_rn(s, dx, acc[0]);
+  acc[1] = __ffma2_rn(s, dy, acc[1]);
+  acc[2] = __ffma2_rn(s, dz, acc[2]);
+}
+
+// Four j per iteration from 16-byte shared loads (qn a multiple of 4, sj 16-byte aligned);
+// the terms and their order are those of two j at a time.
+template <bool DIAG, bool UNITW>
+__device__ __forceinline__ void rp_chunk(const float* __restrict__ sj, int JW, int qn, long long jbase, long long i,
+                                         const float2 (&nh)[3], const float2 (&nl)[3], float2 (&acc)[3]) {
+#pragma unroll 2
+  for (int q = 0; q < qn; q += 4) {
+    const float4 hx = *reinterpret_cast<const float4*>(sj + q);
+    const float4 hy = *reinterpret_cast<const float4*>(sj + JW + q);
+    const float4 hz = *reinterpret_cast<const float4*>(sj + 2 * JW + q);
+    const float4 lx = *reinterpret_cast<const float4*>(sj + 3 * JW + q);
+    const float4 ly = *reinterpret_cast<const float4*>(sj + 4 * JW + q);
+    const float4 lz = *reinterpret_cast<const float4*>(sj + 5 * JW + q);
+    float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!UNITW) w = *reinterpret_cast<const float4*>(sj + 6 * JW + q);
+    rp_pair2<DIAG, UNITW>(make_float2(hx.x, hx.y), make_float2(hy.x, hy.y), make_float2(hz.x, hz.y),
+                          make_float2(lx.x, lx.y), make_float2(ly.x, ly.y), make_float2(lz.x, lz.y),
+                          make_float2(w.x, w.y), jbase + q, i, nh, nl, acc);
+    rp_pair2<DIAG, UNITW>(make_float2(hx.z, hx.w), make_float2(hy.z, hy.w), make_float2(hz.z, hz.w),
+                          make_float2(lx.z, lx.w), make_float2(ly.z, ly.w), make_float2(lz.z, lz.w),
+                          make_float2(w.z, w.w), jbase + q + 2, i, nh, nl, acc);
+  }
+}
+
+template <int W>
+__global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant__ StepArgs A, const RpArgs P) {
+  // dynamic shared memory: per warp 7 x JW floats (SoA j data); partial sums and
+  // compensations [W][3][32] floats each; the RF phase of the K steps; the owned ions'
+  // drag velocities [3][R] (laser cooling needs all three components of an ion)
+  extern __shared__ __align__(16) float4 s_dyn[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const long long n = A.n;
+  const unsigned G = gridDim.x;
+  const int JW = P.JW;
+  const long long r0 = (long long)blockIdx.x * P.R;
+  const int Rg = (int)max(0LL, min((long long)P.R, n - r0));
+  float* sj = reinterpret_cast<float*>(s_dyn) + (size_t)warp * 7 * JW;
+  float* ps = reinterpret_cast<float*>(s_dyn) + (size_t)W * 7 * JW;
+  float* pc = ps + W * 96;
+  double* scos = reinterpret_cast<double*>(pc + W * 96);  // 28 W JW + 768 W bytes in: 8-byte aligned
+  double* svd = scos + P.K;
+  unsigned* ctr_step = P.sync;
+  const int poller = 32 * W - 1;
+  const TrapDev& tp = A.trap;
+  const long long ns0 = *A.step;
+  const bool rf = !(tp.flags & (IONTRAP_RF_OFF | IONTRAP_TRAP_OFF | IONTRAP_PSEUDO));
+  for (long long k = tid; k < P.K; k += 32 * W) scos[k] = rf ? cos(tp.Omega * ((double)(ns0 + k + 1) * tp.dt)) : 0.0;
+
+  // owned items: thread k < 3 Rg integrates component c = k / Rg of ion r0 + k % Rg
+  const int rq = max(Rg, 1);
+  const int oc = tid / rq, oq = tid - oc * rq;
+  const bool own = tid < 3 * Rg;
+  const long long ie = r0 + oq;
+  int spe = 0;
+  double xf = 0.0, vd = 0.0;
+  float z = 0.f;
+  if (own) {
+    spe = A.sp[ie];
+    const double vh = half_kick(A.v[oc * n + ie], A.a[oc * n + ie], tp.hdt);
+    vd = vh;
+    xf = drift(A.x[oc * n + ie], vh, tp.dt);
+  }
+  auto draw = [&](long long counter) {
+    if (own && A.spc[spe].sigma > 0.0) {
+      float zz[3];
+      normals3_f32(tp.seed, counter, ie, zz);
+      z = oc == 0 ? zz[0] : (oc == 1 ? zz[1] : zz[2]);
+    }
+  };
+  // trap and drag of step t (the first operations of accel_ext); the velocity goes to
+  // shared memory for the laser term
+  auto ext_det = [&](long long t) -> double {
+    const SpeciesDev& sd = A.spc[spe];
+    const double kc = trap_spring_c(tp, sd, scos[t], oc);
+    if (tp.laser) svd[oc * rq + oq] = vd;
+    return __fma_rn(-sd.gamma, vd, __dmul_rn(-kc, xf));
+  };
+  __syncthreads();  // scos
+  draw(ns0 + 1);
+  double ext = own ? ext_det(0) : 0.0;
+  float zk = z;
+  if (P.K > 1) draw(ns0 + 2);
+  __syncthreads();  // svd
+
+  for (long long t = 0; t < P.K; ++t) {
+    const long long ns = ns0 + t;
+    const int rb = (int)((ns + 1) & 1);
+    bool bad = false;
+    if (t > 0 && tid == poller) {
+      bad = !gp_wait(ctr_step, G * (unsigned)t, A.err);
+      fence_gpu();
+    }
+    if (__syncthreads_or(bad)) break;
+    if (own) {  // the rest of accel_ext: laser, then the kick
+      const SpeciesDev& sd = A.spc[spe];
+      if (tp.laser && sd.lrate != 0.0) {
+        const double v3[3] = {svd[oq], svd[rq + oq], svd[2 * rq + oq]};
+        ext = __fma_rn(-laser_proj(sd, v3), sd.kdir[oc], ext);
+      }
+      if (sd.sigma > 0.0) ext = __fma_rn(sd.sigma, (double)zk, ext);
+    }
+
+    // stage this warp's j-range (positions x_{ns+1})
+    const float4* __restrict__ ghi = A.hi[rb];
+    const float4* __restrict__ glo = A.lo[rb];
+    const long long jw0 = (long long)warp * JW;
+    for (int q = lane; q < JW; q += 32) {
+      const long long j = jw0 + q;
+      float4 h = make_float4(1e30f, 1e30f, 1e30f, 0.0f), l = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (j < n) {
+        h = __ldcg(ghi + j);
+        l = __ldcg(glo + j);
+      }
+      sj[q] = h.x, sj[JW + q] = h.y, sj[2 * JW + q] = h.z;
+      sj[3 * JW + q] = l.x, sj[4 * JW + q] = l.y, sj[5 * JW + q] = l.z;
+      sj[6 * JW + q] = h.w;
+    }
+    const long long ii = r0 + lane;
+    float4 hi4 = make_float4(0.f, 0.f, 0.f, 0.f), lo4 = hi4;
+    if (lane < Rg) {
+      hi4 = __ldcg(ghi + ii);
+      lo4 = __ldcg(glo + ii);
+    }
+    const float2 nh[3] = {make_float2(-hi4.x, -hi4.x), make_float2(-hi4.y, -hi4.y), make_float2(-hi4.z, -hi4.z)};
+    const float2 nl[3] = {make_float2(-lo4.x, -lo4.x), make_float2(-lo4.y, -lo4.y), make_float2(-lo4.z, -lo4.z)};
+    __syncwarp();
+
+    float ks[3] = {0.f, 0.f, 0.f}, kcp[3] = {0.f, 0.f, 0.f};
+    for (int c0 = 0; c0 < JW; c0 += kSeg) {
+      const int qn = min(kSeg, JW - c0);
+      const long long jc = jw0 + c0;
+      const bool diag = (jc < r0 + Rg) && (r0 < jc + qn);
+      float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+      if (A.unitw) {
+        if (diag)
+          rp_chunk<true, true>(sj + c0, JW, qn, jc, ii, nh, nl, acc);
+        else
+          rp_chunk<false, true>(sj + c0, JW, qn, jc, ii, nh, nl, acc);
+      } else {
+        if (diag)
+          rp_chunk<true, false>(sj + c0, JW, qn, jc, ii, nh, nl, acc);
+        else
+          rp_chunk<false, false>(sj + c0, JW, qn, jc, ii, nh, nl, acc);
+      }
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const float a = acc[d].x + acc[d].y;
+        const float y = a - kcp[d];
+        const float tt = ks[d] + y;
+        kcp[d] = (tt - ks[d]) - y;
+        ks[d] = tt;
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      ps[(warp * 3 + d) * 32 + lane] = ks[d];
+      pc[(warp * 3 + d) * 32 + lane] = kcp[d];
+    }
+    __syncthreads();
+
+    if (own) {  // merge in warp order (Kahan), then finish the step
+      float su = 0.f, cu = 0.f;
+#pragma unroll 8
+      for (int w = 0; w < W; ++w) kahan_merge(su, cu, ps[(w * 3 + oc) * 32 + oq], pc[(w * 3 + oc) * 32 + oq]);
+      const double Sd = (double)cu - (double)su;
+      const SpeciesDev& sd = A.spc[spe];
+      const double acc = __fma_rn(sd.coul, Sd, ext);
+      const double vn = half_kick(vd, acc, tp.hdt);
+      const double vh = half_kick(vn, acc, tp.hdt);
+      const double xn = drift(xf, vh, tp.dt);
+      A.x[oc * n + ie] = xf;
+      A.v[oc * n + ie] = vn;
+      A.a[oc * n + ie] = acc;
+      const float h = __double2float_rn(xn);
+      const float l = __double2float_rn(xn - (double)h);
+      reinterpret_cast<float*>(A.hi[rb ^ 1] + ie)[oc] = h;
+      reinterpret_cast<float*>(A.lo[rb ^ 1] + ie)[oc] = l;
+      if (oc == 0) {
+        reinterpret_cast<float*>(A.hi[rb ^ 1] + ie)[3] = sd.w;
+        reinterpret_cast<float*>(A.lo[rb ^ 1] + ie)[3] = 0.0f;
+      }
+      if (!(isfinite(acc) && isfinite(vn) && isfinite(xn))) atomicOr(A.err, ERR_NONFINITE);
+      vd = vh;
+      xf = xn;
+    }
+    __syncthreads();
+    if (tid == poller) {
+      fence_gpu();
+      atomicAdd(ctr_step, 1u);
+    }
+    // the next step's trap and drag and the noise after it, while the other CTAs finish
+    if (t + 1 < P.K) {
+      if (own) ext = ext_det(t + 1);
+      zk = z;
+      if (t + 2 < P.K) draw(ns + 3);
+    }
+  }
+
+  // once every CTA has counted its last step: clear the counter, advance the step index
+  if (blockIdx.x == 0 && tid == poller) {
+    gp_wait(ctr_step, G * (unsigned)P.K, A.err);
+    *ctr_step = 0u;
+    *A.step = ns0 + P.K;
+    __threadfence();
+  }
+}
+
+size_t rp_smem_bytes(int W, int JW, long long K) {
+  return (size_t)W * 7 * JW * sizeof(float) + 2 * (size_t)W * 96 * sizeof(float) + (size_t)K * sizeof(double) +
+         3 * 32 * sizeof(double);
+}
+
+const void* rp_kernel(int W) {
+  switch (W) {
+    case 8: return (const void*)k_step_f32_rp<8>;
+    case 16: return (const void*)k_step_f32_rp<16>;
+    default: return nullptr;
+  }
+}
+
+// Co-resident CTAs of the W-warp row-persistent kernel with JW j per warp and up to max_k
+// steps per launch (the dynamic shared-memory limit is raised to the largest launch any
+// handle may make: JW of max_jw).
+int rp_max_ctas(int W, int JW, int max_jw, long long max_k, int sms) {
+  const void* fn = rp_kernel(W);
+  if (!fn || JW > max_jw || JW < 2) return 0;
+  const size_t limit = rp_smem_bytes(W, max_jw, max_k);
+  if (limit > 227 * 1024) return 0;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit) != cudaSuccess) return 0;
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, 32 * W, rp_smem_bytes(W, JW, max_k)) != cudaSuccess)
+    return 0;
+  return per * sms;
+}
+
+cudaError_t launch_rp(const StepArgs& a, unsigned* sync, int W, int R, int G, int JW, long long K, cudaStream_t st) {
+  const void* fn = rp_kernel(W);
+  if (!fn) return cudaErrorInvalidValue;
+  RpArgs P{sync, K, R, JW};
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)G);
+  cfg.blockDim = dim3((unsigned)(32 * W));
+  cfg.dynamicSmemBytes = rp_smem_bytes(W, JW, K);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  StepArgs ac = a;
+  void* params[] = {&ac, &P};
+  return cudaLaunchKernelExC(&cfg, fn, params);
+}
+
 }  // namespace it

@@ -78,12 +78,12 @@ FREQS = [(2 * math.pi * 0.32e6, 2 * math.pi * 0.35e6, 2 * math.pi * 0.2e6),
          (2 * math.pi * 0.28e6, 2 * math.pi * 0.3e6, 2 * math.pi * 0.19e6)]
 
 
-@pytest.mark.parametrize("form", ["last_cta", "persistent", "batched", "fp64"])
+@pytest.mark.parametrize("form", ["last_cta", "persistent", "row_persistent", "batched", "fp64"])
 @pytest.mark.parametrize("given", [False, True], ids=["eq2", "frequencies"])
 def test_pseudo_trap_trajectory_matches_oracle(it, form, given):
     """Mixed species in the pseudopotential trap of Eq. 2, or in per-species frequencies,
     with the bath on: 80 steps against the oracle."""
-    n = 3000 if form in ("last_cta", "persistent", "fp64") else 700
+    n = 3000 if form in ("last_cta", "persistent", "row_persistent", "fp64") else 700
     species, sp, x0, v0 = _cloud(n, 12)
     tr = _trap()
     flags = it.IONTRAP_PSEUDO
@@ -99,6 +99,8 @@ def test_pseudo_trap_trajectory_matches_oracle(it, form, given):
             s.set_config(128, 2, 1, -(-n // 12), 1)
         elif form == "persistent":
             s.set_config(256, 2, 1, -(-n // 25), 4)
+        elif form == "row_persistent":
+            s.set_config(512, 1, 1, 20, 5)
         if form == "batched":
             it.iontrap_step_many([s.handle], [80])
         else:
