@@ -326,7 +326,7 @@ typedef struct {
                                     CTAs resident at once); each CTA sums its R ions over
                                     every j, its warps splitting the j-range, merges the warp
                                     partials in shared memory and integrates; one grid-wide
-                                    counter per step; creation and iontrap_forces use form 1
+                                    counter per step; the evaluation at creation uses form 1
                                     over 512-ion j-ranges; not with IONTRAP_COULOMB_OFF.
                                  The FP64 form supports 1 only. */
     int32_t pdl;              /* 1: consecutive step kernels use programmatic dependent launch

@@ -535,7 +535,7 @@ int alloc_scratch(iontrap* h) {
 // Launch one step kernel with programmatic dependent launch, so that consecutive steps
 // overlap one grid's launch with the previous grid's tail.
 cudaError_t launch_step_on(iontrap* h, StepArgs& a, cudaStream_t st) {
-  if (h->fused == 5 && a.mode == MODE_STEP)
+  if (h->fused == 5 && a.mode != MODE_INIT)
     return launch_rp(a, h->d_gsync, h->rp.W, h->rp.R, h->rp.G, h->rp.JW, 1, st);
   if (h->fused == 4 || h->fused == 5) {
     if (h->fused == 4 && a.mode != MODE_INIT)

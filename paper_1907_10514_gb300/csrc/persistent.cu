@@ -460,6 +460,7 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
   const int poller = 32 * W - 1;
   const TrapDev& tp = A.trap;
   const long long ns0 = *A.step;
+  const bool forces = A.mode == MODE_FORCES;  // one force evaluation of the current positions (K = 1)
   const bool rf = !(tp.flags & (IONTRAP_RF_OFF | IONTRAP_TRAP_OFF | IONTRAP_PSEUDO));
   for (long long k = tid; k < P.K; k += 32 * W) scos[k] = rf ? cos(tp.Omega * ((double)(ns0 + k + 1) * tp.dt)) : 0.0;
 
@@ -471,14 +472,14 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
   int spe = 0;
   double xf = 0.0, vd = 0.0;
   float z = 0.f;
-  if (own) {
-    spe = A.sp[ie];
+  if (own) spe = A.sp[ie];
+  if (own && !forces) {
     const double vh = half_kick(A.v[oc * n + ie], A.a[oc * n + ie], tp.hdt);
     vd = vh;
     xf = drift(A.x[oc * n + ie], vh, tp.dt);
   }
   auto draw = [&](long long counter) {
-    if (own && A.spc[spe].sigma > 0.0) {
+    if (own && !forces && A.spc[spe].sigma > 0.0) {
       float zz[3];
       normals3_f32(tp.seed, counter, ie, zz);
       z = oc == 0 ? zz[0] : (oc == 1 ? zz[1] : zz[2]);
@@ -494,21 +495,21 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
   };
   __syncthreads();  // scos
   draw(ns0 + 1);
-  double ext = own ? ext_det(0) : 0.0;
+  double ext = own && !forces ? ext_det(0) : 0.0;
   float zk = z;
   if (P.K > 1) draw(ns0 + 2);
   __syncthreads();  // svd
 
   for (long long t = 0; t < P.K; ++t) {
     const long long ns = ns0 + t;
-    const int rb = (int)((ns + 1) & 1);
+    const int rb = forces ? (int)(ns & 1) : (int)((ns + 1) & 1);
     bool bad = false;
     if (t > 0 && tid == poller) {
       bad = !gp_wait(ctr_step, G * (unsigned)t, A.err);
       fence_gpu();
     }
     if (__syncthreads_or(bad)) break;
-    if (own) {  // the rest of accel_ext: laser, then the kick
+    if (own && !forces) {  // the rest of accel_ext: laser, then the kick
       const SpeciesDev& sd = A.spc[spe];
       if (tp.laser && sd.lrate != 0.0) {
         const double v3[3] = {svd[oq], svd[rq + oq], svd[2 * rq + oq]};
@@ -581,24 +582,28 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
       for (int w = 0; w < W; ++w) kahan_merge(su, cu, ps[(w * 3 + oc) * 32 + oq], pc[(w * 3 + oc) * 32 + oq]);
       const double Sd = (double)cu - (double)su;
       const SpeciesDev& sd = A.spc[spe];
-      const double acc = __fma_rn(sd.coul, Sd, ext);
-      const double vn = half_kick(vd, acc, tp.hdt);
-      const double vh = half_kick(vn, acc, tp.hdt);
-      const double xn = drift(xf, vh, tp.dt);
-      A.x[oc * n + ie] = xf;
-      A.v[oc * n + ie] = vn;
-      A.a[oc * n + ie] = acc;
-      const float h = __double2float_rn(xn);
-      const float l = __double2float_rn(xn - (double)h);
-      reinterpret_cast<float*>(A.hi[rb ^ 1] + ie)[oc] = h;
-      reinterpret_cast<float*>(A.lo[rb ^ 1] + ie)[oc] = l;
-      if (oc == 0) {
-        reinterpret_cast<float*>(A.hi[rb ^ 1] + ie)[3] = sd.w;
-        reinterpret_cast<float*>(A.lo[rb ^ 1] + ie)[3] = 0.0f;
+      if (forces) {
+        A.out[oc * n + ie] = sd.coul * Sd;
+      } else {
+        const double acc = __fma_rn(sd.coul, Sd, ext);
+        const double vn = half_kick(vd, acc, tp.hdt);
+        const double vh = half_kick(vn, acc, tp.hdt);
+        const double xn = drift(xf, vh, tp.dt);
+        A.x[oc * n + ie] = xf;
+        A.v[oc * n + ie] = vn;
+        A.a[oc * n + ie] = acc;
+        const float h = __double2float_rn(xn);
+        const float l = __double2float_rn(xn - (double)h);
+        reinterpret_cast<float*>(A.hi[rb ^ 1] + ie)[oc] = h;
+        reinterpret_cast<float*>(A.lo[rb ^ 1] + ie)[oc] = l;
+        if (oc == 0) {
+          reinterpret_cast<float*>(A.hi[rb ^ 1] + ie)[3] = sd.w;
+          reinterpret_cast<float*>(A.lo[rb ^ 1] + ie)[3] = 0.0f;
+        }
+        if (!(isfinite(acc) && isfinite(vn) && isfinite(xn))) atomicOr(A.err, ERR_NONFINITE);
+        vd = vh;
+        xf = xn;
       }
-      if (!(isfinite(acc) && isfinite(vn) && isfinite(xn))) atomicOr(A.err, ERR_NONFINITE);
-      vd = vh;
-      xf = xn;
     }
     __syncthreads();
     if (tid == poller) {
@@ -606,7 +611,7 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
       atomicAdd(ctr_step, 1u);
     }
     // the next step's trap and drag and the noise after it, while the other CTAs finish
-    if (t + 1 < P.K) {
+    if (t + 1 < P.K && !forces) {
       if (own) ext = ext_det(t + 1);
       zk = z;
       if (t + 2 < P.K) draw(ns + 3);
@@ -617,7 +622,7 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
   if (blockIdx.x == 0 && tid == poller) {
     gp_wait(ctr_step, G * (unsigned)P.K, A.err);
     *ctr_step = 0u;
-    *A.step = ns0 + P.K;
+    if (!forces) *A.step = ns0 + P.K;
     __threadfence();
   }
 }

@@ -87,7 +87,7 @@ def test_forces_match_oracle(it, n):
                                  (256, 4, 0, 100, 1), (128, 4, 1, 1152, 0), (128, 1, 0, 7, 1), (64, 2, 0, 1000, 0),
                                  (32, 1, 0, 376, 2), (64, 1, 0, 501, 2), (128, 4, 1, 1001, 2), (32, 2, 1, 3001, 2),
                                  (64, 1, 0, 501, 3), (128, 2, 1, 1001, 3), (128, 1, 0, 376, 3), (64, 2, 1, 3001, 3),
-                                 (64, 2, 1, 200, 3), (64, 1, 0, 188, 3)])
+                                 (64, 2, 1, 200, 3), (64, 1, 0, 188, 3), (512, 1, 1, 32, 5), (256, 1, 1, 20, 5)])
 @pytest.mark.parametrize("unit", [False, True], ids=["z_mixed", "z_unit"])
 def test_forces_every_tile_config(it, cfg, unit):
     n = 3001
