@@ -420,7 +420,10 @@ int iontrap_forces_noalloc(const iontrap_species *species, int n_species, const 
                            const double *d_x, int64_t n, double *d_acc, void *cuda_stream);
 
 /* Profiling hook: run ONE step with per-CTA phase timestamps (%globaltimer, ns) and copy
- * them to marks[cap] (EINVAL in the persistent forms 4 and 5).  Layout: 4 marks per force-kernel CTA, CTA id = y*grid.x + x
+ * them to marks[cap] (EINVAL in the grid-persistent form 4; in the row-persistent form 5
+ * one launch of 8 steps, 4 marks per CTA and step at mark (CTA 8 + step) 4 + m: grid
+ * barrier passed, warp 0's j-range staged, every warp's pair loop done, integration done;
+ * *n_force = 32 x CTAs, *n_epi = 0).  Layout: 4 marks per force-kernel CTA, CTA id = y*grid.x + x
  * (start after the grid dependency wait, end of the pair loop, start of the fused
  * epilogue or 0, end of the fused epilogue or 0), then 2 per epilogue-kernel CTA (start,
  * end) when the configuration is not fused.  *n_force and *n_epi receive the counts.

@@ -1165,10 +1165,31 @@ int iontrap_restore(iontrap_t* h, const double* x, const double* v, const double
 }
 
 int iontrap_trace_step(iontrap_t* h, unsigned long long* marks, int64_t cap, int64_t* n_force, int64_t* n_epi) {
-  if (!h || !marks || cap < 1 || h->fused >= 4) return IONTRAP_EINVAL;
+  if (!h || !marks || cap < 1 || h->fused == 4) return IONTRAP_EINVAL;
   int st = iontrap_sync(h);
   if (st) return st;
   DeviceGuard g(h->device);
+  if (h->fused == 5) {  // one launch of kRpTraceSteps steps, 4 marks per CTA and step
+    constexpr int64_t kRpTraceSteps = 8;
+    const int64_t nf = 4 * (int64_t)h->rp.G * kRpTraceSteps;
+    if (nf > cap) return IONTRAP_EINVAL;
+    unsigned long long* d = nullptr;
+    if (cudaMalloc(&d, nf * sizeof(unsigned long long)) != cudaSuccess) return IONTRAP_ENOMEM;
+    cudaError_t e = cudaMemsetAsync(d, 0, nf * sizeof(unsigned long long), h->stream);
+    StepArgs a = h->args;
+    a.mode = MODE_STEP;
+    a.out = nullptr;
+    a.trace = d;
+    if (e == cudaSuccess) e = launch_rp(a, h->d_gsync, h->rp.W, h->rp.R, h->rp.G, h->rp.JW, kRpTraceSteps, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(marks, d, nf * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_status(h, e);
+    h->step += kRpTraceSteps;
+    if (n_force) *n_force = nf;
+    if (n_epi) *n_epi = 0;
+    return iontrap_sync(h);
+  }
   const dim3 grid = grid_of(h);
   const int64_t nf = 4 * (int64_t)grid.x * grid.y;
   const int64_t ne = h->fused ? 0 : 2 * cdiv(h->n, 32);

@@ -509,6 +509,9 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
       fence_gpu();
     }
     if (__syncthreads_or(bad)) break;
+    // optional phase timestamps (iontrap_trace_step): 4 per CTA and step
+    const long long tslot = ((long long)blockIdx.x * P.K + t) * 4;
+    trace_mark(A.trace, tslot + 0);
     if (own && !forces) {  // the rest of accel_ext: laser, then the kick
       const SpeciesDev& sd = A.spc[spe];
       if (tp.laser && sd.lrate != 0.0) {
@@ -542,6 +545,7 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
     const float2 nh[3] = {make_float2(-hi4.x, -hi4.x), make_float2(-hi4.y, -hi4.y), make_float2(-hi4.z, -hi4.z)};
     const float2 nl[3] = {make_float2(-lo4.x, -lo4.x), make_float2(-lo4.y, -lo4.y), make_float2(-lo4.z, -lo4.z)};
     __syncwarp();
+    trace_mark(A.trace, tslot + 1);
 
     float ks[3] = {0.f, 0.f, 0.f}, kcp[3] = {0.f, 0.f, 0.f};
     for (int c0 = 0; c0 < JW; c0 += kSeg) {
@@ -575,6 +579,7 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
       pc[(warp * 3 + d) * 32 + lane] = kcp[d];
     }
     __syncthreads();
+    trace_mark(A.trace, tslot + 2);
 
     if (own) {  // merge in warp order (Kahan), then finish the step
       float su = 0.f, cu = 0.f;
@@ -600,12 +605,14 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
           reinterpret_cast<float*>(A.hi[rb ^ 1] + ie)[3] = sd.w;
           reinterpret_cast<float*>(A.lo[rb ^ 1] + ie)[3] = 0.0f;
         }
-        if (!(isfinite(acc) && isfinite(vn) && isfinite(xn))) atomicOr(A.err, ERR_NONFINITE);
+        // a non-finite acceleration or velocity reaches xn = xf + dt (vn + dt/2 acc)
+        if (!isfinite(xn)) atomicOr(A.err, ERR_NONFINITE);
         vd = vh;
         xf = xn;
       }
     }
     __syncthreads();
+    trace_mark(A.trace, tslot + 3);
     if (tid == poller) {
       fence_gpu();
       atomicAdd(ctr_step, 1u);
