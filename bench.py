@@ -52,8 +52,8 @@ NOMINAL_SM_MHZ = 2070.0
 PROFILED_TRAFFIC = {
     # one launch per timestep (profiles/step_f32_cw_mix_n4096.md)
     (128, 2, 1, 512, 3): (485376 + 0, "DRAM bytes per timestep launch (ncu, profiles/step_f32_cw_mix_n4096.md)"),
-    # row-persistent form: a 20-timestep launch read 489 472 B and wrote 2 816 B
-    (512, 1, 1, 32, 5): ((489472 + 2816) / 20, "DRAM bytes per timestep, from a 20-timestep launch of the "
+    # row-persistent form: a 20-timestep launch read 490 240 B and wrote 1 024 B
+    (512, 1, 1, 32, 5): ((490240 + 1024) / 20, "DRAM bytes per timestep, from a 20-timestep launch of the "
                                                "row-persistent kernel (ncu, profiles/step_f32_rp_mix_n4096.md)"),
     # grid-persistent form: a 20-timestep launch read 496 896 B and wrote 113 152 B
     (512, 2, 1, 108, 4): ((496896 + 113152) / 20, "DRAM bytes per timestep, from a 20-timestep launch of the "
@@ -377,6 +377,23 @@ def extra_measurements(it, torch, stream, sms, args):
         out["mix_n4096_species_cooling"] = {"ion_steps_per_s": n * k / (ms / 1e3), "us_per_timestep": 1e3 * ms / k,
                                             "timesteps": k, "tile": list(s.config()),
                                             "cooling": "Ca+: bath 1e5/s 1 mK + laser (1e5, 0, 0)/s; NH3+: bath 2e5/s 2 mK"}
+    # the same workload recording x and the secular velocity (average over one RF period)
+    # every RF period into a device buffer (dump + timeAvg, Sec. 3 "Writing/reading data")
+    with it.Simulation(w.species, w.species_of_ion, w.x0, w.v0, pc, stream=stream) as s:
+        k = 1000
+        fields = it.IONTRAP_REC_X | it.IONTRAP_REC_VAVG
+        buf = torch.empty((k // 20) * 2 * 3 * n, dtype=torch.float64, device="cuda")
+        s.step(100)
+        s.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step_record(k, 20, fields, 20, buf.data_ptr())
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        out["mix_n4096_record_every_rf_period"] = {"ion_steps_per_s": n * k / (ms / 1e3), "us_per_timestep": 1e3 * ms / k,
+                                                   "timesteps": k, "records": k // 20,
+                                                   "fields": "x and the velocity averaged over 20 steps"}
     out.update(modes_measurements(it, stream))
     wc = iongen.crystal_n32768()
     nc = wc.n
