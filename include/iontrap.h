@@ -322,12 +322,14 @@ typedef struct {
                                     CUDA graph, pdl ignored; not with IONTRAP_COULOMB_OFF.
                                  5: row-persistent: one cooperative launch runs up to 1000
                                     steps (threads = 256 or 512, ions_per_thread = 1,
-                                    packed = 1, jsplit = R <= 32 ions per CTA, ceil(n / R)
-                                    CTAs resident at once); each CTA sums its R ions over
-                                    every j, its warps splitting the j-range, merges the warp
-                                    partials in shared memory and integrates; one grid-wide
-                                    counter per step; the evaluation at creation uses form 1
-                                    over 512-ion j-ranges; not with IONTRAP_COULOMB_OFF.
+                                    packed = 1, jsplit = R ions per CTA with 3 R <= threads,
+                                    ceil(n / R) CTAs resident at once, all n positions staged
+                                    in shared memory: n up to about 7000); each CTA sums its R
+                                    ions over every j, thread t taking ion t % R against j-part
+                                    t / R, merges the part partials in shared memory and
+                                    integrates; one grid-wide counter per step; the evaluation
+                                    at creation uses form 1 over 512-ion j-ranges; not with
+                                    IONTRAP_COULOMB_OFF.
                                  The FP64 form supports 1 only. */
     int32_t pdl;              /* 1: consecutive step kernels use programmatic dependent launch
                                  (default 0: measured slower on GB300 for these grids) */

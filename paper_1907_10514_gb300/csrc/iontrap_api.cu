@@ -45,9 +45,10 @@ cudaError_t launch_record(long long n, const double* x, const double* v, const d
 cudaError_t launch_gp(const StepArgs& a, unsigned* sync, int W, int S, int G, int Lmax, long long K,
                       cudaStream_t st);
 int gp_max_ctas(int W, int S, int Lmax, int max_lmax, long long max_k, int sms);
-cudaError_t launch_rp(const StepArgs& a, unsigned* sync, int W, int R, int G, int JW, long long K, cudaStream_t st);
-int rp_max_ctas(int W, int JW, int max_jw, long long max_k, int sms);
-size_t rp_smem_bytes(int W, int JW, long long K);
+cudaError_t launch_rp(const StepArgs& a, unsigned* sync, int W, int R, int NP, int JP, int G, long long K,
+                      cudaStream_t st);
+int rp_max_ctas(int W, int R, int NP, int JP, long long max_k, int sms);
+size_t rp_smem_bytes(int W, int R, int NP, int JP, long long K);
 }  // namespace it
 
 using namespace it;
@@ -69,9 +70,9 @@ struct GpShape {
   int W = 0, S = 0, G = 0, Lmax = 0;
 };
 
-// row-persistent form (fused = 5): W warps, R ions per CTA, G CTAs, JW j per warp
+// row-persistent form (fused = 5): W warps, R ions per CTA, G CTAs, NP j-parts of JP entries
 struct RpShape {
-  int W = 0, R = 0, G = 0, JW = 0;
+  int W = 0, R = 0, G = 0, NP = 0, JP = 0;
 };
 static constexpr int64_t kRpInitJsplit = 512;  // j-range per CTA of its creation-time / force evaluation
 
@@ -318,23 +319,23 @@ bool tuned_config(int64_t n, int f64, int dev, iontrap_config* c) {
 // blocks keep the FP64 epilogue of the last CTA short, large ones reuse each staged j
 // over more ions.  The number of j-splits S makes the grid a multiple of the SM count
 // (equal work per SM) with at least two CTAs per SM where n allows.
-// The largest j-range per warp (a multiple of 4) whose launch fits in 227 KB of shared memory.
-int rp_max_jw(int W) {
-  const size_t fixed = rp_smem_bytes(W, 0, kGpMaxSteps);
-  return (int)(((227 * 1024 - fixed) / (28 * (size_t)W)) & ~(size_t)3);
-}
-
+// Row-persistent shape: R ions per CTA (3 R threads integrate, so R <= 32 W / 3), NP =
+// 32 W / R j-parts per CTA, JP entries per part: a multiple of 4 (16-byte shared loads of
+// four j, 16-byte aligned arrays), with JP / 4 odd when a warp spans several parts (R not
+// a multiple of 32), so that their loads start in distinct banks; the launch must fit in
+// shared memory and on the GPU at once.
 bool rp_shape(int64_t n, int f64, unsigned flags, int sms, int T, int I, int packed, int64_t R, RpShape* out) {
-  if (f64 || (flags & IONTRAP_COULOMB_OFF) || (T != 256 && T != 512) || I != 1 || packed != 1 || R < 1 || R > 32 ||
-      R > n)
+  if (f64 || (flags & IONTRAP_COULOMB_OFF) || (T != 256 && T != 512) || I != 1 || packed != 1 || R < 1 || R > n)
     return false;
   const int W = T / 32;
-  // a multiple of 4 j per warp: the pair loop reads four j per 16-byte shared load, and
-  // every warp's 7 arrays of JW floats then start on 16-byte boundaries
-  const int64_t JW = (cdiv(n, W) + 3) / 4 * 4, G = cdiv(n, R);
-  if (JW < 2 || JW > rp_max_jw(W)) return false;
-  if (G > rp_max_ctas(W, (int)JW, rp_max_jw(W), kGpMaxSteps, sms)) return false;
-  out->W = W, out->R = (int)R, out->G = (int)G, out->JW = (int)JW;
+  if (3 * R > 32 * W) return false;
+  const int64_t NP = (32 * W) / R;
+  int64_t q4 = cdiv(cdiv(n, NP), 4);
+  if (R % 32 != 0 && !(q4 & 1)) ++q4;
+  const int64_t JP = 4 * q4, G = cdiv(n, R);
+  if (rp_smem_bytes(W, (int)R, (int)NP, (int)JP, kGpMaxSteps) > 227 * 1024) return false;
+  if (G > rp_max_ctas(W, (int)R, (int)NP, (int)JP, kGpMaxSteps, sms)) return false;
+  out->W = W, out->R = (int)R, out->G = (int)G, out->NP = (int)NP, out->JP = (int)JP;
   return true;
 }
 
@@ -392,12 +393,13 @@ void default_config(int64_t n, int f64, int sms, int* T, int* I, int* packed, in
       *jsplit = (int)cdiv(n, S);
     }
   }
-  // n <= 32 x SMs: the row-persistent form (32 ions per CTA) measured fastest of all
-  // (us/step on GB300 against the choice above: n = 256: 3.7 vs 10.8; 1024: 6.2 vs 13.4;
-  // 2048: 9.1 vs 9.7; 4096: 15.0 vs 17.3; 4864: 17.7 vs 22.7)
-  if (!f64 && allow_persistent && n <= 32 * (int64_t)sms) {
-    const int W = n < 512 ? 8 : 16;
-    const int64_t R = std::min<int64_t>(32, n);
+  // Wherever its staged j fit in shared memory (n up to about 7000): the row-persistent
+  // form with the ions spread over every SM measured fastest of all (us/step on GB300
+  // against the choices above: n = 1024: 5.3 vs 13.4; 2048: 6.7 vs 9.7; 3000: 9.7 vs 13.0;
+  // 4096: 14.6 vs 17.3; 6000: 25.9 vs 30.6)
+  if (!f64 && allow_persistent) {
+    const int W = n < 2048 ? 8 : 16;
+    const int64_t R = cdiv(n, sms);
     RpShape rs;
     if (rp_shape(n, 0, 0, sms, 32 * W, 1, 1, R, &rs)) {
       *T = 32 * W, *I = 1, *packed = 1, *fused = 5;
@@ -536,7 +538,7 @@ int alloc_scratch(iontrap* h) {
 // overlap one grid's launch with the previous grid's tail.
 cudaError_t launch_step_on(iontrap* h, StepArgs& a, cudaStream_t st) {
   if (h->fused == 5 && a.mode != MODE_INIT)
-    return launch_rp(a, h->d_gsync, h->rp.W, h->rp.R, h->rp.G, h->rp.JW, 1, st);
+    return launch_rp(a, h->d_gsync, h->rp.W, h->rp.R, h->rp.NP, h->rp.JP, h->rp.G, 1, st);
   if (h->fused == 4 || h->fused == 5) {
     if (h->fused == 4 && a.mode != MODE_INIT)
       return launch_gp(a, h->d_gsync, h->gp.W, h->gp.S, h->gp.G, h->gp.Lmax, 1, st);
@@ -875,7 +877,8 @@ int iontrap_step(iontrap_t* h, int64_t n_steps) {
     while (n_steps > 0) {
       const int64_t k = std::min<int64_t>(n_steps, kGpMaxSteps);
       cudaError_t e = h->fused == 4 ? launch_gp(a, h->d_gsync, h->gp.W, h->gp.S, h->gp.G, h->gp.Lmax, k, h->stream)
-                                    : launch_rp(a, h->d_gsync, h->rp.W, h->rp.R, h->rp.G, h->rp.JW, k, h->stream);
+                                    : launch_rp(a, h->d_gsync, h->rp.W, h->rp.R, h->rp.NP, h->rp.JP, h->rp.G, k,
+                                                h->stream);
       if (e != cudaSuccess) return cuda_status(h, e);
       n_steps -= k;
       h->step += k;
@@ -1180,7 +1183,8 @@ int iontrap_trace_step(iontrap_t* h, unsigned long long* marks, int64_t cap, int
     a.mode = MODE_STEP;
     a.out = nullptr;
     a.trace = d;
-    if (e == cudaSuccess) e = launch_rp(a, h->d_gsync, h->rp.W, h->rp.R, h->rp.G, h->rp.JW, kRpTraceSteps, h->stream);
+    if (e == cudaSuccess)
+      e = launch_rp(a, h->d_gsync, h->rp.W, h->rp.R, h->rp.NP, h->rp.JP, h->rp.G, kRpTraceSteps, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(marks, d, nf * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cudaFree(d);
@@ -1416,9 +1420,13 @@ int iontrap_autotune(iontrap_t* h, double trial_us, iontrap_config* best, double
         GpShape gs;
         if (gp_shape(n, 0, h->p.flags, h->sms, c.threads, 2, 1, c.jsplit, &gs)) cands.push_back(c);
       }
-    // row-persistent shapes: the ions spread over every SM, or 32 per CTA
+    // row-persistent shapes: the ions spread over every SM, that count rounded up to a
+    // power of two (parts aligned with warps), or 32 per CTA
+    int64_t r2 = 1;
+    while (r2 < cdiv(n, h->sms)) r2 *= 2;
     for (int W : {8, 16})
-      for (int64_t R : {cdiv(n, h->sms), (int64_t)32}) {
+      for (int64_t R : {cdiv(n, h->sms), r2, (int64_t)32}) {
+        if (R == r2 && r2 == cdiv(n, h->sms)) continue;
         iontrap_config c{32 * W, 1, 1, (int32_t)R, 5, 0, 0};
         RpShape rs;
         if (rp_shape(n, 0, h->p.flags, h->sms, c.threads, 1, 1, R, &rs)) cands.push_back(c);

@@ -371,33 +371,36 @@ int gp_max_ctas(int W, int S, int Lmax, int max_lmax, long long max_k, int sms) 
 }
 
 // ------------------------------------------------------------------ row-persistent form (fused = 5)
-// One cooperative launch advances K steps.  CTA g owns the ions [g R, min((g+1) R, n))
-// (R <= 32, one per lane) and sums their Coulomb term over every j itself: warp w takes the
-// j-range [w JW, (w+1) JW), stages it into shared memory as structure-of-arrays floats,
-// and runs the pair loop two j at a time on packed FP32x2 instructions with the lane's ion
-// in both halves (so no per-j register shuffling); the W warp partials (sum, compensation)
-// merge in warp order in shared memory, and one thread per owned ion component integrates
-// it exactly as the grid-persistent form does.  One grid-wide step counter per step; no
-// partial sum leaves the SM.  The next step's force-independent terms are evaluated right
-// after the CTA has counted itself, while the others finish.
+// One cooperative launch advances K steps.  CTA g owns the ions [g R, min((g+1) R, n)) and
+// sums their Coulomb term over every j itself.  Its threads are laid out part-major:
+// thread t < R NP takes ion t % R against j-part t / R, the part p covering
+// j in [p JP, (p+1) JP) (NP = 32 W / R parts, so nearly every thread works whatever R);
+// the j data of all parts is staged into shared memory as structure-of-arrays floats and
+// the pair loop runs two j at a time on packed FP32x2 instructions with the thread's ion in
+// both halves (four j per 16-byte shared load).  The NP part partials (sum, compensation)
+// of an ion merge in part order in shared memory, and one thread per owned ion component
+// integrates it exactly as the grid-persistent form does.  One grid-wide step counter per
+// step; no partial sum leaves the SM.  The next step's force-independent terms are
+// evaluated right after the CTA has counted itself, while the others finish.
 //
-// Summation order depends on (n, W) only: per warp, j ascending in 128-j chunks summed as
-// even and odd j (the two halves added), chunks Kahan-added; warps Kahan-merged in order.
-// Each (i, j) term is the same FP32 value as in the other forms.
+// Summation order depends on (n, R, W) only: per part, j ascending in 128-j chunks summed
+// as even and odd j (the two halves added), chunks Kahan-added; parts Kahan-merged in
+// order.  Each (i, j) term is the same FP32 value as in the other forms.
 
 struct RpArgs {
   unsigned* sync;  // [0]: step arrivals of all CTAs (zero between launches)
   long long K;     // steps in this launch
-  int R;           // ions per CTA (<= 32)
-  int JW;          // j entries per warp (a multiple of 4; the range past n is padded)
+  int R;           // ions per CTA
+  int NP;          // j-parts per CTA: 32 W / R
+  int JP;          // j entries per part: a multiple of 4 with JP / 4 odd (the parts of one
+                   // warp read from distinct shared-memory banks); entries past n are padding
 };
 
-// Pair terms of one lane's ion against qn (even) staged j of a warp's SoA arrays (stride
-// JW between x_hi, y_hi, z_hi, x_lo, y_lo, z_lo, z), two j per instruction.  Padding
-// entries sit at 1e30 m: r^2 overflows to infinity, rsqrt gives 0, the term is exactly 0.
+// Pair terms of one thread's ion against two j (packed); DIAG: the self pair is excluded
+// by its index (only chunks that may hold it take this variant).
 template <bool DIAG, bool UNITW>
 __device__ __forceinline__ void rp_pair2(float2 hx, float2 hy, float2 hz, float2 lx, float2 ly, float2 lz, float2 w,
-                                         long long j, long long i, const float2 (&nh)[3], const float2 (&nl)[3],
+                                         int j, int i, const float2 (&nh)[3], const float2 (&nl)[3],
                                          float2 (&acc)[3]) {
   const float2 dx = __fadd2_rn(__fadd2_rn(hx, nh[0]), __fadd2_rn(lx, nl[0]));
   const float2 dy = __fadd2_rn(__fadd2_rn(hy, nh[1]), __fadd2_rn(ly, nl[1]));
@@ -415,46 +418,48 @@ __device__ __forceinline__ void rp_pair2(float2 hx, float2 hy, float2 hz, float2
   acc[2] = __ffma2_rn(s, dz, acc[2]);
 }
 
-// Four j per iteration from 16-byte shared loads (qn a multiple of 4, sj 16-byte aligned);
-// the terms and their order are those of two j at a time.
+// qn (a multiple of 4) staged j of one part (stride JP between x_hi, y_hi, z_hi, x_lo,
+// y_lo, z_lo, z), four j per iteration from 16-byte shared loads.  Padding entries sit at
+// 1e30 m: r^2 overflows to infinity, rsqrt gives 0, the term is exactly 0.
 template <bool DIAG, bool UNITW>
-__device__ __forceinline__ void rp_chunk(const float* __restrict__ sj, int JW, int qn, long long jbase, long long i,
+__device__ __forceinline__ void rp_chunk(const float* __restrict__ sj, int JP, int qn, int jbase, int i,
                                          const float2 (&nh)[3], const float2 (&nl)[3], float2 (&acc)[3]) {
 #pragma unroll 2
   for (int q = 0; q < qn; q += 4) {
     const float4 hx = *reinterpret_cast<const float4*>(sj + q);
-    const float4 hy = *reinterpret_cast<const float4*>(sj + JW + q);
-    const float4 hz = *reinterpret_cast<const float4*>(sj + 2 * JW + q);
-    const float4 lx = *reinterpret_cast<const float4*>(sj + 3 * JW + q);
-    const float4 ly = *reinterpret_cast<const float4*>(sj + 4 * JW + q);
-    const float4 lz = *reinterpret_cast<const float4*>(sj + 5 * JW + q);
+    const float4 hy = *reinterpret_cast<const float4*>(sj + JP + q);
+    const float4 hz = *reinterpret_cast<const float4*>(sj + 2 * JP + q);
+    const float4 lx = *reinterpret_cast<const float4*>(sj + 3 * JP + q);
+    const float4 ly = *reinterpret_cast<const float4*>(sj + 4 * JP + q);
+    const float4 lz = *reinterpret_cast<const float4*>(sj + 5 * JP + q);
     float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (!UNITW) w = *reinterpret_cast<const float4*>(sj + 6 * JW + q);
+    if (!UNITW) w = *reinterpret_cast<const float4*>(sj + 6 * JP + q);
     rp_pair2<DIAG, UNITW>(make_float2(hx.x, hx.y), make_float2(hy.x, hy.y), make_float2(hz.x, hz.y),
-                          make_float2(lx.x, lx.y), make_float2(ly.x, ly.y), make_float2(lz.x, lz.y),
-                          make_float2(w.x, w.y), jbase + q, i, nh, nl, acc);
+                    make_float2(lx.x, lx.y), make_float2(ly.x, ly.y), make_float2(lz.x, lz.y), make_float2(w.x, w.y),
+                    jbase + q, i, nh, nl, acc);
     rp_pair2<DIAG, UNITW>(make_float2(hx.z, hx.w), make_float2(hy.z, hy.w), make_float2(hz.z, hz.w),
-                          make_float2(lx.z, lx.w), make_float2(ly.z, ly.w), make_float2(lz.z, lz.w),
-                          make_float2(w.z, w.w), jbase + q + 2, i, nh, nl, acc);
+                    make_float2(lx.z, lx.w), make_float2(ly.z, ly.w), make_float2(lz.z, lz.w), make_float2(w.z, w.w),
+                    jbase + q + 2, i, nh, nl, acc);
   }
 }
 
 template <int W>
 __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant__ StepArgs A, const RpArgs P) {
-  // dynamic shared memory: per warp 7 x JW floats (SoA j data); partial sums and
-  // compensations [W][3][32] floats each; the RF phase of the K steps; the owned ions'
+  // dynamic shared memory: per part 7 x JP floats (SoA j data); partial sums and
+  // compensations [NP][3][R] floats each; the RF phase of the K steps; the owned ions'
   // drag velocities [3][R] (laser cooling needs all three components of an ion)
   extern __shared__ __align__(16) float4 s_dyn[];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   const long long n = A.n;
   const unsigned G = gridDim.x;
-  const int JW = P.JW;
-  const long long r0 = (long long)blockIdx.x * P.R;
-  const int Rg = (int)max(0LL, min((long long)P.R, n - r0));
-  float* sj = reinterpret_cast<float*>(s_dyn) + (size_t)warp * 7 * JW;
-  float* ps = reinterpret_cast<float*>(s_dyn) + (size_t)W * 7 * JW;
-  float* pc = ps + W * 96;
-  double* scos = reinterpret_cast<double*>(pc + W * 96);  // 28 W JW + 768 W bytes in: 8-byte aligned
+  const int R = P.R, NP = P.NP, JP = P.JP;
+  const long long r0 = (long long)blockIdx.x * R;
+  const int Rg = (int)max(0LL, min((long long)R, n - r0));
+  float* sall = reinterpret_cast<float*>(s_dyn);
+  float* ps = sall + (size_t)NP * 7 * JP;
+  float* pc = ps + NP * 3 * R;
+  // 28 NP JP + 24 NP R bytes in: a multiple of 8 (JP is a multiple of 4)
+  double* scos = reinterpret_cast<double*>(pc + NP * 3 * R);
   double* svd = scos + P.K;
   unsigned* ctr_step = P.sync;
   const int poller = 32 * W - 1;
@@ -464,6 +469,10 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
   const bool rf = !(tp.flags & (IONTRAP_RF_OFF | IONTRAP_TRAP_OFF | IONTRAP_PSEUDO));
   for (long long k = tid; k < P.K; k += 32 * W) scos[k] = rf ? cos(tp.Omega * ((double)(ns0 + k + 1) * tp.dt)) : 0.0;
 
+  // this thread's pair work: ion slot and j-part
+  const int part = tid / R, slot = tid - part * R;
+  const bool works = part < NP;
+  const int ii = (int)(r0 + slot);
   // owned items: thread k < 3 Rg integrates component c = k / Rg of ion r0 + k % Rg
   const int rq = max(Rg, 1);
   const int oc = tid / rq, oq = tid - oc * rq;
@@ -521,70 +530,73 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
       if (sd.sigma > 0.0) ext = __fma_rn(sd.sigma, (double)zk, ext);
     }
 
-    // stage this warp's j-range (positions x_{ns+1})
+    // stage every part's j-range (positions x_{ns+1}): entry e is j = e, part e / JP
     const float4* __restrict__ ghi = A.hi[rb];
     const float4* __restrict__ glo = A.lo[rb];
-    const long long jw0 = (long long)warp * JW;
-    for (int q = lane; q < JW; q += 32) {
-      const long long j = jw0 + q;
+    for (int e = tid; e < NP * JP; e += 32 * W) {
+      const int p = e / JP, q = e - p * JP;
       float4 h = make_float4(1e30f, 1e30f, 1e30f, 0.0f), l = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (j < n) {
-        h = __ldcg(ghi + j);
-        l = __ldcg(glo + j);
+      if (e < n) {
+        h = __ldcg(ghi + e);
+        l = __ldcg(glo + e);
       }
-      sj[q] = h.x, sj[JW + q] = h.y, sj[2 * JW + q] = h.z;
-      sj[3 * JW + q] = l.x, sj[4 * JW + q] = l.y, sj[5 * JW + q] = l.z;
-      sj[6 * JW + q] = h.w;
+      float* d = sall + (size_t)p * 7 * JP + q;
+      d[0] = h.x, d[JP] = h.y, d[2 * JP] = h.z;
+      d[3 * JP] = l.x, d[4 * JP] = l.y, d[5 * JP] = l.z;
+      d[6 * JP] = h.w;
     }
-    const long long ii = r0 + lane;
     float4 hi4 = make_float4(0.f, 0.f, 0.f, 0.f), lo4 = hi4;
-    if (lane < Rg) {
+    if (works && slot < Rg) {
       hi4 = __ldcg(ghi + ii);
       lo4 = __ldcg(glo + ii);
     }
     const float2 nh[3] = {make_float2(-hi4.x, -hi4.x), make_float2(-hi4.y, -hi4.y), make_float2(-hi4.z, -hi4.z)};
     const float2 nl[3] = {make_float2(-lo4.x, -lo4.x), make_float2(-lo4.y, -lo4.y), make_float2(-lo4.z, -lo4.z)};
-    __syncwarp();
+    __syncthreads();
     trace_mark(A.trace, tslot + 1);
 
-    float ks[3] = {0.f, 0.f, 0.f}, kcp[3] = {0.f, 0.f, 0.f};
-    for (int c0 = 0; c0 < JW; c0 += kSeg) {
-      const int qn = min(kSeg, JW - c0);
-      const long long jc = jw0 + c0;
-      const bool diag = (jc < r0 + Rg) && (r0 < jc + qn);
-      float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-      if (A.unitw) {
-        if (diag)
-          rp_chunk<true, true>(sj + c0, JW, qn, jc, ii, nh, nl, acc);
-        else
-          rp_chunk<false, true>(sj + c0, JW, qn, jc, ii, nh, nl, acc);
-      } else {
-        if (diag)
-          rp_chunk<true, false>(sj + c0, JW, qn, jc, ii, nh, nl, acc);
-        else
-          rp_chunk<false, false>(sj + c0, JW, qn, jc, ii, nh, nl, acc);
+    if (works) {
+      const float* sj = sall + (size_t)part * 7 * JP;
+      float ks[3] = {0.f, 0.f, 0.f}, kcp[3] = {0.f, 0.f, 0.f};
+      for (int c0 = 0; c0 < JP; c0 += kSeg) {
+        const int qn = min(kSeg, JP - c0);
+        float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        // the self pair can only sit in a chunk that overlaps the CTA's own ions; the
+        // variant is chosen per warp (its lanes may belong to two parts)
+        const int jc = part * JP + c0;
+        const bool diag = __any_sync(__activemask(), (jc < r0 + Rg) && (r0 < jc + qn));
+        if (A.unitw) {
+          if (diag)
+            rp_chunk<true, true>(sj + c0, JP, qn, jc, ii, nh, nl, acc);
+          else
+            rp_chunk<false, true>(sj + c0, JP, qn, jc, ii, nh, nl, acc);
+        } else {
+          if (diag)
+            rp_chunk<true, false>(sj + c0, JP, qn, jc, ii, nh, nl, acc);
+          else
+            rp_chunk<false, false>(sj + c0, JP, qn, jc, ii, nh, nl, acc);
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const float a = acc[d].x + acc[d].y;
+          const float y = a - kcp[d];
+          const float tt = ks[d] + y;
+          kcp[d] = (tt - ks[d]) - y;
+          ks[d] = tt;
+        }
       }
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        const float a = acc[d].x + acc[d].y;
-        const float y = a - kcp[d];
-        const float tt = ks[d] + y;
-        kcp[d] = (tt - ks[d]) - y;
-        ks[d] = tt;
+        ps[(part * 3 + d) * R + slot] = ks[d];
+        pc[(part * 3 + d) * R + slot] = kcp[d];
       }
-    }
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      ps[(warp * 3 + d) * 32 + lane] = ks[d];
-      pc[(warp * 3 + d) * 32 + lane] = kcp[d];
     }
     __syncthreads();
     trace_mark(A.trace, tslot + 2);
 
-    if (own) {  // merge in warp order (Kahan), then finish the step
+    if (own) {  // merge in part order (Kahan), then finish the step
       float su = 0.f, cu = 0.f;
-#pragma unroll 8
-      for (int w = 0; w < W; ++w) kahan_merge(su, cu, ps[(w * 3 + oc) * 32 + oq], pc[(w * 3 + oc) * 32 + oq]);
+      for (int p = 0; p < NP; ++p) kahan_merge(su, cu, ps[(p * 3 + oc) * R + oq], pc[(p * 3 + oc) * R + oq]);
       const double Sd = (double)cu - (double)su;
       const SpeciesDev& sd = A.spc[spe];
       if (forces) {
@@ -634,9 +646,13 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
   }
 }
 
-size_t rp_smem_bytes(int W, int JW, long long K) {
-  return (size_t)W * 7 * JW * sizeof(float) + 2 * (size_t)W * 96 * sizeof(float) + (size_t)K * sizeof(double) +
-         3 * 32 * sizeof(double);
+// Dynamic shared memory of a launch: the parts' SoA j data (NP x 7 x JP floats), the part
+// partials (2 x NP x 3 x R floats), K cosines and 3 R drag velocities.
+size_t rp_smem_bytes(int W, int R, int NP, int JP, long long K) {
+  (void)W;
+  const size_t parts = (size_t)NP * 7 * JP * sizeof(float);
+  const size_t recs = 2 * (size_t)NP * 3 * R * sizeof(float);
+  return parts + recs + (size_t)K * sizeof(double) + 3 * (size_t)R * sizeof(double);
 }
 
 const void* rp_kernel(int W) {
@@ -647,29 +663,28 @@ const void* rp_kernel(int W) {
   }
 }
 
-// Co-resident CTAs of the W-warp row-persistent kernel with JW j per warp and up to max_k
-// steps per launch (the dynamic shared-memory limit is raised to the largest launch any
-// handle may make: JW of max_jw).
-int rp_max_ctas(int W, int JW, int max_jw, long long max_k, int sms) {
+// Co-resident CTAs of a launch shape with up to max_k steps per launch (the kernel's
+// dynamic shared-memory limit is raised to 227 KB once, so handles coexist).
+int rp_max_ctas(int W, int R, int NP, int JP, long long max_k, int sms) {
   const void* fn = rp_kernel(W);
-  if (!fn || JW > max_jw || JW < 2) return 0;
-  const size_t limit = rp_smem_bytes(W, max_jw, max_k);
-  if (limit > 227 * 1024) return 0;
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit) != cudaSuccess) return 0;
+  if (!fn) return 0;
+  const size_t smem = rp_smem_bytes(W, R, NP, JP, max_k);
+  if (smem > 227 * 1024) return 0;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess) return 0;
   int per = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, 32 * W, rp_smem_bytes(W, JW, max_k)) != cudaSuccess)
-    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, 32 * W, smem) != cudaSuccess) return 0;
   return per * sms;
 }
 
-cudaError_t launch_rp(const StepArgs& a, unsigned* sync, int W, int R, int G, int JW, long long K, cudaStream_t st) {
+cudaError_t launch_rp(const StepArgs& a, unsigned* sync, int W, int R, int NP, int JP, int G, long long K,
+                      cudaStream_t st) {
   const void* fn = rp_kernel(W);
   if (!fn) return cudaErrorInvalidValue;
-  RpArgs P{sync, K, R, JW};
+  RpArgs P{sync, K, R, NP, JP};
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)G);
   cfg.blockDim = dim3((unsigned)(32 * W));
-  cfg.dynamicSmemBytes = rp_smem_bytes(W, JW, K);
+  cfg.dynamicSmemBytes = rp_smem_bytes(W, R, NP, JP, K);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

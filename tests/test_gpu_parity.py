@@ -456,11 +456,13 @@ def _rp_cfg(W, R):
 
 @pytest.mark.parametrize("n,W,R,steps", [(300, 8, 2, 100), (1000, 16, 7, 100), (2049, 8, 14, 100),
                                          (3000, 16, 20, 100), (4096, 16, 27, 60), (4096, 8, 32, 60),
-                                         (4864, 16, 32, 20)])
+                                         (4864, 16, 32, 20), (5000, 16, 40, 40), (6000, 16, 100, 40),
+                                         (2500, 16, 170, 60), (1200, 8, 85, 100)])
 def test_row_persistent_form_trajectory_matches_oracle(it, n, W, R, steps):
-    """The row-persistent form (each CTA sums its own ions over every j, warps split the
-    j-range, merge in shared memory) against the oracle on ragged ion counts, both warp
-    counts and ions per CTA from 2 to 32, with mixed charges."""
+    """The row-persistent form (each CTA sums its own ions over every j, its threads laid
+    out as ion x j-part, parts merged in shared memory) against the oracle on ragged ion
+    counts, both warp counts and ions per CTA from 2 to 170 (parts spanning warps, warps
+    spanning parts), with mixed charges."""
     w = _cloud(n, 700 + n)
     q, m, p = _oracle_side(w)
     xo, vo, _ = oracle.run(w.x0, w.v0, q, m, p, steps)
@@ -516,14 +518,20 @@ def test_row_persistent_form_bitwise_across_launches_and_restore(it):
 
 
 def test_row_persistent_shape_limits(it):
-    """More than 32 ions per CTA, the FP64 form, or a j-range per warp beyond shared memory
-    are refused."""
+    """More ions per CTA than a third of its threads, two ions per thread, the FP64 form,
+    or staged j beyond shared memory are refused."""
     w = _cloud(1000, 3)
     with _sim(it, w, 0) as s:
         with pytest.raises(it.IonTrapError):
-            s.set_config(512, 1, 1, 33, 5)
+            s.set_config(512, 1, 1, 171, 5)
+        with pytest.raises(it.IonTrapError):
+            s.set_config(256, 1, 1, 86, 5)
         with pytest.raises(it.IonTrapError):
             s.set_config(512, 2, 1, 16, 5)
+    w2 = _cloud(9000, 4, species=(iongen.CA40,))
+    with _sim(it, w2, 0) as s:
+        with pytest.raises(it.IonTrapError):
+            s.set_config(512, 1, 1, 60, 5)
     with _sim(it, w, 1) as s:
         with pytest.raises(it.IonTrapError):
             s.set_config(512, 1, 1, 16, 5)
