@@ -433,7 +433,8 @@ int iontrap_forces_noalloc(const iontrap_species *species, int n_species, const 
 int iontrap_trace_step(iontrap_t *h, unsigned long long *marks, int64_t cap, int64_t *n_force, int64_t *n_epi);
 
 /* Autotuner.  Times candidate launch configurations (threads x ions per thread x packed,
- * a ladder of split counts, fused or separate epilogue) on this handle's own workload,
+ * a ladder of split counts, the merge forms 0-3 and shapes of the persistent forms 4 and
+ * 5; see iontrap_config) on this handle's own workload,
  * each for about trial_us of steps, installs the fastest and records it in the
  * process-wide tuning table under (precision, floor(log2 n)) for the current device;
  * handles created later with n in that bucket start from it.  The handle's state is
