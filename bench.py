@@ -310,6 +310,9 @@ def run_gpu(args):
                    "tile_fields": "threads, ions_per_thread, packed, jsplit, fused, pdl, graph (autotuned)",
                    "l2": "flushed (256 MB write) between timed steps; state is L2-resident within a step"},
         "pair_interactions_per_s": value * (n - 1),
+        "unordered_pairs_per_s": value * (n - 1) / 2,
+        "pairs_note": "pair_interactions_per_s counts ordered pairs N(N-1) per timestep, as the kernels evaluate "
+                      "them; the method itself needs the N(N-1)/2 unordered pairs (unordered_pairs_per_s)",
         "force_rel_rms_vs_oracle": force_err,
         "error_note": "GPU Coulomb accelerations vs the FP64 oracle on 256 sampled ions of the final state "
                       "(bar 1e-5); trajectories: tests/test_gpu_parity.py",
