@@ -327,7 +327,10 @@ typedef struct {
                                     in shared memory: n up to about 7000); each CTA sums its R
                                     ions over every j, thread t taking ion t % R against j-part
                                     t / R, merges the part partials in shared memory and
-                                    integrates; one grid-wide counter per step; the evaluation
+                                    integrates; one grid-wide counter per step; after a
+                                    launch's first step the positions arrive by bulk TMA
+                                    copies of a part-major global copy that the owners
+                                    write (kept in the handle's partial-sum scratch); the evaluation
                                     at creation uses form 1 over 512-ion j-ranges; not with
                                     IONTRAP_COULOMB_OFF.
                                  The FP64 form supports 1 only. */
@@ -424,7 +427,8 @@ int iontrap_forces_noalloc(const iontrap_species *species, int n_species, const 
 /* Profiling hook: run ONE step with per-CTA phase timestamps (%globaltimer, ns) and copy
  * them to marks[cap] (EINVAL in the grid-persistent form 4; in the row-persistent form 5
  * one launch of 8 steps, 4 marks per CTA and step at mark (CTA 8 + step) 4 + m: grid
- * barrier passed, warp 0's j-range staged, every warp's pair loop done, integration done;
+ * barrier passed, thread 0's j-part in shared memory (its copy run landed; in the
+ * launch's first step, every part staged), every pair loop done, integration done;
  * *n_force = 32 x CTAs, *n_epi = 0).  Layout: 4 marks per force-kernel CTA, CTA id = y*grid.x + x
  * (start after the grid dependency wait, end of the pair loop, start of the fused
  * epilogue or 0, end of the fused epilogue or 0), then 2 per epilogue-kernel CTA (start,
@@ -435,7 +439,8 @@ int iontrap_trace_step(iontrap_t *h, unsigned long long *marks, int64_t cap, int
 /* Autotuner.  Times candidate launch configurations (threads x ions per thread x packed,
  * a ladder of split counts, the merge forms 0-3 and shapes of the persistent forms 4 and
  * 5; see iontrap_config) on this handle's own workload,
- * each for about trial_us of steps, installs the fastest and records it in the
+ * each for about trial_us of steps in each of two passes (a candidate's faster time
+ * counts), installs the fastest and records it in the
  * process-wide tuning table under (precision, floor(log2 n)) for the current device;
  * handles created later with n in that bucket start from it.  The handle's state is
  * checkpointed before and restored after, so tuning does not advance the simulation.

@@ -383,6 +383,13 @@ int gp_max_ctas(int W, int S, int Lmax, int max_lmax, long long max_k, int sms) 
 // step; no partial sum leaves the SM.  The next step's force-independent terms are
 // evaluated right after the CTA has counted itself, while the others finish.
 //
+// Positions travel between steps in the same part-major layout the CTAs hold them in:
+// besides the float4 pair stream, every owner writes its new position into a global copy
+// of the staged arrays, so from the second step of a launch on one thread fetches them
+// with bulk TMA copies of kRpBatches runs of consecutive parts, each completing on its own
+// mbarrier, and a part's threads start as soon as their run has landed.  The CTA's own
+// ions come from shared memory, where their owners left them.
+//
 // Summation order depends on (n, R, W) only: per part, j ascending in 128-j chunks summed
 // as even and odd j (the two halves added), chunks Kahan-added; parts Kahan-merged in
 // order.  Each (i, j) term is the same FP32 value as in the other forms.
@@ -395,6 +402,9 @@ struct RpArgs {
   int JP;          // j entries per part: a multiple of 4 with JP / 4 odd (the parts of one
                    // warp read from distinct shared-memory banks); entries past n are padding
 };
+
+// Bulk copies (and mbarriers) per step: the parts are fetched in up to this many runs.
+constexpr int kRpBatches = 8;
 
 // Pair terms of one thread's ion against two j (packed); DIAG: the self pair is excluded
 // by its index (only chunks that may hold it take this variant).
@@ -447,7 +457,8 @@ template <int W>
 __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant__ StepArgs A, const RpArgs P) {
   // dynamic shared memory: per part 7 x JP floats (SoA j data); partial sums and
   // compensations [NP][3][R] floats each; the RF phase of the K steps; the owned ions'
-  // drag velocities [3][R] (laser cooling needs all three components of an ion)
+  // drag velocities [3][R] (laser cooling needs all three components of an ion); the
+  // copy mbarriers; the owned ions' next positions [6][R] (hi x, y, z, lo x, y, z)
   extern __shared__ __align__(16) float4 s_dyn[];
   const int tid = threadIdx.x;
   const long long n = A.n;
@@ -461,6 +472,12 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
   // 28 NP JP + 24 NP R bytes in: a multiple of 8 (JP is a multiple of 4)
   double* scos = reinterpret_cast<double*>(pc + NP * 3 * R);
   double* svd = scos + P.K;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(svd + 3 * R);
+  float* sself = reinterpret_cast<float*>(bar + kRpBatches);
+  // global part-major copies of the staged arrays, one per pair-stream buffer
+  const long long soa_len = (long long)NP * 7 * JP;
+  float* gsoa = reinterpret_cast<float*>(A.part);
+  const int nb = min(NP, kRpBatches);
   unsigned* ctr_step = P.sync;
   const int poller = 32 * W - 1;
   const TrapDev& tp = A.trap;
@@ -468,16 +485,33 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
   const bool forces = A.mode == MODE_FORCES;  // one force evaluation of the current positions (K = 1)
   const bool rf = !(tp.flags & (IONTRAP_RF_OFF | IONTRAP_TRAP_OFF | IONTRAP_PSEUDO));
   for (long long k = tid; k < P.K; k += 32 * W) scos[k] = rf ? cos(tp.Omega * ((double)(ns0 + k + 1) * tp.dt)) : 0.0;
+  if (tid == 0)
+    for (int b = 0; b < nb; ++b) mbar_init(&bar[b], 1);
+  // the padding entries of both global copies (their values never change); published to
+  // the other CTAs by this CTA's first step arrival
+  if (blockIdx.x == 0 && P.K > 1)
+    for (long long e = n + tid; e < (long long)NP * JP; e += 32 * W) {
+      const int p = (int)(e / JP), q = (int)(e - (long long)p * JP);
+#pragma unroll
+      for (int c = 0; c < 7; ++c) {
+        const float val = c < 3 ? 1e30f : 0.0f;
+        gsoa[(long long)p * 7 * JP + c * JP + q] = val;
+        gsoa[soa_len + (long long)p * 7 * JP + c * JP + q] = val;
+      }
+    }
 
   // this thread's pair work: ion slot and j-part
   const int part = tid / R, slot = tid - part * R;
   const bool works = part < NP;
   const int ii = (int)(r0 + slot);
+  const int mybatch = works ? ((part + 1) * nb - 1) / NP : 0;  // the copy run holding this part
   // owned items: thread k < 3 Rg integrates component c = k / Rg of ion r0 + k % Rg
   const int rq = max(Rg, 1);
   const int oc = tid / rq, oq = tid - oc * rq;
   const bool own = tid < 3 * Rg;
   const long long ie = r0 + oq;
+  const long long iep = ie / JP;
+  const long long ieo = iep * 7 * JP + (ie - iep * JP);  // ion ie's entry in a part-major copy
   int spe = 0;
   double xf = 0.0, vd = 0.0;
   float z = 0.f;
@@ -516,6 +550,19 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
     if (t > 0 && tid == poller) {
       bad = !gp_wait(ctr_step, G * (unsigned)t, A.err);
       fence_gpu();
+      if (!bad) {
+        // the positions the other CTAs wrote (generic stores, ordered by the counter)
+        // are read by the copy engine, and this CTA's shared memory last read by threads
+        // is written by it: both need a proxy fence
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        const float* src = gsoa + (rb ? soa_len : 0);
+        for (int b = 0; b < nb; ++b) {
+          const int p0 = b * NP / nb, p1 = (b + 1) * NP / nb;
+          const uint32_t bytes = (uint32_t)((p1 - p0) * 7 * JP * sizeof(float));
+          mbar_arrive_expect_tx(&bar[b], bytes);
+          tma_bulk_g2s(sall + (size_t)p0 * 7 * JP, src + (size_t)p0 * 7 * JP, bytes, &bar[b]);
+        }
+      }
     }
     if (__syncthreads_or(bad)) break;
     // optional phase timestamps (iontrap_trace_step): 4 per CTA and step
@@ -530,32 +577,41 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
       if (sd.sigma > 0.0) ext = __fma_rn(sd.sigma, (double)zk, ext);
     }
 
-    // stage every part's j-range (positions x_{ns+1}): entry e is j = e, part e / JP
-    const float4* __restrict__ ghi = A.hi[rb];
-    const float4* __restrict__ glo = A.lo[rb];
-    for (int e = tid; e < NP * JP; e += 32 * W) {
-      const int p = e / JP, q = e - p * JP;
-      float4 h = make_float4(1e30f, 1e30f, 1e30f, 0.0f), l = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (e < n) {
-        h = __ldcg(ghi + e);
-        l = __ldcg(glo + e);
-      }
-      float* d = sall + (size_t)p * 7 * JP + q;
-      d[0] = h.x, d[JP] = h.y, d[2 * JP] = h.z;
-      d[3 * JP] = l.x, d[4 * JP] = l.y, d[5 * JP] = l.z;
-      d[6 * JP] = h.w;
-    }
+    // positions x_{ns+1} of every part: entry e is j = e, part e / JP.  The first step of
+    // a launch stages them from the pair stream; later steps wait for their copy run.
     float4 hi4 = make_float4(0.f, 0.f, 0.f, 0.f), lo4 = hi4;
-    if (works && slot < Rg) {
-      hi4 = __ldcg(ghi + ii);
-      lo4 = __ldcg(glo + ii);
+    if (t == 0) {
+      const float4* __restrict__ ghi = A.hi[rb];
+      const float4* __restrict__ glo = A.lo[rb];
+      for (int e = tid; e < NP * JP; e += 32 * W) {
+        const int p = e / JP, q = e - p * JP;
+        float4 h = make_float4(1e30f, 1e30f, 1e30f, 0.0f), l = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (e < n) {
+          h = __ldcg(ghi + e);
+          l = __ldcg(glo + e);
+        }
+        float* d = sall + (size_t)p * 7 * JP + q;
+        d[0] = h.x, d[JP] = h.y, d[2 * JP] = h.z;
+        d[3 * JP] = l.x, d[4 * JP] = l.y, d[5 * JP] = l.z;
+        d[6 * JP] = h.w;
+      }
+      if (works && slot < Rg) {
+        hi4 = __ldcg(ghi + ii);
+        lo4 = __ldcg(glo + ii);
+      }
+      __syncthreads();
+    } else {
+      if (works && slot < Rg) {
+        hi4 = make_float4(sself[slot], sself[R + slot], sself[2 * R + slot], 0.f);
+        lo4 = make_float4(sself[3 * R + slot], sself[4 * R + slot], sself[5 * R + slot], 0.f);
+      }
+      if (works) bad = !mbar_wait_bounded(&bar[mybatch], (uint32_t)((t - 1) & 1), kWaitLimitNs);
     }
     const float2 nh[3] = {make_float2(-hi4.x, -hi4.x), make_float2(-hi4.y, -hi4.y), make_float2(-hi4.z, -hi4.z)};
     const float2 nl[3] = {make_float2(-lo4.x, -lo4.x), make_float2(-lo4.y, -lo4.y), make_float2(-lo4.z, -lo4.z)};
-    __syncthreads();
     trace_mark(A.trace, tslot + 1);
 
-    if (works) {
+    if (works && !bad) {
       const float* sj = sall + (size_t)part * 7 * JP;
       float ks[3] = {0.f, 0.f, 0.f}, kcp[3] = {0.f, 0.f, 0.f};
       for (int c0 = 0; c0 < JP; c0 += kSeg) {
@@ -591,7 +647,14 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
         pc[(part * 3 + d) * R + slot] = kcp[d];
       }
     }
-    __syncthreads();
+    if (__syncthreads_or(bad)) {  // a copy run never landed: flag, let every copy finish, stop
+      if (tid == poller) {
+        atomicOr(A.err, ERR_TIMEOUT);
+        for (int b = 0; b < nb; ++b) mbar_wait_bounded(&bar[b], (uint32_t)((t - 1) & 1), kWaitLimitNs);
+      }
+      __syncthreads();
+      break;
+    }
     trace_mark(A.trace, tslot + 2);
 
     if (own) {  // merge in part order (Kahan), then finish the step
@@ -616,6 +679,15 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
         if (oc == 0) {
           reinterpret_cast<float*>(A.hi[rb ^ 1] + ie)[3] = sd.w;
           reinterpret_cast<float*>(A.lo[rb ^ 1] + ie)[3] = 0.0f;
+        }
+        if (t + 1 < P.K) {  // the next step's copies: part-major global, own ions in shared
+          float* g = gsoa + (rb ? 0 : soa_len) + ieo;
+          g[oc * JP] = h;
+          g[(3 + oc) * JP] = l;
+          if (oc == 0) g[6 * JP] = sd.w;
+          sself[oc * R + oq] = h;
+          sself[(3 + oc) * R + oq] = l;
+          asm volatile("fence.proxy.async.global;" ::: "memory");
         }
         // a non-finite acceleration or velocity reaches xn = xf + dt (vn + dt/2 acc)
         if (!isfinite(xn)) atomicOr(A.err, ERR_NONFINITE);
@@ -647,13 +719,18 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
 }
 
 // Dynamic shared memory of a launch: the parts' SoA j data (NP x 7 x JP floats), the part
-// partials (2 x NP x 3 x R floats), K cosines and 3 R drag velocities.
+// partials (2 x NP x 3 x R floats), K cosines, 3 R drag velocities, the copy mbarriers and
+// the owned ions' next positions (6 R floats).
 size_t rp_smem_bytes(int W, int R, int NP, int JP, long long K) {
   (void)W;
   const size_t parts = (size_t)NP * 7 * JP * sizeof(float);
   const size_t recs = 2 * (size_t)NP * 3 * R * sizeof(float);
-  return parts + recs + (size_t)K * sizeof(double) + 3 * (size_t)R * sizeof(double);
+  return parts + recs + (size_t)K * sizeof(double) + 3 * (size_t)R * sizeof(double) +
+         kRpBatches * sizeof(uint64_t) + 6 * (size_t)R * sizeof(float);
 }
+
+// Global scratch of a launch: the two part-major position copies (NP x 7 x JP floats each).
+size_t rp_scratch_bytes(int NP, int JP) { return 2 * (size_t)NP * 7 * JP * sizeof(float); }
 
 const void* rp_kernel(int W) {
   switch (W) {
