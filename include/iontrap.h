@@ -246,9 +246,11 @@ int iontrap_restore(iontrap_t *h, const double *x, const double *v, const double
 
 /* Enqueue n_steps[k] steps on each of count handles (the batched form of evolve(N)).
  * FP32-form handles with n <= 2048 on the device of the first such handle are advanced
- * together by one launch per 100 steps of a cluster kernel that keeps every ensemble
- * resident in shared memory (pair stream) and registers (FP64 state); the others are
- * stepped one by one as by iontrap_step.  Work is ordered after what is already queued
+ * together, 100 steps per launch, with every ensemble resident in shared memory
+ * (positions) and registers (FP64 state): ensembles above 256 ions by groups of 2, 4 or
+ * 8 CTAs of a cluster (part-major, positions exchanged through distributed shared
+ * memory), smaller ones by a CTA or a warp each, the two grids side by side; the others
+ * are stepped one by one as by iontrap_step.  Work is ordered after what is already queued
  * on each handle's stream, and each handle's later work waits for the batch.  A
  * batched ensemble's result depends only on its own inputs: it is bitwise the same
  * alone or in any mix (its summation order differs from iontrap_step's, so the two

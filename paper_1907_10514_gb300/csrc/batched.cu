@@ -1,22 +1,22 @@
 // batched.cu -- many independent trap simulations advanced by one launch (sm_103a).
 //
-// Each ensemble (N <= 2048, FP32 form) keeps its FP32 hi/lo pair stream resident in
-// shared memory and its FP64 state (x, v, a) in registers for all K steps of a launch,
-// so a step costs no global-memory traffic and no kernel boundary.  CTAs of 128 threads
-// (4 warps, 2 ions per lane on packed FP32x2 instructions, 64 ions per warp) are grouped
-// in clusters of 8:
-//   N <= 64          one warp; up to four such ensembles share a CTA
-//   64 < N <= 256    one CTA
-//   256 < N <= 2048  2, 4 or 8 CTAs of one cluster, 256 ions each; every CTA keeps a full
-//                    copy of the ensemble's pair stream and writes its ions' new entries
-//                    into the other copies through distributed shared memory
-// Every step: pair sum over the ensemble's stream -> cluster barrier (all reads done) ->
-// integrate own ions, write new stream entries locally and remotely -> cluster barrier.
-// The barriers are the hardware cluster barrier: no spin-wait on memory.
+// Each ensemble (N <= 2048, FP32 form) keeps its positions resident in shared memory and
+// its FP64 state in registers for all K steps of a launch, so a step costs no
+// global-memory traffic and no kernel boundary.  Two kernels share the work:
+//   N <= 256         k_batched: CTAs of 128 threads (4 warps, 2 ions per lane on packed
+//                    FP32x2 instructions, 64 ions per warp); an ensemble of <= 64 ions is
+//                    one warp (up to four share a CTA), a larger one a whole CTA; the CTA
+//                    barrier is the only synchronisation
+//   256 < N <= 2048  k_batched_rp: groups of 2, 4 or 8 CTAs of 256 threads inside a
+//                    cluster of 8, part-major like the row-persistent form, positions
+//                    exchanged through distributed shared memory, one cluster barrier per
+//                    step (no spin-wait on memory)
+// The two grids run on two streams side by side.  In both, the summation order of an
+// ion's Coulomb sum is a function of N only: an ensemble's trajectory is the same bits
+// alone or packed with any other ensembles.
 //
-// The Coulomb sum of an ion runs over j ascending in 64-ion chunks (plain FP32 inside a
-// chunk, Kahan across chunks), a function of N only: an ensemble's trajectory is the
-// same bits alone or packed with any other ensembles.
+// k_batched: the Coulomb sum of an ion runs over j ascending in 64-ion chunks (plain FP32
+// inside a chunk, Kahan across chunks).
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -30,12 +30,11 @@ namespace cg = cooperative_groups;
 
 namespace it {
 
-constexpr int kBCluster = 8;
 constexpr int kBThreads = 128;
 constexpr int kBWarps = kBThreads / 32;
 constexpr int kBWarpIons = 64;
 constexpr int kBCtaIons = kBWarps * kBWarpIons;  // 256
-constexpr int kBMaxN = kBCluster * kBCtaIons;    // 2048
+constexpr int kBMaxN = 2048;                     // largest batched ensemble
 constexpr int kBChunk = 64;
 
 
@@ -45,26 +44,16 @@ struct BatchCta {
   int soff[kBWarps];       // float4 offset of each ensemble's hi block in shared memory
   int warp_le[kBWarps];    // local ensemble index served by each warp, -1 idle
   int warp_i0[kBWarps];    // first ion of each warp's 64-ion slice
-  int rank0, nranks;       // cluster ranks that hold copies of ens[0] (multi-CTA ensemble)
 };
 
-// clustered = 1: launched in clusters of 8 (ensembles spread over several CTAs, synced by
-// the hardware cluster barrier); 0: every CTA holds whole ensembles and only syncs itself.
+// Every CTA holds whole ensembles and only syncs itself.
 __global__ void __launch_bounds__(kBThreads)
-    k_batched(BatchEns* __restrict__ E, const BatchCta* __restrict__ J, int K, int clustered) {
+    k_batched(BatchEns* __restrict__ E, const BatchCta* __restrict__ J, int K) {
   extern __shared__ __align__(16) float4 sm[];
   __shared__ BatchCta job;
   __shared__ double s_springs[kBWarps][IONTRAP_MAX_SPECIES][3];
   __shared__ int s_steps[kBWarps];
   __shared__ long long s_n0[kBWarps];
-  cg::cluster_group cluster = cg::this_cluster();
-  const unsigned my_rank = clustered ? cluster.block_rank() : 0u;
-  auto sync_all = [&]() {
-    if (clustered)
-      cluster.sync();
-    else
-      __syncthreads();
-  };
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
   if (tid == 0) job = J[blockIdx.x];
@@ -116,9 +105,9 @@ __global__ void __launch_bounds__(kBThreads)
         xf[q][c] = drift(x[q][c], vd[q][c], ens->trap.dt);
       }
   }
-  sync_all();  // every copy staged before any CTA writes into another's
+  __syncthreads();  // every stream staged
 
-  // CTAs of one cluster may hold ensembles with different step counts: the loop runs to K
+  // the ensembles of one CTA may have different step counts: the loop runs to K
   for (int k = 0; k < K; ++k) {
     // per held ensemble: RF phase at the force time, then its species' spring constants
     if (tid < job.nens && k < s_steps[tid]) {
@@ -189,7 +178,7 @@ __global__ void __launch_bounds__(kBThreads)
 #pragma unroll
         for (int c = 0; c < 3; ++c) S[q][c] = (double)kc[q][c] - (double)ks[q][c];  // negated sums
     }
-    sync_all();  // every read of every stream copy is done
+    __syncthreads();  // every read of the stream is done
     if (active) {
       const TrapDev& tp = ens->trap;
       float4* sh = sm + job.soff[le];
@@ -219,14 +208,11 @@ __global__ void __launch_bounds__(kBThreads)
         }
         const float4 h4 = make_float4(hv[0], hv[1], hv[2], sd.w);
         const float4 l4 = make_float4(lv[0], lv[1], lv[2], 0.0f);
-        for (int r = job.rank0; r < job.rank0 + job.nranks; ++r) {
-          float4* dst = (r == (int)my_rank) ? sh : cluster.map_shared_rank(sh, (unsigned)r);
-          dst[ii[q]] = h4;
-          dst[n + ii[q]] = l4;
-        }
+        sh[ii[q]] = h4;
+        sh[n + ii[q]] = l4;
       }
     }
-    sync_all();  // new entries visible in every copy
+    __syncthreads();  // new entries visible
   }
 
   // write back: FP64 state, the pair stream x_{n+1} of the final state, step, flags
@@ -255,17 +241,260 @@ __global__ void __launch_bounds__(kBThreads)
   }
 }
 
-// ------------------------------------------------------------------ host side
-struct BatchPlan {
-  std::vector<BatchCta> clustered;  // CTAs of ensembles spread over 2, 4 or 8 CTAs (clusters of 8)
-  std::vector<BatchCta> single;     // CTAs holding whole ensembles (no cluster)
-  size_t smem_clustered = 0, smem_single = 0;
+// ------------------------------------------------------------------ part-major groups
+// Ensembles of 257..2048 ions: a group of C = 2, 4 or 8 CTAs of kBRThreads threads inside a
+// cluster of kBRCluster CTAs, each CTA owning R = ceil(n / C) ions.  Every CTA holds the whole ensemble as part-major SoA floats (NP parts of JP
+// entries: x_hi, y_hi, z_hi, x_lo, y_lo, z_lo) in two shared-memory buffers, the positions
+// of the current step and those of the next, which the owners of every CTA of the group
+// write through distributed shared memory, and the charges z once.  The pair work is R x NP items (ion slot s, part p), item
+// m = p R + s, taken round-robin by the threads (NP chosen so that the threads are busy in
+// every round); the part partials merge in part order and thread s < R integrates ion
+// r R + s in FP64.  One cluster barrier per step.
+//
+// Summation order: per part, j ascending in 128-j chunks (even and odd j summed apart and
+// added), chunks Kahan-added, parts Kahan-merged in order -- a function of n only (C, R,
+// NP and JP are), so an ensemble's trajectory is the same bits alone or in any mix.
+constexpr int kBRThreads = 256;
+constexpr int kBRCluster = 8;
+constexpr int kBRMaxParts = 16;
+
+struct BatchRpCta {
+  int e;      // ensemble, -1: idle CTA
+  int r;      // this CTA's index in the ensemble's group
+  int rank0;  // cluster rank of the group's first CTA
+  int C;      // CTAs in the group
+  int R;      // ions per CTA: ceil(n / C)
+  int NP;     // j-parts
+  int JP;     // entries per part: a multiple of 4 (JP / 4 odd when R % 32 != 0)
 };
 
-// Pack ensembles (sizes n[e]) into CTAs: ensembles above one CTA's 256 ions into
-// aligned power-of-two groups of clusters of 8 (largest first, similar sizes together);
-// the rest one per CTA (64 < N <= 256) or four per CTA (N <= 64), heaviest first, in a
-// grid without clusters.
+// Shared memory of a group CTA: two buffers of NP x 6 x JP floats, the charges (NP x JP)
+// and the part partials (sum, compensation) [NP][3][R] floats each.  At most ~113 KB (two
+// CTAs per SM) up to n ~ 2048.
+static size_t brp_smem_bytes(int R, int NP, int JP) {
+  return 13 * (size_t)NP * JP * sizeof(float) + 2 * (size_t)NP * 3 * R * sizeof(float);
+}
+
+__global__ void __launch_bounds__(kBRThreads, 2)
+    k_batched_rp(BatchEns* __restrict__ E, const BatchRpCta* __restrict__ J, int K) {
+  extern __shared__ __align__(16) float4 sm[];
+  __shared__ double s_springs[IONTRAP_MAX_SPECIES][3];
+  const int tid = threadIdx.x;
+  const BatchRpCta job = J[blockIdx.x];
+  BatchEns* ens = job.e >= 0 ? E + job.e : nullptr;
+  const int n = ens ? (int)ens->n : 0;
+  const int R = job.R, NP = job.NP, JP = job.JP;
+  const int blen = NP * 6 * JP;  // floats per buffer
+  float* buf = reinterpret_cast<float*>(sm);
+  float* wz = buf + 2 * blen;     // charges, [NP][JP]
+  float* ps = wz + NP * JP;
+  float* pc = ps + NP * 3 * R;
+  // read before the first barrier; the group's first CTA rewrites them after the last
+  const int steps = ens ? (int)min((long long)K, ens->remaining) : 0;
+  const long long n0 = ens ? *ens->step : 0;
+  cg::cluster_group cluster = cg::this_cluster();
+
+  // stage the positions x_{n0+1} into buffer 0, the padding into both buffers and the
+  // charges (padding entries sit at 1e30 m: r^2 overflows, rsqrt gives 0, the term is 0)
+  if (steps > 0) {
+    const int b = (int)((n0 + 1) & 1);
+    const float4* __restrict__ gh = ens->hi[b];
+    const float4* __restrict__ gl = ens->lo[b];
+    for (int e = tid; e < NP * JP; e += kBRThreads) {
+      const int p = e / JP, q = e - p * JP;
+      float4 h = make_float4(1e30f, 1e30f, 1e30f, 0.f), l = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (e < n) {
+        h = gh[e];
+        l = gl[e];
+      }
+      float* d = buf + p * 6 * JP + q;
+      d[0] = h.x, d[JP] = h.y, d[2 * JP] = h.z;
+      d[3 * JP] = l.x, d[4 * JP] = l.y, d[5 * JP] = l.z;
+      wz[e] = h.w;
+      float* d1 = d + blen;
+      if (e >= n) {
+        d1[0] = d1[JP] = d1[2 * JP] = 1e30f;
+        d1[3 * JP] = d1[4 * JP] = d1[5 * JP] = 0.f;
+      }
+    }
+  }
+  // the owned ion and its FP64 state: drift and half kick toward the next force
+  // evaluation, carried from step to step
+  const int r0 = job.r * R;
+  const int Rg = steps > 0 ? max(0, min(R, n - r0)) : 0;
+  const bool own = tid < Rg;
+  const int ie = r0 + tid;
+  const int eo = own ? (ie / JP) * 6 * JP + (ie % JP) : 0;  // ion ie's entry in a buffer
+  int spi = 0;
+  double xf[3] = {0.0, 0.0, 0.0}, vd[3] = {0.0, 0.0, 0.0};
+  if (own) {
+    spi = ens->sp[ie];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      vd[c] = half_kick(ens->v[c * n + ie], ens->a[c * n + ie], ens->trap.hdt);
+      xf[c] = drift(ens->x[c * n + ie], vd[c], ens->trap.dt);
+    }
+  }
+  bool finite = true;
+  cluster.sync();  // every copy staged before the first remote write
+
+  int cur = 0;
+  for (int k = 0; k < K; ++k) {
+    const bool active = k < steps;
+    if (active && tid < ens->nspecies) {  // this step's spring constants per species
+      const TrapDev& tp = ens->trap;
+      const double cosv = (tp.flags & (IONTRAP_RF_OFF | IONTRAP_TRAP_OFF | IONTRAP_PSEUDO))
+                              ? 0.0
+                              : cos(tp.Omega * ((double)(n0 + k + 1) * tp.dt));
+      trap_springs(tp, ens->spc[tid], cosv, s_springs[tid]);
+    }
+    __syncthreads();
+    // the force-independent part of the acceleration, ahead of the pair work
+    double ext[3];
+    if (own && active) accel_ext<false>(ens->trap, ens->spc[spi], s_springs[spi], xf, vd, n0 + k + 1, ie, ext);
+    if (active) {
+      const float* sb = buf + cur * blen;
+      const bool unitw = ens->unitw != 0;
+      for (int m = tid; m < R * NP; m += kBRThreads) {
+        const int p = m / R, s = m - p * R;
+        const int i = r0 + s;
+        if (i >= n) continue;
+        const float* si = sb + (i / JP) * 6 * JP + (i % JP);
+        const float2 nh[3] = {make_float2(-si[0], -si[0]), make_float2(-si[JP], -si[JP]),
+                              make_float2(-si[2 * JP], -si[2 * JP])};
+        const float2 nl[3] = {make_float2(-si[3 * JP], -si[3 * JP]), make_float2(-si[4 * JP], -si[4 * JP]),
+                              make_float2(-si[5 * JP], -si[5 * JP])};
+        const float* sj = sb + p * 6 * JP;
+        const float* sw = wz + p * JP;
+        float ks[3] = {0.f, 0.f, 0.f}, kcp[3] = {0.f, 0.f, 0.f};
+        for (int c0 = 0; c0 < JP; c0 += kSeg) {
+          const int qn = min(kSeg, JP - c0);
+          float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+          // the self pair can only sit in a chunk that overlaps the CTA's own ions; the
+          // variant is chosen per warp (its lanes may hold different items)
+          const int jc = p * JP + c0;
+          const bool diag = __any_sync(__activemask(), (jc < r0 + Rg) && (r0 < jc + qn));
+          if (unitw) {
+            if (diag)
+              rp_chunk<true, true>(sj + c0, sw + c0, JP, qn, jc, i, nh, nl, acc);
+            else
+              rp_chunk<false, true>(sj + c0, sw + c0, JP, qn, jc, i, nh, nl, acc);
+          } else {
+            if (diag)
+              rp_chunk<true, false>(sj + c0, sw + c0, JP, qn, jc, i, nh, nl, acc);
+            else
+              rp_chunk<false, false>(sj + c0, sw + c0, JP, qn, jc, i, nh, nl, acc);
+          }
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            const float a = acc[d].x + acc[d].y;
+            const float y = a - kcp[d];
+            const float t = ks[d] + y;
+            kcp[d] = (t - ks[d]) - y;
+            ks[d] = t;
+          }
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          ps[(p * 3 + d) * R + s] = ks[d];
+          pc[(p * 3 + d) * R + s] = kcp[d];
+        }
+      }
+    }
+    __syncthreads();
+    if (own && active) {  // merge in part order (Kahan), integrate, publish the next positions
+      double S[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        float su = 0.f, cu = 0.f;
+        for (int p = 0; p < NP; ++p) kahan_merge(su, cu, ps[(p * 3 + d) * R + tid], pc[(p * 3 + d) * R + tid]);
+        S[d] = (double)cu - (double)su;  // the accumulators hold the negated sum
+      }
+      const SpeciesDev& sd = ens->spc[spi];
+      const TrapDev& tp = ens->trap;
+      double acc[3];
+      accel_total(sd, S, ext, acc);
+      const bool last = k == steps - 1;
+      float h[3], l[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double vn = half_kick(vd[c], acc[c], tp.hdt);
+        const double vh = half_kick(vn, acc[c], tp.hdt);
+        const double xn = drift(xf[c], vh, tp.dt);
+        finite = finite && isfinite(acc[c]) && isfinite(vn) && isfinite(xn);
+        if (last) {
+          ens->x[c * n + ie] = xf[c];
+          ens->v[c * n + ie] = vn;
+          ens->a[c * n + ie] = acc[c];
+        }
+        xf[c] = xn;
+        vd[c] = vh;
+        h[c] = __double2float_rn(xn);
+        l[c] = __double2float_rn(xn - (double)h[c]);
+      }
+      float* dl = buf + (cur ^ 1) * blen + eo;
+      for (int rr = 0; rr < job.C; ++rr) {
+        float* d = cluster.map_shared_rank(dl, (unsigned)(job.rank0 + rr));
+        d[0] = h[0], d[JP] = h[1], d[2 * JP] = h[2];
+        d[3 * JP] = l[0], d[4 * JP] = l[1], d[5 * JP] = l[2];
+      }
+      if (last) {  // the pair stream of the final state, x_{n+1}
+        const int bn = (int)((n0 + steps + 1) & 1);
+        ens->hi[bn][ie] = make_float4(h[0], h[1], h[2], sd.w);
+        ens->lo[bn][ie] = make_float4(l[0], l[1], l[2], 0.f);
+      }
+    }
+    cluster.sync();  // every CTA's reads of this step's buffer and writes of the next are done
+    cur ^= 1;
+  }
+  if (own && !finite) atomicOr(ens->err, ERR_NONFINITE);
+  if (steps > 0 && job.r == 0 && tid == 0) {  // one thread per ensemble
+    *ens->step = n0 + steps;
+    ens->remaining -= steps;
+  }
+}
+
+// ------------------------------------------------------------------ host side
+struct BatchPlan {
+  std::vector<BatchRpCta> groups;   // part-major groups of 2, 4 or 8 CTAs (clusters of 8)
+  std::vector<BatchCta> single;     // CTAs holding whole ensembles of <= 256 ions (no cluster)
+  size_t smem_groups = 0, smem_single = 0;
+};
+
+// Part count of a part-major CTA with R ions of an n-ion ensemble: the threads take the
+// R x NP items in ceil(R NP / threads) rounds of JP entries each, so NP minimises
+// rounds x (JP + the per-item overhead in pair equivalents), within the shared memory
+// that lets two CTAs share an SM if any shape fits there, else within the CTA limit.
+constexpr int kBRItemCost = 8;
+constexpr size_t kBRSmemTwo = 112 * 1024;  // two CTAs per SM (228 KB less 1 KB each reserved, static arrays)
+constexpr size_t kBRSmemOne = 226 * 1024;  // 227 KB less the static arrays
+static void brp_shape(int n, int C, BatchRpCta* t) {
+  const int R = (n + C - 1) / C;
+  for (size_t lim : {kBRSmemTwo, kBRSmemOne}) {
+    long long best = -1;
+    for (int np = 1; np <= kBRMaxParts; ++np) {
+      long long q4 = ((n + np - 1) / np + 3) / 4;
+      if (R % 32 != 0 && !(q4 & 1)) ++q4;
+      const int jp = (int)(4 * q4);
+      if (brp_smem_bytes(R, np, jp) > lim) continue;
+      const long long rounds = ((long long)R * np + kBRThreads - 1) / kBRThreads;
+      const long long cost = rounds * (jp + kBRItemCost);
+      if (best < 0 || cost < best) {
+        best = cost;
+        t->NP = np;
+        t->JP = jp;
+      }
+    }
+    if (best >= 0) break;
+  }
+  t->R = R;
+  t->C = C;
+}
+
+// Pack ensembles (sizes n[e]) into CTAs.  Above 256 ions: part-major groups of 2 CTAs up
+// to 512 ions, 4 up to 1024, 8 above, placed buddy-aligned in clusters of 8 (largest
+// first, similar sizes together).  The rest one per CTA (64 < N <= 256) or four per CTA
+// (N <= 64), heaviest first, in a grid without clusters.
 static BatchPlan plan_batch(const std::vector<long long>& n) {
   BatchPlan plan;
   struct Job {
@@ -280,9 +509,7 @@ static BatchPlan plan_batch(const std::vector<long long>& n) {
     } else if (n[e] <= kBCtaIons) {
       mid.push_back({e, 1, n[e] * n[e]});
     } else {
-      int c = 2;
-      while ((long long)c * kBCtaIons < n[e]) c *= 2;
-      big.push_back({e, c, n[e] * n[e]});
+      big.push_back({e, n[e] <= 512 ? 2 : (n[e] <= 1024 ? 4 : 8), n[e] * n[e]});
     }
   }
   auto heavier = [](const Job& a, const Job& b) { return a.ctas != b.ctas ? a.ctas > b.ctas : a.work > b.work; };
@@ -293,44 +520,53 @@ static BatchPlan plan_batch(const std::vector<long long>& n) {
     BatchCta c{};
     c.nens = 0;
     for (int w = 0; w < kBWarps; ++w) c.warp_le[w] = -1;
-    c.rank0 = 0;
-    c.nranks = 1;
     return c;
   };
-  auto whole = [&](const Job& j, int r, int r0, int c) {
+  auto whole = [&](const Job& j) {
     BatchCta t = blank();
     t.nens = 1;
     t.ens[0] = j.e;
     t.soff[0] = 0;
     for (int w = 0; w < kBWarps; ++w) {
-      const long long i0 = (long long)r * kBCtaIons + (long long)w * kBWarpIons;
+      const long long i0 = (long long)w * kBWarpIons;
       if (i0 < n[j.e]) {
         t.warp_le[w] = 0;
         t.warp_i0[w] = (int)i0;
       }
     }
-    t.rank0 = r0;
-    t.nranks = c;
     return t;
   };
-  // clustered grid: buddy placement of power-of-two groups inside clusters of 8
+  // part-major groups: buddy placement of the groups of 2, 4 and 8 inside clusters of 8
   int used = 0;
   for (const Job& j : big) {
+    BatchRpCta t{};
+    t.e = j.e;
+    brp_shape((int)n[j.e], j.ctas, &t);
+    const size_t smem = brp_smem_bytes(t.R, t.NP, t.JP);
     while (used % j.ctas) {
-      plan.clustered.push_back(blank());
+      BatchRpCta idle{};
+      idle.e = -1;
+      plan.groups.push_back(idle);
       ++used;
     }
-    if (used == kBCluster) used = 0;
-    const int r0 = used;
-    for (int r = 0; r < j.ctas; ++r) plan.clustered.push_back(whole(j, r, r0, j.ctas));
+    if (used == kBRCluster) used = 0;
+    t.rank0 = used;
+    for (int r = 0; r < j.ctas; ++r) {
+      t.r = r;
+      plan.groups.push_back(t);
+    }
     used += j.ctas;
-    if (used == kBCluster) used = 0;
-    plan.smem_clustered = std::max(plan.smem_clustered, (size_t)n[j.e] * 2 * sizeof(float4));
+    if (used == kBRCluster) used = 0;
+    plan.smem_groups = std::max(plan.smem_groups, smem);
   }
-  while (plan.clustered.size() % kBCluster) plan.clustered.push_back(blank());
+  while (plan.groups.size() % kBRCluster) {
+    BatchRpCta idle{};
+    idle.e = -1;
+    plan.groups.push_back(idle);
+  }
   // single grid
   for (const Job& j : mid) {
-    plan.single.push_back(whole(j, 0, 0, 1));
+    plan.single.push_back(whole(j));
     plan.smem_single = std::max(plan.smem_single, (size_t)n[j.e] * 2 * sizeof(float4));
   }
   for (size_t k = 0; k < small.size(); k += kBWarps) {
@@ -357,7 +593,9 @@ struct BatchBuffers {
   size_t ens_cap = 0;
   BatchCta* d_cta = nullptr;
   size_t cta_cap = 0;
-  cudaStream_t side = nullptr;  // second stream: the single-CTA grid runs beside the clustered one
+  BatchRpCta* d_rp = nullptr;
+  size_t rp_cap = 0;
+  cudaStream_t side = nullptr;  // second stream: the small-ensemble grid runs beside the clustered one
   cudaEvent_t fork = nullptr, join = nullptr;
   cudaEvent_t done = nullptr;   // recorded after the previous launches, which read the tables
   bool pending = false;
@@ -404,45 +642,49 @@ cudaError_t launch_batched(const std::vector<BatchEns>& ens_in, const std::vecto
     if (err != cudaSuccess) return err;
     g_bb.pending = false;
   }
-  const size_t nc = plan.clustered.size(), ns = plan.single.size();
+  const size_t ng = plan.groups.size(), ns = plan.single.size();
   err = grow((void**)&g_bb.d_ens, &g_bb.ens_cap, ens_in.size(), sizeof(BatchEns));
-  if (err == cudaSuccess) err = grow((void**)&g_bb.d_cta, &g_bb.cta_cap, nc + ns, sizeof(BatchCta));
+  if (err == cudaSuccess) err = grow((void**)&g_bb.d_cta, &g_bb.cta_cap, ns, sizeof(BatchCta));
+  if (err == cudaSuccess) err = grow((void**)&g_bb.d_rp, &g_bb.rp_cap, ng, sizeof(BatchRpCta));
   if (err != cudaSuccess) return err;
   std::vector<BatchEns> ens = ens_in;
   for (size_t e = 0; e < ens.size(); ++e) ens[e].remaining = steps[e];
-  std::vector<BatchCta> ctas = plan.clustered;
-  ctas.insert(ctas.end(), plan.single.begin(), plan.single.end());
   // synchronous copies: the host vectors die with this call
   err = cudaStreamSynchronize(stream);
   if (err == cudaSuccess)
     err = cudaMemcpy(g_bb.d_ens, ens.data(), ens.size() * sizeof(BatchEns), cudaMemcpyHostToDevice);
-  if (err == cudaSuccess) err = cudaMemcpy(g_bb.d_cta, ctas.data(), ctas.size() * sizeof(BatchCta), cudaMemcpyHostToDevice);
+  if (err == cudaSuccess && ns)
+    err = cudaMemcpy(g_bb.d_cta, plan.single.data(), ns * sizeof(BatchCta), cudaMemcpyHostToDevice);
+  if (err == cudaSuccess && ng)
+    err = cudaMemcpy(g_bb.d_rp, plan.groups.data(), ng * sizeof(BatchRpCta), cudaMemcpyHostToDevice);
   if (err != cudaSuccess) return err;
-  const size_t smem = std::max<size_t>(std::max(plan.smem_clustered, plan.smem_single), 16);
-  err = cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (ns) err = cudaFuncSetAttribute(k_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)std::max<size_t>(plan.smem_single, 16));
+  if (err == cudaSuccess && ng)
+    err = cudaFuncSetAttribute(k_batched_rp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem_groups);
   if (err != cudaSuccess) return err;
-  // fork: the single-CTA grid on the side stream, the clustered grid on `stream`
+  // fork: the small-ensemble grid on the side stream, the clustered grid on `stream`
   err = cudaEventRecord(g_bb.fork, stream);
   if (err == cudaSuccess) err = cudaStreamWaitEvent(g_bb.side, g_bb.fork, 0);
   for (long long done = 0; done < max_steps && err == cudaSuccess; done += K) {
-    if (nc) {
+    if (ng) {
       cudaLaunchConfig_t cfg{};
-      cfg.gridDim = dim3((unsigned)nc);
-      cfg.blockDim = dim3(kBThreads);
-      cfg.dynamicSmemBytes = std::max<size_t>(plan.smem_clustered, 16);
+      cfg.gridDim = dim3((unsigned)ng);
+      cfg.blockDim = dim3(kBRThreads);
+      cfg.dynamicSmemBytes = plan.smem_groups;
       cfg.stream = stream;
       cudaLaunchAttribute attr[1];
       attr[0].id = cudaLaunchAttributeClusterDimension;
-      attr[0].val.clusterDim.x = kBCluster;
+      attr[0].val.clusterDim.x = kBRCluster;
       attr[0].val.clusterDim.y = 1;
       attr[0].val.clusterDim.z = 1;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
-      err = cudaLaunchKernelEx(&cfg, k_batched, g_bb.d_ens, (const BatchCta*)g_bb.d_cta, K, 1);
+      err = cudaLaunchKernelEx(&cfg, k_batched_rp, g_bb.d_ens, (const BatchRpCta*)g_bb.d_rp, K);
     }
     if (ns && err == cudaSuccess) {
       k_batched<<<(unsigned)ns, kBThreads, std::max<size_t>(plan.smem_single, 16), g_bb.side>>>(
-          g_bb.d_ens, g_bb.d_cta + nc, K, 0);
+          g_bb.d_ens, g_bb.d_cta, K);
       err = cudaGetLastError();
     }
   }

@@ -406,53 +406,6 @@ struct RpArgs {
 // Bulk copies (and mbarriers) per step: the parts are fetched in up to this many runs.
 constexpr int kRpBatches = 8;
 
-// Pair terms of one thread's ion against two j (packed); DIAG: the self pair is excluded
-// by its index (only chunks that may hold it take this variant).
-template <bool DIAG, bool UNITW>
-__device__ __forceinline__ void rp_pair2(float2 hx, float2 hy, float2 hz, float2 lx, float2 ly, float2 lz, float2 w,
-                                         int j, int i, const float2 (&nh)[3], const float2 (&nl)[3],
-                                         float2 (&acc)[3]) {
-  const float2 dx = __fadd2_rn(__fadd2_rn(hx, nh[0]), __fadd2_rn(lx, nl[0]));
-  const float2 dy = __fadd2_rn(__fadd2_rn(hy, nh[1]), __fadd2_rn(ly, nl[1]));
-  const float2 dz = __fadd2_rn(__fadd2_rn(hz, nh[2]), __fadd2_rn(lz, nl[2]));
-  const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
-  float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
-  if (DIAG) {
-    ri.x = (j == i) ? 0.0f : ri.x;
-    ri.y = (j + 1 == i) ? 0.0f : ri.y;
-  }
-  const float2 ri2 = __fmul2_rn(ri, ri);
-  const float2 s = UNITW ? __fmul2_rn(ri, ri2) : __fmul2_rn(__fmul2_rn(w, ri), ri2);
-  acc[0] = __ffma2_rn(s, dx, acc[0]);
-  acc[1] = __ffma2_rn(s, dy, acc[1]);
-  acc[2] = __ffma2_rn(s, dz, acc[2]);
-}
-
-// qn (a multiple of 4) staged j of one part (stride JP between x_hi, y_hi, z_hi, x_lo,
-// y_lo, z_lo, z), four j per iteration from 16-byte shared loads.  Padding entries sit at
-// 1e30 m: r^2 overflows to infinity, rsqrt gives 0, the term is exactly 0.
-template <bool DIAG, bool UNITW>
-__device__ __forceinline__ void rp_chunk(const float* __restrict__ sj, int JP, int qn, int jbase, int i,
-                                         const float2 (&nh)[3], const float2 (&nl)[3], float2 (&acc)[3]) {
-#pragma unroll 2
-  for (int q = 0; q < qn; q += 4) {
-    const float4 hx = *reinterpret_cast<const float4*>(sj + q);
-    const float4 hy = *reinterpret_cast<const float4*>(sj + JP + q);
-    const float4 hz = *reinterpret_cast<const float4*>(sj + 2 * JP + q);
-    const float4 lx = *reinterpret_cast<const float4*>(sj + 3 * JP + q);
-    const float4 ly = *reinterpret_cast<const float4*>(sj + 4 * JP + q);
-    const float4 lz = *reinterpret_cast<const float4*>(sj + 5 * JP + q);
-    float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (!UNITW) w = *reinterpret_cast<const float4*>(sj + 6 * JP + q);
-    rp_pair2<DIAG, UNITW>(make_float2(hx.x, hx.y), make_float2(hy.x, hy.y), make_float2(hz.x, hz.y),
-                    make_float2(lx.x, lx.y), make_float2(ly.x, ly.y), make_float2(lz.x, lz.y), make_float2(w.x, w.y),
-                    jbase + q, i, nh, nl, acc);
-    rp_pair2<DIAG, UNITW>(make_float2(hx.z, hx.w), make_float2(hy.z, hy.w), make_float2(hz.z, hz.w),
-                    make_float2(lx.z, lx.w), make_float2(ly.z, ly.w), make_float2(lz.z, lz.w), make_float2(w.z, w.w),
-                    jbase + q + 2, i, nh, nl, acc);
-  }
-}
-
 template <int W>
 __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant__ StepArgs A, const RpArgs P) {
   // dynamic shared memory: per part 7 x JP floats (SoA j data); partial sums and
@@ -623,14 +576,14 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
         const bool diag = __any_sync(__activemask(), (jc < r0 + Rg) && (r0 < jc + qn));
         if (A.unitw) {
           if (diag)
-            rp_chunk<true, true>(sj + c0, JP, qn, jc, ii, nh, nl, acc);
+            rp_chunk<true, true>(sj + c0, sj + 6 * JP + c0, JP, qn, jc, ii, nh, nl, acc);
           else
-            rp_chunk<false, true>(sj + c0, JP, qn, jc, ii, nh, nl, acc);
+            rp_chunk<false, true>(sj + c0, sj + 6 * JP + c0, JP, qn, jc, ii, nh, nl, acc);
         } else {
           if (diag)
-            rp_chunk<true, false>(sj + c0, JP, qn, jc, ii, nh, nl, acc);
+            rp_chunk<true, false>(sj + c0, sj + 6 * JP + c0, JP, qn, jc, ii, nh, nl, acc);
           else
-            rp_chunk<false, false>(sj + c0, JP, qn, jc, ii, nh, nl, acc);
+            rp_chunk<false, false>(sj + c0, sj + 6 * JP + c0, JP, qn, jc, ii, nh, nl, acc);
         }
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
