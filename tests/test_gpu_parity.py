@@ -377,10 +377,11 @@ def _run_many(it, ws, steps):
             s.close()
 
 
-@pytest.mark.parametrize("n", [1, 2, 16, 63, 64, 65, 200, 256, 257, 700, 1024, 1500, 2048])
+@pytest.mark.parametrize("n", [1, 2, 16, 63, 64, 65, 200, 256, 257, 513, 700, 1024, 1025, 1100, 1500, 2048])
 def test_batched_trajectory_matches_oracle(it, n):
-    """The batched resident kernel (every packing class: one warp, one CTA, 2/4/8 CTAs of
-    a cluster) against the oracle over 100 steps."""
+    """The batched resident kernels (every packing class: one warp, one CTA, part-major
+    groups of 2/4/8 CTAs of a cluster, with one to eleven j-parts and one to six rounds of
+    (ion, part) items, ragged last CTAs) against the oracle over 100 steps."""
     w = _cloud(n, 300 + n)
     q, m, p = _oracle_side(w)
     # the 1500-ion cloud has a close encounter between steps 80 and 100 that takes every
