@@ -236,6 +236,69 @@ def test_long_run_temperature_equipartition(it):
     assert np.all(np.abs(t_gpu / t_or - 1) < 0.03), (t_gpu, t_or)
 
 
+def _floquet_trace(trap, sgn):
+    """Trace of the one-RF-period matrix of the discrete kick-drift-kick map of one ion
+    in the Mathieu trap (radial axis: sgn = -1 for x, +1 for y)."""
+    aeff = trap.a - 2 * trap.omega_z ** 2 / trap.Omega ** 2
+    k = lambda t: trap.Omega ** 2 / 4 * (aeff + sgn * 2 * trap.q * math.cos(trap.Omega * t))
+    M, dt = np.eye(2), trap.dt
+    for st in range(20):
+        k0, k1 = k(st * dt), k((st + 1) * dt)
+        M = np.array([[1 - 0.5 * dt * dt * k0, dt],
+                      [-0.5 * dt * (k0 + k1) + 0.25 * dt ** 3 * k0 * k1, 1 - 0.5 * dt * dt * k1]]) @ M
+    return np.trace(M)
+
+
+def test_long_run_secular_frequency_of_the_centre_of_mass(it):
+    """Long runs compared by secular frequency: 256 interacting Ca+ ions over 300 RF
+    periods (6000 steps), far past the chaotic horizon of single trajectories.  The
+    internal Coulomb forces cancel in the centre-of-mass motion of one species, so the
+    centre of mass, sampled once per RF period, obeys s_{k+1} + s_{k-1} = tau s_k with
+    the one-ion Floquet trace tau; the secular frequency arccos(tau / 2) / T_RF fitted
+    from the GPU run, from the oracle run and from the discrete map agree within 0.1%."""
+    n, periods = 256, 300
+    trap = iongen.Trap(Omega=iongen.OMEGA_RF, a=-0.001, q=0.3, omega_z=2 * math.pi * 0.2e6, gamma=0.0,
+                       T_bath=0.0, dt=iongen.rf_period_dt(iongen.OMEGA_RF))
+    x0 = iongen.gaussian_positions(n, 20e-6, seed=12) + np.array([[6e-6], [-4e-6], [8e-6]])
+    sp = np.zeros(n, np.uint8)
+    q, m, qm0 = oracle.ion_arrays([iongen.CA40], sp)
+    p = oracle.params(trap, qm0)
+    T_rf = 20 * trap.dt
+
+    def omega_s(com):
+        c = np.asarray(com)
+        w = []
+        for ax in range(3):
+            s = c[:, ax]
+            tau = np.dot(s[2:] + s[:-2], s[1:-1]) / np.dot(s[1:-1], s[1:-1])
+            w.append(math.acos(tau / 2) / T_rf)
+        return np.array(w)
+
+    x, v, a = oracle.run(x0, np.zeros((3, n)), q, m, p, 0)
+    com_or, step = [x.mean(axis=1)], 0
+    for _ in range(periods):
+        x, v, a = oracle.run(x, v, q, m, p, 20, step0=step, a0=a)
+        step += 20
+        com_or.append(x.mean(axis=1))
+    w_or = omega_s(com_or)
+    # radial: the Floquet trace of the one-period map; axial: a constant-spring Verlet map,
+    # cos(w dt) = 1 - (w_z dt)^2 / 2 per step
+    theory = np.array([math.acos(_floquet_trace(trap, -1.0) / 2) / T_rf,
+                       math.acos(_floquet_trace(trap, 1.0) / 2) / T_rf,
+                       math.acos(1 - (trap.dt * trap.omega_z) ** 2 / 2) / trap.dt])
+    assert np.all(np.abs(w_or / theory - 1) < 1e-3), (w_or, theory)
+    for prec in (it.IONTRAP_PREC_FP32, it.IONTRAP_PREC_FP64):
+        com = []
+        with _ion_run(it, [iongen.CA40], sp, x0, np.zeros((3, n)), trap, prec) as sim:
+            com.append(sim.state()[0].mean(axis=1))
+            for _ in range(periods):
+                sim.step(20)
+                com.append(sim.state()[0].mean(axis=1))
+        w_gpu = omega_s(com)
+        assert np.all(np.abs(w_gpu / w_or - 1) < 1e-3), (prec, w_gpu, w_or)
+        assert np.all(np.abs(w_gpu / theory - 1) < 1e-3), (prec, w_gpu, theory)
+
+
 # ------------------------------------------------------------------ closed forms via the C ABI
 
 def _ion_run(it, species, sp, x0, v0, trap, prec, flags=0):

@@ -11,7 +11,8 @@ term, a wrong sign or index, a transposed operand, a wrong constant) fails one o
                          difference gradient of the pair energy, Newton's third law,
                          permutation invariance
   trap (Eq. 1, Eq. 3)    the field written in voltage form V0, U0, R0, Z0, kappa
-  Verlet + trap          exact stroboscopic Floquet recurrence x_{k+1}+x_{k-1}=tr(M) x_k,
+  Verlet + trap          exact stroboscopic Floquet recurrence x_{k+1}+x_{k-1}=tr(M) x_k
+                         (one ion, and the centre of mass of an interacting cloud),
                          the axial Verlet recurrence, the paper's largest-Fourier-peak
                          secular frequency, the continuous Mathieu exponent (RK4)
   equilibria             two- and three-ion axial spacings (closed forms), James' fit
@@ -230,6 +231,36 @@ def test_stroboscopic_floquet_recurrence_is_exact():
         assert abs(tau) < 2
         res = s[2:, c] + s[:-2, c] - tau * s[1:-1, c]
         assert np.abs(res).max() < 1e-9 * np.abs(s[:, c]).max()
+
+
+def test_centre_of_mass_of_a_coulomb_cloud_follows_the_one_ion_map():
+    """Internal Coulomb forces cancel in the centre-of-mass motion of one species, so the
+    centre of mass of 64 interacting ions, sampled once per RF period, obeys the one-ion
+    recurrence s_{k+1} + s_{k-1} = tr(M) s_k radially and the axial Verlet recurrence of
+    a 20-step period: a Coulomb sum that breaks Newton's third law, or a trap term that
+    depends on anything but the ion's own position, fails it."""
+    tr = _trap(a=-0.001)
+    aeff = tr.a - 2 * tr.omega_z ** 2 / OMEGA_RF ** 2
+    n = 64
+    rng = np.random.default_rng(21)
+    x0 = rng.normal(0.0, 15e-6, (3, n)) + np.array([[6e-6], [-4e-6], [8e-6]])
+    q, m, qm0 = _ions([CA40], [0] * n)
+    p = oracle.params(tr, qm0)
+    x, v, a = oracle.run(x0, np.zeros((3, n)), q, m, p, 0)
+    com, s = [x.mean(axis=1)], 0
+    for _ in range(100):
+        x, v, a = oracle.run(x, v, q, m, p, 20, step0=s, a0=a)
+        s += 20
+        com.append(x.mean(axis=1))
+    com = np.array(com)
+    theta = math.acos(1 - (DT * tr.omega_z) ** 2 / 2)
+    for c, tau in ((0, None), (1, None), (2, 2 * math.cos(20 * theta))):
+        if tau is None:
+            sgn = -1.0 if c == 0 else 1.0
+            k = lambda t, sgn=sgn: OMEGA_RF ** 2 / 4 * (aeff + sgn * 2 * tr.q * math.cos(OMEGA_RF * t))
+            tau = _kdk_trace(k, DT, 20)
+        res = com[2:, c] + com[:-2, c] - tau * com[1:-1, c]
+        assert np.abs(res).max() < 1e-9 * np.abs(com[:, c]).max()
 
 
 def test_axial_verlet_recurrence():
