@@ -509,7 +509,7 @@ def batched_measurement(it, torch, stream, steps=2000):
     return {"ensembles": len(ws), "ions": ions, "timesteps": steps, "ms": ms,
             "force_rel_rms_vs_oracle_max": max(errs), "error_sample": "8 ensembles, 64 ions each, after the run",
             "ion_steps_per_s": ions * steps / (ms / 1e3), "pair_interactions_per_s": pairs * steps / (ms / 1e3),
-            "launches": (steps + 99) // 100}
+            "launches": 2 * ((steps + 999) // 1000)}
 
 
 def serve_measurement(it, torch, count, step_scale, budget_bytes, fp64_subset):

@@ -246,7 +246,7 @@ int iontrap_restore(iontrap_t *h, const double *x, const double *v, const double
 
 /* Enqueue n_steps[k] steps on each of count handles (the batched form of evolve(N)).
  * FP32-form handles with n <= 2048 on the device of the first such handle are advanced
- * together, 100 steps per launch, with every ensemble resident in shared memory
+ * together, up to 1000 steps per launch, with every ensemble resident in shared memory
  * (positions) and registers (FP64 state): ensembles above 256 ions by groups of 2, 4 or
  * 8 CTAs of a cluster (part-major, positions exchanged through distributed shared
  * memory), smaller ones by a CTA or a warp each, the two grids side by side; the others

@@ -1276,7 +1276,7 @@ int iontrap_step_many(iontrap_t* const* hs, const int64_t* n_steps, int count) {
     std::memcpy(E.spc, h->args.spc, sizeof(E.spc));
     steps[b] = n_steps[batch[b]];
   }
-  if (e == cudaSuccess) e = launch_batched(ens, steps, kGraphSteps, st0);
+  if (e == cudaSuccess) e = launch_batched(ens, steps, (int)kGpMaxSteps, st0);
   for (size_t b = 0; b < batch.size(); ++b) {
     iontrap* h = hs[batch[b]];
     if (e != cudaSuccess) {
