@@ -388,7 +388,9 @@ int gp_max_ctas(int W, int S, int Lmax, int max_lmax, long long max_k, int sms) 
 // of the staged arrays, so from the second step of a launch on one thread fetches them
 // with bulk TMA copies of kRpBatches runs of consecutive parts, each completing on its own
 // mbarrier, and a part's threads start as soon as their run has landed.  The CTA's own
-// ions come from shared memory, where their owners left them.
+// ions come from shared memory, where their owners left them.  The FP64 state and the
+// float4 pair stream, which only the next launch reads, are written in a launch's last
+// step (a launch stopped by a timeout leaves the state it started from).
 //
 // Summation order depends on (n, R, W) only: per part, j ascending in 128-j chunks summed
 // as even and odd j (the two halves added), chunks Kahan-added; parts Kahan-merged in
@@ -489,6 +491,11 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
     if (tp.laser) svd[oc * rq + oq] = vd;
     return __fma_rn(-sd.gamma, vd, __dmul_rn(-kc, xf));
   };
+  // the charges of the owned ions into both global copies (they never change)
+  if (own && !forces && oc == 0 && P.K > 1) {
+    gsoa[ieo + 6 * JP] = A.spc[spe].w;
+    gsoa[soa_len + ieo + 6 * JP] = A.spc[spe].w;
+  }
   __syncthreads();  // scos
   draw(ns0 + 1);
   double ext = own && !forces ? ext_det(0) : 0.0;
@@ -622,22 +629,22 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
         const double vn = half_kick(vd, acc, tp.hdt);
         const double vh = half_kick(vn, acc, tp.hdt);
         const double xn = drift(xf, vh, tp.dt);
-        A.x[oc * n + ie] = xf;
-        A.v[oc * n + ie] = vn;
-        A.a[oc * n + ie] = acc;
         const float h = __double2float_rn(xn);
         const float l = __double2float_rn(xn - (double)h);
-        reinterpret_cast<float*>(A.hi[rb ^ 1] + ie)[oc] = h;
-        reinterpret_cast<float*>(A.lo[rb ^ 1] + ie)[oc] = l;
-        if (oc == 0) {
-          reinterpret_cast<float*>(A.hi[rb ^ 1] + ie)[3] = sd.w;
-          reinterpret_cast<float*>(A.lo[rb ^ 1] + ie)[3] = 0.0f;
-        }
-        if (t + 1 < P.K) {  // the next step's copies: part-major global, own ions in shared
+        if (t + 1 == P.K) {  // the launch's last step: FP64 state and the pair stream
+          A.x[oc * n + ie] = xf;
+          A.v[oc * n + ie] = vn;
+          A.a[oc * n + ie] = acc;
+          reinterpret_cast<float*>(A.hi[rb ^ 1] + ie)[oc] = h;
+          reinterpret_cast<float*>(A.lo[rb ^ 1] + ie)[oc] = l;
+          if (oc == 0) {
+            reinterpret_cast<float*>(A.hi[rb ^ 1] + ie)[3] = sd.w;
+            reinterpret_cast<float*>(A.lo[rb ^ 1] + ie)[3] = 0.0f;
+          }
+        } else {  // the next step's copies: part-major global, own ions in shared
           float* g = gsoa + (rb ? 0 : soa_len) + ieo;
           g[oc * JP] = h;
           g[(3 + oc) * JP] = l;
-          if (oc == 0) g[6 * JP] = sd.w;
           sself[oc * R + oq] = h;
           sself[(3 + oc) * R + oq] = l;
           asm volatile("fence.proxy.async.global;" ::: "memory");
