@@ -59,6 +59,30 @@ __device__ __noinline__ bool gp_wait(const unsigned* ctr, unsigned target, int* 
   }
 }
 
+
+// Wait of the row-persistent form's poller for the step counter: the counter alone is
+// polled, the timeout flag and the clock every 64 polls.  ACQ: acquire loads (no fence
+// needed after a successful wait).
+template <bool ACQ>
+__device__ __noinline__ bool rp_wait(const unsigned* ctr, unsigned target, int* err) {
+  const unsigned long long t0 = globaltimer_ns();
+  for (unsigned it = 1;; ++it) {
+    unsigned c;
+    if (ACQ)
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(c) : "l"(ctr) : "memory");
+    else
+      c = ld_relaxed_u32(ctr);
+    if (c >= target) return true;
+    if ((it & 63) == 0) {
+      if (*(volatile int*)err & ERR_TIMEOUT) return false;
+      if (globaltimer_ns() - t0 > kWaitLimitNs) {
+        atomicOr(err, ERR_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+
 // Trap spring constant of component c (the c-th value trap_springs gives, same roundings).
 __device__ __forceinline__ double trap_spring_c(const TrapDev& tp, const SpeciesDev& sd, double cosv, int c) {
   if (tp.flags & IONTRAP_TRAP_OFF) return 0.0;
@@ -508,8 +532,7 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
     const int rb = forces ? (int)(ns & 1) : (int)((ns + 1) & 1);
     bool bad = false;
     if (t > 0 && tid == poller) {
-      bad = !gp_wait(ctr_step, G * (unsigned)t, A.err);
-      fence_gpu();
+      bad = !rp_wait<true>(ctr_step, G * (unsigned)t, A.err);
       if (!bad) {
         // the positions the other CTAs wrote (generic stores, ordered by the counter)
         // are read by the copy engine, and this CTA's shared memory last read by threads
@@ -657,10 +680,7 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
     }
     __syncthreads();
     trace_mark(A.trace, tslot + 3);
-    if (tid == poller) {
-      fence_gpu();
-      atomicAdd(ctr_step, 1u);
-    }
+    if (tid == poller) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctr_step) : "memory");
     // the next step's trap and drag and the noise after it, while the other CTAs finish
     if (t + 1 < P.K && !forces) {
       if (own) ext = ext_det(t + 1);
