@@ -38,33 +38,12 @@ __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
   return v;
 }
 
-// Release/acquire fence at GPU scope: orders this thread's (and, after a CTA barrier,
-// the CTA's) earlier accesses before a counter update, or a counter read before later
-// accesses.
-__device__ __forceinline__ void fence_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
-
-// Wait until *ctr >= target (relaxed polling: the caller fences after a successful
-// wait).  Gives up (false) after kWaitLimitNs, setting the timeout flag, or at once when
-// the flag is already set by another CTA.
-__device__ __noinline__ bool gp_wait(const unsigned* ctr, unsigned target, int* err) {
-  if (ld_relaxed_u32(ctr) >= target) return true;
-  const unsigned long long t0 = globaltimer_ns();
-  for (;;) {
-    if (ld_relaxed_u32(ctr) >= target) return true;
-    if (*(volatile int*)err & ERR_TIMEOUT) return false;
-    if (globaltimer_ns() - t0 > kWaitLimitNs) {
-      atomicOr(err, ERR_TIMEOUT);
-      return false;
-    }
-  }
-}
-
-
-// Wait of the row-persistent form's poller for the step counter: the counter alone is
-// polled, the timeout flag and the clock every 64 polls.  ACQ: acquire loads (no fence
-// needed after a successful wait).
+// Wait of a persistent form's poller until *ctr >= target: the counter alone is polled,
+// the timeout flag and the clock every 64 polls.  ACQ: acquire loads (no fence needed
+// after a successful wait).  Gives up (false) after kWaitLimitNs, setting the timeout
+// flag, or when another CTA has set it.
 template <bool ACQ>
-__device__ __noinline__ bool rp_wait(const unsigned* ctr, unsigned target, int* err) {
+__device__ __noinline__ bool poll_wait(const unsigned* ctr, unsigned target, int* err) {
   const unsigned long long t0 = globaltimer_ns();
   for (unsigned it = 1;; ++it) {
     unsigned c;
@@ -81,6 +60,12 @@ __device__ __noinline__ bool rp_wait(const unsigned* ctr, unsigned target, int* 
       }
     }
   }
+}
+
+// A CTA's arrival on a counter: release at GPU scope orders the CTA's earlier writes
+// (after a CTA barrier) before the increment.
+__device__ __forceinline__ void arrive_release(unsigned* ctr) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctr) : "memory");
 }
 
 // Trap spring constant of component c (the c-th value trap_springs gives, same roundings).
@@ -168,8 +153,7 @@ __global__ void __launch_bounds__(32 * W, 16 / W) k_step_f32_gp(const __grid_con
     // positions x_{ns+1} are complete once every CTA has finished step t-1
     bool bad = false;
     if (t > 0 && tid == poller) {
-      bad = !gp_wait(ctr_step, G * (unsigned)t, A.err);
-      fence_gpu();
+      bad = !poll_wait<true>(ctr_step, G * (unsigned)t, A.err);
     }
     if (__syncthreads_or(bad)) break;
 
@@ -244,10 +228,8 @@ __global__ void __launch_bounds__(32 * W, 16 / W) k_step_f32_gp(const __grid_con
     }
     __syncthreads();
     if (tid == poller) {
-      fence_gpu();
-      atomicAdd(ctr_grp, 1u);
-      bad = !gp_wait(ctr_grp, (unsigned)S * (unsigned)(t + 1), A.err);
-      fence_gpu();
+      arrive_release(ctr_grp);
+      bad = !poll_wait<true>(ctr_grp, (unsigned)S * (unsigned)(t + 1), A.err);
     }
     // while the group's CTAs arrive: the owned components' force-independent terms
     // (trap, drag, laser, kick; the operations and order of accel_ext) and the next
@@ -321,15 +303,12 @@ __global__ void __launch_bounds__(32 * W, 16 / W) k_step_f32_gp(const __grid_con
       }
     }
     __syncthreads();
-    if (tid == poller) {
-      fence_gpu();
-      atomicAdd(ctr_step, 1u);
-    }
+    if (tid == poller) arrive_release(ctr_step);
   }
 
   // once every CTA has counted its last step: clear the counters, advance the step index
   if (blockIdx.x == 0 && tid == poller) {
-    gp_wait(ctr_step, G * (unsigned)P.K, A.err);
+    poll_wait<true>(ctr_step, G * (unsigned)P.K, A.err);
     const int groups = (int)(G / (unsigned)S);
     for (int q = 0; q < groups; ++q) P.sync[32 * (1 + q)] = 0u;
     *ctr_step = 0u;
@@ -532,7 +511,7 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
     const int rb = forces ? (int)(ns & 1) : (int)((ns + 1) & 1);
     bool bad = false;
     if (t > 0 && tid == poller) {
-      bad = !rp_wait<true>(ctr_step, G * (unsigned)t, A.err);
+      bad = !poll_wait<true>(ctr_step, G * (unsigned)t, A.err);
       if (!bad) {
         // the positions the other CTAs wrote (generic stores, ordered by the counter)
         // are read by the copy engine, and this CTA's shared memory last read by threads
@@ -680,7 +659,7 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
     }
     __syncthreads();
     trace_mark(A.trace, tslot + 3);
-    if (tid == poller) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctr_step) : "memory");
+    if (tid == poller) arrive_release(ctr_step);
     // the next step's trap and drag and the noise after it, while the other CTAs finish
     if (t + 1 < P.K && !forces) {
       if (own) ext = ext_det(t + 1);
@@ -691,7 +670,7 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
 
   // once every CTA has counted its last step: clear the counter, advance the step index
   if (blockIdx.x == 0 && tid == poller) {
-    gp_wait(ctr_step, G * (unsigned)P.K, A.err);
+    poll_wait<true>(ctr_step, G * (unsigned)P.K, A.err);
     *ctr_step = 0u;
     if (!forces) *A.step = ns0 + P.K;
     __threadfence();
