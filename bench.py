@@ -52,8 +52,8 @@ NOMINAL_SM_MHZ = 2070.0
 PROFILED_TRAFFIC = {
     # one launch per timestep (profiles/step_f32_cw_mix_n4096.md)
     (128, 2, 1, 512, 3): (485376 + 0, "DRAM bytes per timestep launch (ncu, profiles/step_f32_cw_mix_n4096.md)"),
-    # row-persistent form: a 20-timestep launch read 503 808 B and wrote 4 352 B
-    (512, 1, 1, 27, 5): ((503808 + 4352) / 20, "DRAM bytes per timestep, from a 20-timestep launch of the "
+    # row-persistent form: a 20-timestep launch read 504 064 B and wrote 1 792 B
+    (512, 1, 1, 27, 5): ((504064 + 1792) / 20, "DRAM bytes per timestep, from a 20-timestep launch of the "
                                                "row-persistent kernel (ncu, profiles/step_f32_rp_mix_n4096.md)"),
     # grid-persistent form: a 20-timestep launch read 496 896 B and wrote 113 152 B
     (512, 2, 1, 108, 4): ((496896 + 113152) / 20, "DRAM bytes per timestep, from a 20-timestep launch of the "
