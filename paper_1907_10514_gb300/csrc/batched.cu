@@ -666,8 +666,16 @@ cudaError_t launch_batched(const std::vector<BatchEns>& ens_in, const std::vecto
   // fork: the small-ensemble grid on the side stream, the clustered grid on `stream`
   err = cudaEventRecord(g_bb.fork, stream);
   if (err == cudaSuccess) err = cudaStreamWaitEvent(g_bb.side, g_bb.fork, 0);
+  // each grid loops over no more steps per launch than its longest ensemble still needs
+  long long max_g = 0, max_s = 0;
+  for (const BatchRpCta& t : plan.groups)
+    if (t.e >= 0) max_g = std::max(max_g, steps[t.e]);
+  for (const BatchCta& t : plan.single)
+    for (int w = 0; w < t.nens; ++w) max_s = std::max(max_s, steps[t.ens[w]]);
   for (long long done = 0; done < max_steps && err == cudaSuccess; done += K) {
-    if (ng) {
+    const int Kg = (int)std::max<long long>(0, std::min<long long>(K, max_g - done));
+    const int Ks = (int)std::max<long long>(0, std::min<long long>(K, max_s - done));
+    if (ng && Kg > 0) {
       cudaLaunchConfig_t cfg{};
       cfg.gridDim = dim3((unsigned)ng);
       cfg.blockDim = dim3(kBRThreads);
@@ -680,11 +688,11 @@ cudaError_t launch_batched(const std::vector<BatchEns>& ens_in, const std::vecto
       attr[0].val.clusterDim.z = 1;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
-      err = cudaLaunchKernelEx(&cfg, k_batched_rp, g_bb.d_ens, (const BatchRpCta*)g_bb.d_rp, K);
+      err = cudaLaunchKernelEx(&cfg, k_batched_rp, g_bb.d_ens, (const BatchRpCta*)g_bb.d_rp, Kg);
     }
-    if (ns && err == cudaSuccess) {
+    if (ns && Ks > 0 && err == cudaSuccess) {
       k_batched<<<(unsigned)ns, kBThreads, std::max<size_t>(plan.smem_single, 16), g_bb.side>>>(
-          g_bb.d_ens, g_bb.d_cta, K);
+          g_bb.d_ens, g_bb.d_cta, Ks);
       err = cudaGetLastError();
     }
   }
