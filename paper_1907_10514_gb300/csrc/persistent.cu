@@ -408,8 +408,11 @@ struct RpArgs {
                    // warp read from distinct shared-memory banks); entries past n are padding
 };
 
-// Bulk copies (and mbarriers) per step: the parts are fetched in up to this many runs.
+// Bulk copies (and mbarriers) per step: the parts are fetched in runs of about
+// kRpRunBytes, at most kRpBatches of them (measured at N = 1024 .. 4096: 8 runs of 14 KB
+// beat 4 of 29 KB, 4 runs of 15 KB beat 8 of 7.6 KB).
 constexpr int kRpBatches = 8;
+constexpr long long kRpRunBytes = 16 * 1024;
 
 template <int W>
 __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant__ StepArgs A, const RpArgs P) {
@@ -435,7 +438,8 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
   // global part-major copies of the staged arrays, one per pair-stream buffer
   const long long soa_len = (long long)NP * 7 * JP;
   float* gsoa = reinterpret_cast<float*>(A.part);
-  const int nb = min(NP, kRpBatches);
+  const int nb = (int)min((long long)min(NP, kRpBatches),
+                           max(1LL, (28LL * NP * JP + kRpRunBytes - 1) / kRpRunBytes));
   unsigned* ctr_step = P.sync;
   const int poller = 32 * W - 1;
   const TrapDev& tp = A.trap;
