@@ -461,6 +461,8 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
         gsoa[soa_len + (long long)p * 7 * JP + c * JP + q] = val;
       }
     }
+  // every generic writer of data the copy engine reads fences against the async proxy
+  if (blockIdx.x == 0 && P.K > 1) asm volatile("fence.proxy.async.global;" ::: "memory");
 
   // this thread's pair work: ion slot and j-part
   const int part = tid / R, slot = tid - part * R;
@@ -502,6 +504,7 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
   if (own && !forces && oc == 0 && P.K > 1) {
     gsoa[ieo + 6 * JP] = A.spc[spe].w;
     gsoa[soa_len + ieo + 6 * JP] = A.spc[spe].w;
+    asm volatile("fence.proxy.async.global;" ::: "memory");
   }
   __syncthreads();  // scos
   draw(ns0 + 1);
