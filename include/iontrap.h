@@ -417,12 +417,17 @@ void iontrap_server_destroy(iontrap_server_t *s);
  * Asynchronous: the result is ready when the stream reaches it.  Allocates nothing: the
  * pair stream, split partials and counters live in one fixed device array that is part
  * of the library image (2.25 MiB on every GPU that loads the library, held until the
- * process exits).  n > 8192 returns IONTRAP_ETOOLARGE and launches nothing.  The first
- * call on a device looks up that array's device address (cudaGetSymbolAddress) with the
- * device current; make that first call before any stream capture.  All calls on a
- * device share the array and each clears its counters before launching: calls whose
- * work overlaps on the GPU race and must be serialised by the caller.  EINVAL on bad
- * arguments, ECUDA when a launch fails. */
+ * process exits).  n > 8192 returns IONTRAP_ETOOLARGE and launches nothing.  The array's
+ * device address is looked up (cudaGetSymbolAddress, with the device current) on every
+ * call made outside stream capture, so calls after a cudaDeviceReset find the array
+ * where the new context put it; a call made while its stream is being captured reuses
+ * the address of the last uncaptured call on that device, so make one call before any
+ * capture (and again after a reset).  All calls on a device share the array and each
+ * clears its counters before launching: calls whose work overlaps on the GPU race and
+ * must be serialised by the caller.  d_acc is set to NaN before the kernels run; an ion
+ * whose sum did not complete (a bounded device wait expired) is left NaN, which is how
+ * this call reports a device-side failure.  EINVAL on bad arguments, ECUDA when a launch
+ * fails. */
 int iontrap_forces_noalloc(const iontrap_species *species, int n_species, const uint8_t *d_species_of_ion,
                            const double *d_x, int64_t n, double *d_acc, void *cuda_stream);
 

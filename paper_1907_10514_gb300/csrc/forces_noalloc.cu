@@ -54,21 +54,28 @@ constexpr size_t kScratchBytes = kOffPart + kPartBytes;  // 2.25 MiB + 768 B
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 // Device address of g_scratch per device.  In host code the name g_scratch is only a
-// host-side stand-in for the symbol, so the address is resolved once per device, with
-// that device current, by cudaGetSymbolAddress.
+// host-side stand-in for the symbol, so the address is looked up with that device
+// current by cudaGetSymbolAddress.  The lookup is repeated on every call made outside
+// stream capture, because the address belongs to the device's current context: after a
+// cudaDeviceReset (or any other teardown of the primary context) the module is loaded
+// again and the array may sit elsewhere.  A call made while its stream is being captured
+// uses the address the last uncaptured call on that device found.
 std::mutex g_mu;
 constexpr int kMaxDevices = 64;
 unsigned char* g_addr[kMaxDevices] = {};
 
-int scratch_for_device(int dev, unsigned char** out) {
+int scratch_for_device(int dev, cudaStream_t stream, unsigned char** out) {
   if (dev < 0 || dev >= kMaxDevices) return IONTRAP_ECUDA;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess) return IONTRAP_ECUDA;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
+  if (cs == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
     if (e != cudaSuccess || !p) return IONTRAP_ECUDA;
     g_addr[dev] = static_cast<unsigned char*>(p);
   }
+  if (!g_addr[dev]) return IONTRAP_ECUDA;
   *out = g_addr[dev];
   return IONTRAP_OK;
 }
@@ -88,10 +95,10 @@ extern "C" int iontrap_forces_noalloc(const iontrap_species* species, int n_spec
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return IONTRAP_ECUDA;
-  unsigned char* base = nullptr;
-  const int st = scratch_for_device(dev, &base);
-  if (st) return st;
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  unsigned char* base = nullptr;
+  const int st = scratch_for_device(dev, stream, &base);
+  if (st) return st;
 
   StepArgs A{};
   A.n = n;
@@ -118,8 +125,11 @@ extern "C" int iontrap_forces_noalloc(const iontrap_species* species, int n_spec
     A.spc[s].w = (float)z;
   }
 
-  // step = 0, error flags = 0, done = 0, counters = 0
+  // step = 0, error flags = 0, done = 0, counters = 0; the output starts as NaN (all bits
+  // set), so an ion whose sum never completes -- its i-block gave up on a bounded wait --
+  // reads NaN instead of a stale value
   cudaError_t e = cudaMemsetAsync(base, 0, kOffCnt + kCntBytes, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_acc, 0xFF, 3 * (size_t)n * sizeof(double), stream);
   int b = 0, f64 = 0;
   void* prep_params[] = {&A, &b, &f64};
   const unsigned prep_blocks = (unsigned)std::min<long long>((n + 255) / 256, 4096);

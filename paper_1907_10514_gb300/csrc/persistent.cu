@@ -307,13 +307,15 @@ __global__ void __launch_bounds__(32 * W, 16 / W) k_step_f32_gp(const __grid_con
   }
 
   // once every CTA has counted its last step: clear the counters, advance the step index
+  // (not after a wait gave up: the handle's sticky timeout status retires it)
   if (blockIdx.x == 0 && tid == poller) {
-    poll_wait<true>(ctr_step, G * (unsigned)P.K, A.err);
-    const int groups = (int)(G / (unsigned)S);
-    for (int q = 0; q < groups; ++q) P.sync[32 * (1 + q)] = 0u;
-    *ctr_step = 0u;
-    if (!forces) *A.step = ns0 + P.K;
-    __threadfence();
+    if (poll_wait<true>(ctr_step, G * (unsigned)P.K, A.err)) {
+      const int groups = (int)(G / (unsigned)S);
+      for (int q = 0; q < groups; ++q) P.sync[32 * (1 + q)] = 0u;
+      *ctr_step = 0u;
+      if (!forces) *A.step = ns0 + P.K;
+      __threadfence();
+    }
   }
 }
 
@@ -521,9 +523,12 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
       bad = !poll_wait<true>(ctr_step, G * (unsigned)t, A.err);
       if (!bad) {
         // the positions the other CTAs wrote (generic stores, ordered by the counter)
-        // are read by the copy engine, and this CTA's shared memory last read by threads
-        // is written by it: both need a proxy fence
+        // are read by the copy engine: a proxy fence orders them before the copies.  The
+        // copies then overwrite shared memory that this CTA's threads last read before
+        // the CTA barrier that preceded its arrival; the second fence orders those
+        // generic accesses before the async writes as well.
         asm volatile("fence.proxy.async.global;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         const float* src = gsoa + (rb ? soa_len : 0);
         for (int b = 0; b < nb; ++b) {
           const int p0 = b * NP / nb, p1 = (b + 1) * NP / nb;
@@ -675,12 +680,15 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
     }
   }
 
-  // once every CTA has counted its last step: clear the counter, advance the step index
+  // once every CTA has counted its last step: clear the counter, advance the step index.
+  // A launch that gave up on a wait leaves both alone: its FP64 state is still the one it
+  // started from, and the handle's sticky timeout status retires the counter with it.
   if (blockIdx.x == 0 && tid == poller) {
-    poll_wait<true>(ctr_step, G * (unsigned)P.K, A.err);
-    *ctr_step = 0u;
-    if (!forces) *A.step = ns0 + P.K;
-    __threadfence();
+    if (poll_wait<true>(ctr_step, G * (unsigned)P.K, A.err)) {
+      *ctr_step = 0u;
+      if (!forces) *A.step = ns0 + P.K;
+      __threadfence();
+    }
   }
 }
 

@@ -141,11 +141,13 @@ def test_forces_maximum_size_sampled(it):
 # ------------------------------------------------------------------ trajectories
 
 def test_mix_n4096_trajectory_100_steps(it):
-    """The N = 4096 two-species cloud diverges chaotically before step 100: CPU emulation
-    of correctly rounded FP32 pair arithmetic departs from the FP64 oracle by 1.2e-7 at
-    step 50, 1.6e-5 at 75 and 7.9e-5 at 100 (2.4e-7 / 4.2e-5 / 1.9e-4 with an rsqrt of
-    MUFU accuracy).  So the FP32 form is held to 1e-6 at step 50, before the divergence,
-    and to 5e-4 at step 100; the plain FP64 form to 1e-9 at both."""
+    """The N = 4096 two-species cloud amplifies force perturbations more than a
+    hundredfold between steps 50 and 100 (pinned on the CPU by test_fp32_horizon.py:
+    FP32 pair arithmetic of any rsqrt accuracy, correctly rounded included, departs from
+    the FP64 oracle by < 1e-6 at step 50 and by 6e-5 .. 1.8e-4 at step 100, and the FP64
+    oracle under 1e-7 force perturbations by 1.7e-4 .. 2.9e-4).  So the FP32 form is held
+    to 1e-6 at step 50 and to 5e-4 at step 100 (velocities 1e-5 and 1e-3); the plain FP64
+    form to 1e-9 at both."""
     w = iongen.mix_n4096()
     q, m, p = _oracle_side(w)
     x50, v50, a50 = oracle.run(w.x0, w.v0, q, m, p, 50)
@@ -154,12 +156,14 @@ def test_mix_n4096_trajectory_100_steps(it):
         with _sim(it, w, prec) as sim:
             sim.step(50)
             x, v, step, t = sim.state()
-            assert step == 50 and rel_rms(x, x50) < tol50, prec
-            assert rel_rms(v, v50) < 10 * tol50, prec
+            e50 = (rel_rms(x, x50), rel_rms(v, v50))
             sim.step(50)
-            x, v, step, t = sim.state()
-        assert step == 100 and t == pytest.approx(100 * w.trap.dt, rel=1e-15)
-        assert rel_rms(x, x100) < tol100, prec
+            x, v, step100, t = sim.state()
+        e100 = (rel_rms(x, x100), rel_rms(v, v100))
+        print(f"\n  precision {prec}: step 50 x {e50[0]:.2e} v {e50[1]:.2e}; step 100 x {e100[0]:.2e} v {e100[1]:.2e}")
+        assert step == 50 and e50[0] < tol50 and e50[1] < 10 * tol50, (prec, e50)
+        assert step100 == 100 and t == pytest.approx(100 * w.trap.dt, rel=1e-15)
+        assert e100[0] < tol100 and e100[1] < (1e-3 if prec == it.IONTRAP_PREC_FP32 else tol100), (prec, e100)
 
 
 def test_plain_n64_trajectory(it):
@@ -447,13 +451,19 @@ def test_batched_trajectory_matches_oracle(it, n):
     (ion, part) items, ragged last CTAs) against the oracle over 100 steps."""
     w = _cloud(n, 300 + n)
     q, m, p = _oracle_side(w)
-    # the 1500-ion cloud has a close encounter between steps 80 and 100 that takes every
-    # form (batched, last-CTA, row-persistent) from ~1e-6 to 4e-5 .. 3e-4 of the oracle
-    steps = 80 if n == 1500 else 100
-    xo, vo, _ = oracle.run(w.x0, w.v0, q, m, p, steps)
-    (x, v, step, _), = _run_many(it, [w], [steps])
-    assert step == steps
-    if n > 1:
+    xo, vo, _ = oracle.run(w.x0, w.v0, q, m, p, 100)
+    (x, v, step, _), = _run_many(it, [w], [100])
+    assert step == 100
+    if n == 1500:
+        # a close encounter between steps 80 and 100 amplifies any FP32-sized force error
+        # to ~1e-4 by step 100 (the FP64 oracle under 1e-7 force perturbations: < 3e-6 at
+        # step 80, 0.7 .. 1.1e-4 at step 100; test_fp32_horizon.py): step 80 is held to the
+        # 1e-4 bar and step 100 to 5e-4 (velocities 1e-3 and 5e-3)
+        x80, v80, _ = oracle.run(w.x0, w.v0, q, m, p, 80)
+        (xg, vg, s80, _), = _run_many(it, [w], [80])
+        assert s80 == 80 and rel_rms(xg, x80) < FP32_TRAJ_TOL and rel_rms(vg, v80) < 10 * FP32_TRAJ_TOL
+        assert rel_rms(x, xo) < 5e-4 and rel_rms(v, vo) < 5e-3
+    elif n > 1:
         assert rel_rms(x, xo) < FP32_TRAJ_TOL and rel_rms(v, vo) < 10 * FP32_TRAJ_TOL
     else:  # a lone ion: only the FP32 Box-Muller noise differs from the oracle's FP64 noise
         assert rel_rms(x, xo) < 1e-9

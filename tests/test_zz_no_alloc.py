@@ -1,15 +1,17 @@
 """The allocation-free force entry point, for callers that cannot allocate device memory
 (their memory pool owns the device, or they host this library as a plugin, or they
 cannot take cudaMalloc's implicit synchronisation).  It must give the same Coulomb
-accelerations as iontrap_forces on a handle, within the FP32 force tolerance of the
-other tests, on consecutive calls that reuse its fixed scratch array.  This file is
-named to be collected last."""
+accelerations as iontrap_forces on a handle, and the FP64 oracle's, within the FP32
+force tolerance of the other tests, on consecutive calls that reuse its fixed scratch
+array (at n = 8192, the size limit, on sampled ions).  This file is named to be
+collected last."""
 import math
 
 import numpy as np
 import pytest
 
 import iongen
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -50,6 +52,11 @@ def test_forces_noalloc_matches_handle_forces_on_consecutive_calls():
         got = d_acc.cpu().numpy()
         assert np.isfinite(got).all()
         assert _rel_rms(got, ref) < FP32_FORCE_TOL, n
+        # against the FP64 oracle (all ions, or 512 sampled ones at the size limit)
+        q, m, _ = oracle.ion_arrays(species, sp)
+        idx = np.arange(n) if n < 8192 else np.random.default_rng(seed).choice(n, 512, replace=False)
+        exact = oracle.coulomb_accel(x, q, m, idx=idx)
+        assert _rel_rms(got[:, idx], exact) < FP32_FORCE_TOL, n
 
 
 def test_forces_noalloc_rejects_sizes_beyond_its_scratch():
