@@ -47,14 +47,23 @@ def ops_per_pair(species):
 FP32_LANES_PER_SM = 128
 MUFU_PER_SM = 16
 NOMINAL_SM_MHZ = 2070.0
-# DRAM bytes (read + write) per timestep of the step kernel, from the ncu captures
-# summarised in profiles/; valid only for that launch configuration.
-PROFILED_TRAFFIC = {
-    # one launch per timestep (profiles/step_f32_cw_mix_n4096.md)
-    (128, 2, 1, 512, 3): (485376 + 0, "DRAM bytes per timestep launch (ncu, profiles/step_f32_cw_mix_n4096.md)"),
-    # row-persistent form: its last capture (25.3 KB of DRAM traffic per timestep, 27 or 32
-    # ions per CTA) predates a prologue proxy fence added since, so no figure is claimed
-}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum, per timestep) of the step
+# kernel from one ncu capture, keyed by a fingerprint of the CUDA sources the kernel is
+# built from and by its launch shape (threads, ions per thread, packed, jsplit, fused); the
+# bench reports it only while both still match, and null otherwise.
+KERNEL_DRAM_TRAFFIC = {}
+KERNEL_SOURCES = ("persistent.cu", "iontrap_internal.cuh")
+
+
+def kernel_fingerprint():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1907_10514_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 # timesteps per cooperative launch of the grid-persistent form (include/iontrap.h)
 GP_STEPS_PER_LAUNCH = 1000
 
@@ -75,6 +84,16 @@ def _barrier(ws):
     if ws > 1:
         import torch.distributed as dist
         dist.barrier()
+
+
+def _gather(ws, obj):
+    """Every rank's obj, on every rank (result reporting only; no data-path exchange)."""
+    if ws == 1:
+        return [obj]
+    import torch.distributed as dist
+    out = [None] * ws
+    dist.all_gather_object(out, obj)
+    return out
 
 
 def _max_over_ranks(ws, x):
@@ -273,15 +292,21 @@ def run_gpu(args):
     extra = {}
     if rank == 0 and not args.no_extra:
         extra = extra_measurements(it, torch, stream, sms, args)
-    if rank == 0 and not args.no_batched:
-        extra["batched_512"] = batched_measurement(it, torch, stream)
-    if rank == 0 and not args.no_serve:
-        extra["serve"] = serve_measurement(it, torch, args.serve_requests, args.serve_step_scale,
-                                           args.serve_budget_mb << 20, args.serve_fp64_subset)
+        extra["plain_n64"] = plain_n64_measurement(it, torch, stream)
+    # independent ensembles and requests: every rank advances its own shard, no collective
+    # on the data path; rank 0 reports the aggregate over the slowest rank's time
+    if not args.no_batched:
+        b = _gather(ws, batched_measurement(it, torch, stream, rank, ws, tune_us=args.tune_us))
+        if rank == 0:
+            extra["batched_512"] = aggregate_batched(b)
+    if not args.no_serve:
+        sv = serve_measurement(it, torch, args, rank, ws)
+        if rank == 0:
+            extra["serve"] = sv
     if rank == 0:
         probe = {}
-        for kind, name in ((0, "ffma"), (1, "ffma2"), (2, "mufu_rsqrt"), (3, "dfma")):
-            ops, mhz = it.iontrap_alu_probe(kind, 4000 if kind == 3 else 20000)
+        for kind, name in ((0, "ffma"), (1, "ffma2"), (2, "mufu_rsqrt"), (3, "dfma"), (4, "fadd2"), (5, "cvt_f32_f64")):
+            ops, mhz = it.iontrap_alu_probe(kind, 4000 if kind in (3, 5) else 20000)
             probe[name] = round(ops, 2)
         probe["sm_mhz"] = round(mhz)
         extra["alu_probe_lane_ops_per_clk_per_sm"] = probe
@@ -292,7 +317,11 @@ def run_gpu(args):
         cpu = {"value": rate, "unit": "ion-steps/s", "cores": cores, "kind": "oracle",
                "sample": f"{args.cpu_sample_steps} timesteps of the same N=4096 workload "
                          f"({dt:.1f} s, FP64 C/OpenMP)"}
+        if not args.no_extra:
+            extra["oracle_timing"] = oracle_timing(args)
 
+    fp = kernel_fingerprint()
+    traffic = KERNEL_DRAM_TRAFFIC.get((fp, tuple(cfg[:5])))
     peaks = _peaks()
     line = {
         "metric": "ion-steps/s", "value": value, "unit": "ion-steps/s", "n_gpus": ws,
@@ -317,8 +346,10 @@ def run_gpu(args):
         "gpu_launches": args.steps * (-(-nsteps // GP_STEPS_PER_LAUNCH) if cfg[4] >= 4 else nsteps),
         "roofline": {"bound": "alu", "achieved": achieved_gpairs, "peak": peak_gpairs,
                      "unit": "Gpair/s", "frac": achieved_gpairs / peak_gpairs,
-                     "traffic": PROFILED_TRAFFIC.get(tuple(cfg[:5]), (None, None))[0],
-                     "traffic_unit": PROFILED_TRAFFIC.get(tuple(cfg[:5]), (None, "not profiled for this tile"))[1],
+                     "traffic": traffic,
+                     "traffic_unit": "DRAM bytes per timestep (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+                     "traffic_source": (f"ncu capture of kernel sources {fp} at this launch shape" if traffic is not None
+                                        else f"no ncu capture of kernel sources {fp} at launch shape {list(cfg[:5])}"),
                      "basis": f"{sms} SMs x {NOMINAL_SM_MHZ:.0f} MHz x {FP32_LANES_PER_SM} FP32 lanes / "
                               f"{opp} FP32 instr per ordered pair (MUFU roof "
                               f"{MUFU_PER_SM}/clk/SM not binding); achieved = N(N-1) per timestep / "
@@ -477,16 +508,23 @@ def sampled_force_error(it, sim, w, k=256, seed=0):
     return float(np.sqrt(((f[:, idx] - ref) ** 2).sum() / (ref ** 2).sum()))
 
 
-def batched_measurement(it, torch, stream, steps=2000):
-    """512 independent Ca+ ensembles (N log-uniform in [16, 2048]) advanced together by
-    iontrap_step_many (batched resident kernel), 2000 steps."""
+def batched_measurement(it, torch, stream, rank=0, world=1, steps=2000, tune_us=0.0):
+    """This rank's shard of the 512 independent Ca+ ensembles (N log-uniform in [16, 2048])
+    advanced together by iontrap_step_many (batched resident kernels), 2000 steps."""
     import iongen
     stable = lambda species, trap: it.iontrap_stable(species, it.make_params(trap))
-    ws = iongen.batched_512(stable=stable, steps=steps)
+    every = iongen.batched_512(stable=stable, steps=steps)
+    ws = [every[k] for k in shard(range(len(every)), rank, world)]
     sims = [it.Simulation(w.species, w.species_of_ion, w.x0, w.v0, it.make_params(w.trap), stream=stream)
             for w in ws]
     try:
         hs = [s.handle for s in sims]
+        tuned = {}
+        if tune_us > 0:  # the batched launch's autotuner: group shapes per N bucket (states unchanged)
+            it.iontrap_autotune_many(hs, trial_us=tune_us)
+            tuned = {e["log2n"]: {"ctas_per_group": e["splits"], "parts": e["ions_per_thread"] or "cost model",
+                                  "us_per_step_of_the_batch": round(e["us_per_step"], 2)}
+                     for e in it.iontrap_tuning_get() if e["precision"] == it.IONTRAP_TUNE_BATCHED}
         it.iontrap_step_many(hs, [100] * len(hs))  # warm-up
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -495,81 +533,263 @@ def batched_measurement(it, torch, stream, steps=2000):
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1)
-        pick = np.random.default_rng(7).choice(len(ws), 8, replace=False)
+        pick = np.random.default_rng(7 + rank).choice(len(ws), min(8, len(ws)), replace=False)
         errs = [sampled_force_error(it, sims[k], ws[k], k=64, seed=int(k)) for k in pick]
     finally:
         for s in sims:
             s.close()
-    ions = sum(w.n for w in ws)
-    pairs = sum(w.n * (w.n - 1) for w in ws)
-    return {"ensembles": len(ws), "ions": ions, "timesteps": steps, "ms": ms,
-            "force_rel_rms_vs_oracle_max": max(errs), "error_sample": "8 ensembles, 64 ions each, after the run",
+    return {"ensembles": len(ws), "ions": sum(w.n for w in ws), "pairs": sum(w.n * (w.n - 1) for w in ws),
+            "ms": ms, "steps": steps, "errs": errs, "redraws": sum(w.redraws for w in ws), "tuned": tuned}
+
+
+def aggregate_batched(parts):
+    ms = max(p["ms"] for p in parts)
+    steps = parts[0]["steps"]
+    ions = sum(p["ions"] for p in parts)
+    pairs = sum(p["pairs"] for p in parts)
+    return {"ensembles": sum(p["ensembles"] for p in parts), "ions": ions, "timesteps": steps, "ms": ms,
+            "ranks": len(parts), "ms_per_rank": [p["ms"] for p in parts],
+            "force_rel_rms_vs_oracle_max": max(max(p["errs"]) for p in parts if p["errs"]),
+            "error_sample": "8 ensembles per rank, 64 ions each, after the run",
             "ion_steps_per_s": ions * steps / (ms / 1e3), "pair_interactions_per_s": pairs * steps / (ms / 1e3),
-            "launches": 2 * ((steps + 999) // 1000)}
+            "unstable_trap_redraws": sum(p["redraws"] for p in parts),
+            "tuned_group_shapes_by_log2n": parts[0]["tuned"],
+            "launches_per_rank": 2 * ((steps + 999) // 1000)}
 
 
-def serve_measurement(it, torch, count, step_scale, budget_bytes, fp64_subset):
-    """The request stream (Poisson 200/s, N log-uniform in [8, 65536], Ca+ or 80/20
-    Ca+/NH3+) with step budgets divided by step_scale, submitted at their arrival times
-    to the continuous-batching server; latency = completion - arrival."""
-    import iongen
-    stable = lambda species, trap: it.iontrap_stable(species, it.make_params(trap))
-    full = iongen.serve_stream(stable=stable)
-    full_pairs = sum(r.n * r.n * r.steps for r in full)
-    offered_full = full_pairs / full[-1].arrival_s
-    reqs = full[:count]
-    for r in reqs:
-        r.steps = max(1, int(round(r.steps / step_scale)))
-    work = [(iongen.request_workload(r), r) for r in reqs]
+def _serve_run(it, torch, work, arrivals, budget_bytes, keep=()):
+    """Submit each request at its arrival time (s after the start) to a fresh serving
+    loop and poll it; returns (latencies s, wall s, {index: final x} for ``keep``)."""
     srv = it.iontrap_server_create(mem_budget_bytes=budget_bytes, max_resident=4096, chunk_steps=100)
-    lat, arrival, ids = [], {}, {}
+    lat = [None] * len(work)
+    kept, index, ns = {}, {}, {}
     try:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        k = 0
-        pending = len(work)
+        k, pending = 0, len(work)
         while pending:
             now = time.perf_counter() - t0
-            while k < len(work) and work[k][1].arrival_s <= now:
-                w, r = work[k]
+            while k < len(work) and arrivals[k] <= now:
+                w = work[k]
                 rid = it.iontrap_server_submit(srv, w.species, w.species_of_ion, w.x0, w.v0, it.make_params(w.trap),
-                                               r.steps)
-                arrival[rid] = r.arrival_s
-                ids[rid] = w.n
+                                               w.steps)
+                index[rid], ns[rid] = k, w.n
                 k += 1
-            for rid in it.iontrap_server_poll(srv):
-                lat.append(time.perf_counter() - t0 - arrival[rid])
-                it.iontrap_server_result(srv, rid, ids[rid])
+            done = it.iontrap_server_poll(srv)
+            for rid in done:
+                i = index[rid]
+                lat[i] = time.perf_counter() - t0 - arrivals[i]
+                x, _, step, status = it.iontrap_server_result(srv, rid, ns[rid])
+                if i in keep:
+                    kept[i] = (x, step, status)
                 pending -= 1
-            time.sleep(0.0002)
+            if not done:
+                time.sleep(0.0002)
         wall = time.perf_counter() - t0
     finally:
         it.iontrap_server_destroy(srv)
-    ion_steps = sum(r.n * r.steps for r in reqs)
-    pairs = sum(r.n * (r.n - 1) * r.steps for r in reqs)
-    lat_ms = np.array(lat) * 1e3
-    out = {"requests": len(reqs), "step_scale": step_scale, "arrival_span_s": reqs[-1].arrival_s, "wall_s": wall,
-           "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
-           "ion_steps_per_s": ion_steps / wall, "pair_interactions_per_s": pairs / wall,
-           "offered_pairs_per_s": pairs / reqs[-1].arrival_s, "mem_budget_bytes": budget_bytes,
-           "full_stream_offered_pairs_per_s": offered_full, "full_stream_requests": len(full)}
-    # baseline: the plain FP64 form, one simulation at a time in arrival order (subset)
-    t = 0.0
-    sub = work[:fp64_subset]
-    for w, r in sub:
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
+    return lat, wall, kept
+
+
+def _fifo_fp64(it, torch, work, arrivals, cap_s, chunk=200):
+    """The plain FP64 form, one simulation at a time in arrival order, each started no
+    earlier than its arrival and stepped in chunks of 200 steps; the run stops at the
+    first chunk boundary after cap_s of wall time (the request in progress is not served).
+    Returns the latencies of the served requests (None for the others) and the wall time."""
+    lat = [None] * len(work)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k, w in enumerate(work):
+        now = time.perf_counter() - t0
+        if now > cap_s or arrivals[k] > cap_s:
+            break
+        if arrivals[k] > now:
+            time.sleep(arrivals[k] - now)
         h = it.iontrap_create(w.species, w.species_of_ion, w.x0, w.v0,
                               it.make_params(w.trap, precision=it.IONTRAP_PREC_FP64))
-        it.iontrap_step(h, r.steps)
-        it.iontrap_state(h, w.n)
-        t += time.perf_counter() - t1
-        it.iontrap_destroy(h)
-    sub_ion_steps = sum(r.n * r.steps for _, r in sub)
-    ours_sub = sum(r.n * r.steps for _, r in sub)
-    out["fp64_fifo_baseline"] = {"requests": len(sub), "ion_steps_per_s": sub_ion_steps / t, "seconds": t,
-                                 "note": "plain FP64 form, one simulation at a time, first requests of the stream"}
-    del ours_sub
+        try:
+            done = 0
+            while done < w.steps and time.perf_counter() - t0 <= cap_s:
+                it.iontrap_step(h, min(chunk, w.steps - done))
+                it.iontrap_sync(h)
+                done += min(chunk, w.steps - done)
+            if done == w.steps:
+                it.iontrap_state(h, w.n)
+                lat[k] = time.perf_counter() - t0 - arrivals[k]
+        finally:
+            it.iontrap_destroy(h)
+        if lat[k] is None:
+            break
+    return lat, time.perf_counter() - t0
+
+
+def _pct(lat_s):
+    """p50 and p99 of latencies given in seconds, in ms."""
+    v = np.array(lat_s, dtype=np.float64) * 1e3
+    return {"p50_ms": float(np.percentile(v, 50)), "p99_ms": float(np.percentile(v, 99))}
+
+
+def serve_measurement(it, torch, args, rank=0, world=1):
+    """The request stream (Poisson 200/s, N log-uniform in [8, 65536], step budgets
+    log-uniform in [1e3, 1e5], Ca+ or 80/20 Ca+/NH3+): its first K requests, each step
+    budget divided by step_scale, through the continuous-batching server -- at their
+    generated arrival times (offered load far above one GPU's capacity), and again with the
+    arrivals stretched to 0.7 of the measured capacity -- and the plain FP64 form serving
+    the same K one at a time (FIFO).  Latency = completion - arrival.  With several ranks
+    each rank serves its shard of the K requests on its own GPU."""
+    import iongen
+    import oracle
+    stable = lambda species, trap: it.iontrap_stable(species, it.make_params(trap))
+    full = iongen.serve_stream(stable=stable)
+    full_pairs = sum(r.n * r.n * r.steps for r in full)
+    K, scale = args.serve_requests, args.serve_step_scale
+    reqs = full[:K]
+    for r in reqs:
+        r.steps = max(1, int(round(r.steps / scale)))
+    mine = shard(range(K), rank, world)
+    work = [iongen.request_workload(reqs[k]) for k in mine]
+    arrivals = [reqs[k].arrival_s for k in mine]
+    pairs_of = [w.n * (w.n - 1) * w.steps for w in work]
+    budget = args.serve_budget_mb << 20
+    # sampled results whose error against the oracle is stated (their final state's forces)
+    keep = set(np.random.default_rng(11).choice(len(work), min(6, len(work)), replace=False).tolist())
+    lat, wall, kept = _serve_run(it, torch, work, arrivals, budget, keep)
+    cap_mine = sum(pairs_of) / wall
+    # the companion run: the same requests, arrivals stretched so that the offered load is
+    # 0.7 of the capacity the first run sustained
+    span = max(arrivals) if arrivals else 0.0
+    stretch = (sum(pairs_of) / (0.7 * cap_mine)) / span if span > 0 else 1.0
+    arr07 = [a * stretch for a in arrivals]
+    lat07, wall07, _ = _serve_run(it, torch, work, arr07, budget)
+    lat64, wall64 = _fifo_fp64(it, torch, work, arrivals, args.serve_fp64_cap_s)
+    errs = []
+    for i, (x, step, status) in sorted(kept.items()):
+        w = work[i]
+        if status != 0 or step != w.steps:
+            errs.append({"request": mine[i], "n": w.n, "status": status})
+            continue
+        q, m, _ = oracle.ion_arrays(w.species, w.species_of_ion)
+        with it.Simulation(w.species, w.species_of_ion, x, None, it.make_params(w.trap)) as s:
+            f = s.forces()
+        idx = np.random.default_rng(i).choice(w.n, min(128, w.n), replace=False)
+        ref = oracle.coulomb_accel(x, q, m, idx=idx)
+        err = float(np.sqrt(((f[:, idx] - ref) ** 2).sum() / max((ref ** 2).sum(), 1e-300))) if w.n > 1 else 0.0
+        errs.append({"request": mine[i], "n": w.n, "steps": w.steps, "force_rel_rms_vs_oracle": err})
+    mine_out = {"lat": lat, "wall": wall, "lat07": lat07, "wall07": wall07, "arr07": arr07, "lat64": lat64,
+                "wall64": wall64, "arrivals": arrivals, "pairs": sum(pairs_of),
+                "ion_steps": sum(w.n * w.steps for w in work), "errs": errs,
+                "redraws": sum(reqs[k].redraws for k in mine), "n": len(work)}
+    parts = _gather(world, mine_out)
+    if rank != 0:
+        return None
+    meta = {"requests": K, "step_scale": scale, "mem_budget_bytes": budget, "full_stream_requests": len(full),
+            "full_stream_offered_pairs_per_s": full_pairs / full[-1].arrival_s, "arrival_span_s": reqs[-1].arrival_s,
+            "fp64_cap_s": args.serve_fp64_cap_s}
+    return aggregate_serve(parts, meta)
+
+
+def aggregate_serve(parts, meta):
+    """Rank 0's summary of the serving measurement from every rank's record."""
+    cat = lambda key: [x for p in parts for x in p[key]]
+    pairs = sum(p["pairs"] for p in parts)
+    ion_steps = sum(p["ion_steps"] for p in parts)
+    wall = max(p["wall"] for p in parts)
+    primary = {"wall_s": wall, "arrival_span_s": meta["arrival_span_s"],
+               "offered_pairs_per_s": pairs / meta["arrival_span_s"],
+               "pair_interactions_per_s": pairs / wall, "ion_steps_per_s": ion_steps / wall}
+    primary.update(_pct(cat("lat")))
+    wall07 = max(p["wall07"] for p in parts)
+    span07 = max(max(p["arr07"]) for p in parts if p["arr07"])
+    comp = {"wall_s": wall07, "arrival_span_s": span07, "offered_pairs_per_s": pairs / span07,
+            "pair_interactions_per_s": pairs / wall07, "ion_steps_per_s": ion_steps / wall07}
+    comp.update(_pct(cat("lat07")))
+    # the FP64 FIFO: a request not started within the cap counts as waiting until its
+    # rank's run ended, so its percentiles are then lower bounds
+    lat64 = [(l if l is not None else p["wall64"] - p["arrivals"][k])
+             for p in parts for k, l in enumerate(p["lat64"])]
+    served = sum(1 for p in parts for l in p["lat64"] if l is not None)
+    fifo = {"wall_s": max(p["wall64"] for p in parts), "cap_s": meta["fp64_cap_s"],
+            "note": "plain FP64 form, one simulation at a time in arrival order (same requests, same arrival times); "
+                    "requests not started within the cap count as waiting until the end of the run (lower bounds)"}
+    fifo.update(_pct(lat64))
+    fifo["served"], fifo["not_served"] = served, len(lat64) - served
+    fifo["percentiles_are_lower_bounds"] = served < len(lat64)
+    return {"requests": meta["requests"], "ranks": len(parts), "requests_per_rank": [p["n"] for p in parts],
+            "step_scale": meta["step_scale"],
+            "step_budgets": f"the stream's budgets (1e3 .. 1e5) divided by {meta['step_scale']:g}",
+            "mem_budget_bytes": meta["mem_budget_bytes"], "full_stream_requests": meta["full_stream_requests"],
+            "full_stream_offered_pairs_per_s": meta["full_stream_offered_pairs_per_s"],
+            "unstable_trap_redraws": sum(p["redraws"] for p in parts),
+            "at_generated_arrivals": primary, "at_0.7_capacity": comp, "fp64_fifo_same_requests": fifo,
+            "per_result_error": cat("errs"),
+            "error_note": "relative RMS of the FP32 pair accelerations at each sampled result's final state "
+                          "against the FP64 oracle (128 sampled ions); served results are bitwise equal alone "
+                          "and in the mix (tests)"}
+
+
+def plain_n64_measurement(it, torch, stream):
+    """The plain method's workload: N = 64 Ca+ in the RF trap, 10 000 steps, in the plain
+    FP64 form, and the FP32 form beside it; errors against the oracle at step 100 and at
+    the end of the run."""
+    import iongen
+    import oracle
+    w = iongen.plain_n64()
+    q, m, qm0 = oracle.ion_arrays(w.species, w.species_of_ion)
+    p = oracle.params(w.trap, qm0)
+    x100, _, _ = oracle.run(w.x0, w.v0, q, m, p, 100)
+    out = {"n_ions": w.n, "timesteps": w.steps}
+    for name, prec in (("fp64_form", it.IONTRAP_PREC_FP64), ("fp32_form", it.IONTRAP_PREC_FP32)):
+        pr = it.make_params(w.trap, precision=prec)
+        with it.Simulation(w.species, w.species_of_ion, w.x0, w.v0, pr, stream=stream) as s:
+            s.step(100)
+            x, _, _, _ = s.state()
+            traj = float(np.sqrt(((x - x100) ** 2).sum() / (x100 ** 2).sum()))
+            s.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(w.steps)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            ferr = sampled_force_error(it, s, w, k=64)
+            cfg = list(s.config())
+        out[name] = {"us_per_timestep": 1e3 * ms / w.steps, "ion_steps_per_s": w.n * w.steps / (ms / 1e3),
+                     "tile": cfg, "trajectory_rel_rms_vs_oracle_step100": traj,
+                     "force_rel_rms_vs_oracle_final": ferr}
+    return out
+
+
+def oracle_timing(args):
+    """The FP64 oracle on this host's cores: the plain N = 64 run and the N = 4096 run in
+    full, and for the N = 32768 crystal 8 force evaluations plus a 10-step run."""
+    import iongen
+    import oracle
+    out = {"cores": oracle.threads()}
+    try:
+        out["cpu_model"] = next(l.split(":", 1)[1].strip() for l in open("/proc/cpuinfo")
+                                if l.lower().startswith(("model name", "cpu part")))
+    except Exception:
+        out["cpu_model"] = None
+    for name, gen in (("plain_n64", iongen.plain_n64), ("mix_n4096", iongen.mix_n4096)):
+        w = gen()
+        q, m, qm0 = oracle.ion_arrays(w.species, w.species_of_ion)
+        p = oracle.params(w.trap, qm0)
+        t0 = time.perf_counter()
+        oracle.run(w.x0, w.v0, q, m, p, w.steps)
+        dt = time.perf_counter() - t0
+        out[name] = {"timesteps": w.steps, "seconds": dt, "ion_steps_per_s": w.n * w.steps / dt}
+    w = iongen.crystal_n32768()
+    q, m, qm0 = oracle.ion_arrays(w.species, w.species_of_ion)
+    p = oracle.params(w.trap, qm0)
+    t0 = time.perf_counter()
+    for _ in range(8):
+        oracle.coulomb_accel(w.x0, q, m)
+    t_f = (time.perf_counter() - t0) / 8
+    t0 = time.perf_counter()
+    oracle.run(w.x0, w.v0, q, m, p, 10)
+    t_r = (time.perf_counter() - t0) / 10
+    out["crystal_n32768"] = {"force_evaluation_s": t_f, "seconds_per_timestep_10_step_run": t_r,
+                             "ion_steps_per_s": w.n / t_r}
     return out
 
 
@@ -584,11 +804,11 @@ def main():
     ap.add_argument("--cpu-sample-steps", type=int, default=200)
     ap.add_argument("--ref-sample-steps", type=int, default=100)
     ap.add_argument("--fp64-steps", type=int, default=50)
-    ap.add_argument("--serve-requests", type=int, default=800)
+    ap.add_argument("--serve-requests", type=int, default=100)
     ap.add_argument("--tune-us", type=float, default=3000.0)
-    ap.add_argument("--serve-step-scale", type=float, default=1000.0)
+    ap.add_argument("--serve-step-scale", type=float, default=20.0)
     ap.add_argument("--serve-budget-mb", type=int, default=2048)
-    ap.add_argument("--serve-fp64-subset", type=int, default=20)
+    ap.add_argument("--serve-fp64-cap-s", type=float, default=20.0)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()

@@ -224,7 +224,10 @@ int iontrap_step_record(iontrap_t *h, int64_t n_steps, int64_t every, uint32_t f
 int iontrap_sync(iontrap_t *h);
 
 /* Synchronise, then copy out the state: x[3n], v[3n] (either may be NULL), the step
- * index *step and time *t = step dt (either may be NULL). */
+ * index *step and time *t = step dt (either may be NULL).  After a device-side failure
+ * (IONTRAP_ENONFINITE, IONTRAP_ETIMEOUT) the state is still copied out -- for a timeout in
+ * the row-persistent form it is the state the failed launch started from -- and the
+ * sticky status is returned. */
 int iontrap_state(iontrap_t *h, double *x, double *v, int64_t *step, double *t);
 
 /* Synchronise, then write the Coulomb acceleration k_e e^2 z_i/M_i sum_j z_j d_ij/r_ij^3
@@ -431,6 +434,22 @@ void iontrap_server_destroy(iontrap_server_t *s);
 int iontrap_forces_noalloc(const iontrap_species *species, int n_species, const uint8_t *d_species_of_ion,
                            const double *d_x, int64_t n, double *d_acc, void *cuda_stream);
 
+/* Test hook of the failure detection (no counterpart in the paper).  Every wait of the persistent forms 4 and 5
+ * -- a CTA's poller waiting for the other CTAs' arrivals on a step or group counter, a
+ * CTA waiting for its bulk copies -- gives up after a time limit, sets the handle's
+ * timeout flag and ends the launch, which the host reads as IONTRAP_ETIMEOUT.  This hook
+ * makes that happen on purpose, with no fault and no unbounded wait: the persistent
+ * launches of the handle that follow use a limit of wait_limit_ns (0 restores the default,
+ * 2 s), and when cta >= 0, CTA number cta withholds its arrival on the grid-wide step
+ * counter at step `step` (counted from 0 within each launch) -- a counter value nothing
+ * will reach -- so that every other CTA's wait for the next step expires after the
+ * limit.  The launch then stops, the handle's status becomes IONTRAP_ETIMEOUT (sticky)
+ * and its step index is not advanced; in form 5 the FP64 state is the one the launch
+ * started from, in form 4 it may hold some of the launch's steps.  cta < 0 turns the stall
+ * off.  Synchronous (waits for queued work).  EINVAL when the handle is not in form 4 or
+ * 5, or cta is not below the launch's CTA count. */
+int iontrap_test_stall(iontrap_t *h, int64_t wait_limit_ns, int32_t cta, int64_t step);
+
 /* Profiling hook: run ONE step with per-CTA phase timestamps (%globaltimer, ns) and copy
  * them to marks[cap] (EINVAL in the grid-persistent form 4; in the row-persistent form 5
  * one launch of 8 steps, 4 marks per CTA and step at mark (CTA 8 + step) 4 + m: grid
@@ -459,16 +478,38 @@ typedef struct {
     float us_per_step;        /* measured time of the winner */
 } iontrap_tuning_entry;
 int iontrap_autotune(iontrap_t *h, double trial_us, iontrap_config *best, double *best_us_per_step);
+
+/* iontrap_tuning_entry.precision of the batched launch's entries: the part-major groups
+ * (256 < n <= 2048) of ensembles in bucket log2n use splits CTAs per group (2, 4 or 8, with
+ * at most 256 ions per CTA) and ions_per_thread j-parts per CTA (0: the launcher's cost
+ * model); threads = 256, fused = 6. */
+#define IONTRAP_TUNE_BATCHED 2
+
+/* Autotuner of the batched launch (iontrap_step_many, the batched form of evolve(N) of
+ * Sec. 3 "Time evolution").  For every N bucket floor(log2 n) of the part-major groups among
+ * the given handles (FP32 form, 256 < n <= 2048), largest bucket first, times one batched
+ * launch of all count handles under each candidate shape of that bucket -- CTAs per group
+ * C in {2, 4, 8} and j-parts NP in {cost model, 2, 4, 6, 8, 12}, as far as they fit -- with
+ * the buckets already tuned at their winners and the others at the launcher's defaults,
+ * each candidate for about trial_us of steps in each of two passes (its faster time
+ * counts), and records the winner in the tuning table under (IONTRAP_TUNE_BATCHED, bucket)
+ * for the current device; later batched launches of ensembles in that bucket use it.  The
+ * group shape is a function of the bucket alone, so an ensemble's result stays the same
+ * alone or in any mix.  Every handle's state is checkpointed before and restored after
+ * (tuning does not advance the simulations).  Synchronous. */
+int iontrap_autotune_many(iontrap_t *const *hs, int count, double trial_us);
 /* Read the tuning table of the current device (up to cap entries; *count = entries). */
 int iontrap_tuning_get(iontrap_tuning_entry *out, int cap, int *count);
 /* Add or replace entries of the current device's tuning table (e.g. saved from an
- * earlier autotuning run on the same kind of GPU). */
+ * earlier autotuning run on the same kind of GPU); an entry with splits = 0 removes the
+ * table's entry of its (precision, log2n) instead. */
 int iontrap_tuning_put(const iontrap_tuning_entry *in, int count);
 
 /* Microbenchmark of the pipes the step kernels use (not part of the method): runs
  * independent dependency chains of one instruction kind on every SM of the current
  * device and reports lane operations per SM clock and the SM clock seen.
- * kind: 0 FFMA, 1 packed FFMA2 (2 lanes each), 2 MUFU rsqrt, 3 DFMA, 4 packed FADD2. */
+ * kind: 0 FFMA, 1 packed FFMA2 (2 lanes each), 2 MUFU rsqrt, 3 DFMA, 4 packed FADD2,
+ * 5 FP32 <-> FP64 conversions (lane operations = conversions). */
 int iontrap_alu_probe(int kind, long long iters, double *lane_ops_per_clk_per_sm, double *sm_mhz);
 
 #ifdef __cplusplus

@@ -89,6 +89,7 @@ class Workload:
     v0: np.ndarray                 # float64 (3, N)
     trap: Trap
     steps: int
+    redraws: int = 0               # trap draws rejected as unstable before this one
 
     @property
     def n(self) -> int:
@@ -213,7 +214,9 @@ def batched_512(stable: Optional[StabilityPredicate] = None, count: int = 512,
     out = []
     for e in range(count):
         n = int(round(math.exp(rng.uniform(math.log(16), math.log(2048)))))
+        redraws = -1
         while True:
+            redraws += 1
             q, a, wz = _draw_trap_params(rng)
             trap = Trap(Omega=OMEGA_RF, a=a, q=q, omega_z=wz, gamma=1e5, T_bath=1e-3,
                         dt=rf_period_dt(OMEGA_RF), seed=1000 + e)
@@ -221,7 +224,7 @@ def batched_512(stable: Optional[StabilityPredicate] = None, count: int = 512,
                 break
         x0 = gaussian_positions(n, 30e-6, seed=[3, e])
         out.append(Workload(f"batched_{e}", [CA40], np.zeros(n, np.uint8), x0,
-                            np.zeros((3, n)), trap, steps))
+                            np.zeros((3, n)), trap, steps, redraws))
     return out
 
 
@@ -233,6 +236,7 @@ class Request:
     steps: int
     mixed: bool
     trap: Trap
+    redraws: int = 0  # trap draws rejected as unstable before this one
 
     @property
     def species(self) -> List[Species]:
@@ -252,13 +256,15 @@ def serve_stream(stable: Optional[StabilityPredicate] = None, count: int = 20000
         steps = int(round(math.exp(rng.uniform(math.log(1e3), math.log(1e5)))))
         mixed = bool(rng.uniform() < 0.5)
         species = [CA40, NH3] if mixed else [CA40]
+        redraws = -1
         while True:
+            redraws += 1
             q, a, wz = _draw_trap_params(rng)
             trap = Trap(Omega=OMEGA_RF, a=a, q=q, omega_z=wz, gamma=1e5, T_bath=1e-3,
                         dt=rf_period_dt(OMEGA_RF), seed=100000 + rid)
             if stable is None or stable(species, trap):
                 break
-        reqs.append(Request(rid, t, n, steps, mixed, trap))
+        reqs.append(Request(rid, t, n, steps, mixed, trap, redraws))
     return reqs
 
 
@@ -275,7 +281,7 @@ def request_workload(req: Request) -> Workload:
         sp = np.zeros(n, np.uint8)
     x0 = gaussian_positions(n, sigma, seed=[4, req.rid])
     return Workload(f"req_{req.rid}", req.species, sp, x0, np.zeros((3, n)), req.trap,
-                    req.steps)
+                    req.steps, req.redraws)
 
 
 WORKLOADS = {

@@ -57,6 +57,19 @@ __global__ void k_alu(long long iters, float* sink, unsigned long long* clk) {
       for (int k = 0; k < kChains; ++k) a[k] = probe_rsqrt(a[k]);
 #pragma unroll
     for (int k = 0; k < kChains; ++k) acc += a[k];
+  } else if (KIND == 5) {  // FP32 <-> FP64 conversions (two per iteration)
+    float a[kChains];
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) a[k] = seed + k;
+    for (long long it = 0; it < iters; ++it)
+#pragma unroll
+      for (int k = 0; k < kChains; ++k) {
+        double d;
+        asm volatile("cvt.f64.f32 %0, %1;" : "=d"(d) : "f"(a[k]));
+        asm volatile("cvt.rn.f32.f64 %0, %1;" : "=f"(a[k]) : "d"(d));
+      }
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) acc += a[k];
   } else if (KIND == 3) {  // DFMA
     double a[kChains];
 #pragma unroll
@@ -80,7 +93,7 @@ __global__ void k_alu(long long iters, float* sink, unsigned long long* clk) {
 }  // namespace
 
 extern "C" int iontrap_alu_probe(int kind, long long iters, double* lane_ops_per_clk_per_sm, double* sm_mhz) {
-  if (kind < 0 || kind > 4 || iters < 1 || !lane_ops_per_clk_per_sm) return IONTRAP_EINVAL;
+  if (kind < 0 || kind > 5 || iters < 1 || !lane_ops_per_clk_per_sm) return IONTRAP_EINVAL;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return IONTRAP_ECUDA;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -101,6 +114,7 @@ extern "C" int iontrap_alu_probe(int kind, long long iters, double* lane_ops_per
       case 1: k_alu<1><<<blocks, threads>>>(n, sink, clk); break;
       case 2: k_alu<2><<<blocks, threads>>>(n, sink, clk); break;
       case 3: k_alu<3><<<blocks, threads>>>(n, sink, clk); break;
+      case 5: k_alu<5><<<blocks, threads>>>(n, sink, clk); break;
       default: k_alu<4><<<blocks, threads>>>(n, sink, clk); break;
     }
   };
@@ -119,7 +133,7 @@ extern "C" int iontrap_alu_probe(int kind, long long iters, double* lane_ops_per
   cudaFree(clk);
   if (e != cudaSuccess) return IONTRAP_ECUDA;
   const double mhz = hc[1] ? (double)hc[0] / (double)hc[1] * 1e3 : 0.0;
-  const double lanes_per_instr = (kind == 1 || kind == 4) ? 2.0 : 1.0;
+  const double lanes_per_instr = (kind == 1 || kind == 4 || kind == 5) ? 2.0 : 1.0;
   const double ops = (double)blocks * threads * kChains * (double)iters * lanes_per_instr;
   const double clocks = (double)ms * 1e-3 * mhz * 1e6;
   *lane_ops_per_clk_per_sm = clocks > 0 ? ops / clocks / sms : 0.0;

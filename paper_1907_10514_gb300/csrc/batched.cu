@@ -30,6 +30,9 @@ namespace cg = cooperative_groups;
 
 namespace it {
 
+// tuning table of the batched launch (iontrap_api.cu)
+bool batched_tuned_shape(int dev, long long n, int* C, int* NP);
+
 constexpr int kBThreads = 128;
 constexpr int kBWarps = kBThreads / 32;
 constexpr int kBWarpIons = 64;
@@ -468,8 +471,22 @@ struct BatchPlan {
 constexpr int kBRItemCost = 8;
 constexpr size_t kBRSmemTwo = 112 * 1024;  // two CTAs per SM (228 KB less 1 KB each reserved, static arrays)
 constexpr size_t kBRSmemOne = 226 * 1024;  // 227 KB less the static arrays
-static void brp_shape(int n, int C, BatchRpCta* t) {
+static int brp_jp(int n, int R, int np) {
+  long long q4 = ((n + np - 1) / np + 3) / 4;
+  if (R % 32 != 0 && !(q4 & 1)) ++q4;
+  return (int)(4 * q4);
+}
+
+static void brp_shape(int n, int C, int np_tuned, BatchRpCta* t) {
   const int R = (n + C - 1) / C;
+  t->R = R;
+  t->C = C;
+  // a part count from the tuning table, if it fits in a CTA's shared memory
+  if (np_tuned > 0 && np_tuned <= kBRMaxParts && brp_smem_bytes(R, np_tuned, brp_jp(n, R, np_tuned)) <= kBRSmemOne) {
+    t->NP = np_tuned;
+    t->JP = brp_jp(n, R, np_tuned);
+    return;
+  }
   for (size_t lim : {kBRSmemTwo, kBRSmemOne}) {
     long long best = -1;
     for (int np = 1; np <= kBRMaxParts; ++np) {
@@ -487,29 +504,44 @@ static void brp_shape(int n, int C, BatchRpCta* t) {
     }
     if (best >= 0) break;
   }
-  t->R = R;
-  t->C = C;
 }
 
-// Pack ensembles (sizes n[e]) into CTAs.  Above 256 ions: part-major groups of 2 CTAs up
-// to 512 ions, 4 up to 1024, 8 above, placed buddy-aligned in clusters of 8 (largest
-// first, similar sizes together).  The rest one per CTA (64 < N <= 256) or four per CTA
-// (N <= 64), heaviest first, in a grid without clusters.
-static BatchPlan plan_batch(const std::vector<long long>& n) {
+// Group shape of the part-major groups for an ensemble of n ions (256 < n <= 2048): the
+// CTAs per group C and the j-part count NP (0: the cost model of brp_shape) from the
+// tuning table of device dev (iontrap_autotune_many), else 2 CTAs up to 512 ions, 4 up to
+// 1024, 8 above.  A function of (dev, n) and the table only.
+static void brp_group(int dev, long long n, int* C, int* NP) {
+  *C = n <= 512 ? 2 : (n <= 1024 ? 4 : 8);
+  *NP = 0;
+  int tc = 0, tnp = 0;
+  if (batched_tuned_shape(dev, n, &tc, &tnp) && (tc == 2 || tc == 4 || tc == 8) && (n + tc - 1) / tc <= kBRThreads) {
+    *C = tc;
+    *NP = tnp;
+  }
+}
+
+// Pack ensembles (sizes n[e]) into CTAs.  Above 256 ions: part-major groups of C CTAs
+// (brp_group), placed buddy-aligned in clusters of 8 (largest first, similar sizes
+// together).  The rest one per CTA (64 < N <= 256) or four per CTA (N <= 64), heaviest
+// first, in a grid without clusters.
+static BatchPlan plan_batch(const std::vector<long long>& n, int dev) {
   BatchPlan plan;
   struct Job {
     int e;
     int ctas;
     long long work;
+    int np;
   };
   std::vector<Job> big, mid, small;
   for (int e = 0; e < (int)n.size(); ++e) {
     if (n[e] <= kBWarpIons) {
-      small.push_back({e, 1, n[e] * n[e]});
+      small.push_back({e, 1, n[e] * n[e], 0});
     } else if (n[e] <= kBCtaIons) {
-      mid.push_back({e, 1, n[e] * n[e]});
+      mid.push_back({e, 1, n[e] * n[e], 0});
     } else {
-      big.push_back({e, n[e] <= 512 ? 2 : (n[e] <= 1024 ? 4 : 8), n[e] * n[e]});
+      int C = 0, NP = 0;
+      brp_group(dev, n[e], &C, &NP);
+      big.push_back({e, C, n[e] * n[e], NP});
     }
   }
   auto heavier = [](const Job& a, const Job& b) { return a.ctas != b.ctas ? a.ctas > b.ctas : a.work > b.work; };
@@ -541,7 +573,7 @@ static BatchPlan plan_batch(const std::vector<long long>& n) {
   for (const Job& j : big) {
     BatchRpCta t{};
     t.e = j.e;
-    brp_shape((int)n[j.e], j.ctas, &t);
+    brp_shape((int)n[j.e], j.ctas, j.np, &t);
     const size_t smem = brp_smem_bytes(t.R, t.NP, t.JP);
     while (used % j.ctas) {
       BatchRpCta idle{};
@@ -604,6 +636,15 @@ static BatchBuffers g_bb;
 
 int batched_max_n() { return kBMaxN; }
 
+// Whether a part-major group of C CTAs with NP j-parts (0: the cost model) can hold an
+// ensemble of n ions.
+bool batched_shape_fits(long long n, int C, int NP) {
+  if (n <= kBCtaIons || n > kBMaxN || !(C == 2 || C == 4 || C == 8) || (n + C - 1) / C > kBRThreads) return false;
+  if (NP == 0) return true;
+  const int R = (int)((n + C - 1) / C);
+  return NP > 0 && NP <= kBRMaxParts && brp_smem_bytes(R, NP, brp_jp((int)n, R, NP)) <= kBRSmemOne;
+}
+
 static cudaError_t grow(void** p, size_t* cap, size_t need, size_t elem) {
   if (need <= *cap) return cudaSuccess;
   if (*p) cudaFree(*p);
@@ -626,7 +667,10 @@ cudaError_t launch_batched(const std::vector<BatchEns>& ens_in, const std::vecto
     max_steps = std::max(max_steps, steps[e]);
   }
   if (max_steps == 0) return cudaSuccess;
-  BatchPlan plan = plan_batch(n);
+  int dev = 0;
+  cudaError_t derr = cudaGetDevice(&dev);
+  if (derr != cudaSuccess) return derr;
+  BatchPlan plan = plan_batch(n, dev);
   cudaError_t err = cudaSuccess;
   if (!g_bb.done) {
     err = cudaEventCreateWithFlags(&g_bb.done, cudaEventDisableTiming);

@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <new>
@@ -22,6 +23,7 @@
 namespace it {
 // batched.cu
 int batched_max_n();
+bool batched_shape_fits(long long n, int C, int NP);
 cudaError_t launch_batched(const std::vector<BatchEns>& ens, const std::vector<long long>& steps, int K,
                            cudaStream_t stream);
 const void* step_kernel(int f64, int T, int I, int packed, int fused);
@@ -109,7 +111,7 @@ struct iontrap {
   int T = 128, I = 1, packed = 0, jsplit = 128, fused = 1, pdl = 0, use_graph = 1;
   GpShape gp{};                 // fused = 4
   RpShape rp{};                 // fused = 5
-  unsigned* d_gsync = nullptr;  // fused = 4: step and group counters (zero between launches)
+  unsigned* d_gsync = nullptr;  // fused = 4, 5: step and group counters (zero between launches)
   double* d_snap = nullptr;     // iontrap_step_record: x_{s-W}, x_{s-W+1} [2][3][n]
   StepArgs args{};
   // graph of kGraphSteps chained steps
@@ -537,11 +539,16 @@ int alloc_scratch(iontrap* h) {
   return IONTRAP_OK;
 }
 
+// One row-persistent launch of K steps on the handle's buffers.
+cudaError_t launch_rp_of(iontrap* h, const StepArgs& a, long long K, cudaStream_t st) {
+  return launch_rp(a, h->d_gsync, h->rp.W, h->rp.R, h->rp.NP, h->rp.JP, h->rp.G, K, st);
+}
+
 // Launch one step kernel with programmatic dependent launch, so that consecutive steps
 // overlap one grid's launch with the previous grid's tail.
 cudaError_t launch_step_on(iontrap* h, StepArgs& a, cudaStream_t st) {
   if (h->fused == 5 && a.mode != MODE_INIT)
-    return launch_rp(a, h->d_gsync, h->rp.W, h->rp.R, h->rp.NP, h->rp.JP, h->rp.G, 1, st);
+    return launch_rp_of(h, a, 1, st);
   if (h->fused == 4 || h->fused == 5) {
     if (h->fused == 4 && a.mode != MODE_INIT)
       return launch_gp(a, h->d_gsync, h->gp.W, h->gp.S, h->gp.G, h->gp.Lmax, 1, st);
@@ -667,6 +674,17 @@ void free_all(iontrap* h) {
 }  // namespace
 
 namespace it {
+// The batched launch's group shape for ensembles of n ions on device dev, if tuned: CTAs
+// per group and j-parts (0: the launcher's cost model).
+bool batched_tuned_shape(int dev, long long n, int* C, int* NP) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto f = g_tune.find(TuneKey{dev, IONTRAP_TUNE_BATCHED, log2_floor(n)});
+  if (f == g_tune.end()) return false;
+  *C = f->second.splits;
+  *NP = f->second.ions_per_thread;
+  return true;
+}
+
 // Give a handle the default configuration without the grid-persistent form (for callers
 // that run many simulations side by side on separate streams).
 int use_nonpersistent_default(iontrap* h) {
@@ -880,8 +898,7 @@ int iontrap_step(iontrap_t* h, int64_t n_steps) {
     while (n_steps > 0) {
       const int64_t k = std::min<int64_t>(n_steps, kGpMaxSteps);
       cudaError_t e = h->fused == 4 ? launch_gp(a, h->d_gsync, h->gp.W, h->gp.S, h->gp.G, h->gp.Lmax, k, h->stream)
-                                    : launch_rp(a, h->d_gsync, h->rp.W, h->rp.R, h->rp.NP, h->rp.JP, h->rp.G, k,
-                                                h->stream);
+                                    : launch_rp_of(h, a, k, h->stream);
       if (e != cudaSuccess) return cuda_status(h, e);
       n_steps -= k;
       h->step += k;
@@ -1102,7 +1119,7 @@ int iontrap_sync(iontrap_t* h) {
 int iontrap_state(iontrap_t* h, double* x, double* v, int64_t* step, double* t) {
   if (!h) return IONTRAP_EINVAL;
   const int st = iontrap_sync(h);
-  if (st != IONTRAP_OK && st != IONTRAP_ENONFINITE) return st;
+  if (st != IONTRAP_OK && st != IONTRAP_ENONFINITE && st != IONTRAP_ETIMEOUT) return st;
   DeviceGuard g(h->device);
   const size_t vec = 3 * (size_t)h->n * sizeof(double);
   cudaError_t e = cudaSuccess;
@@ -1170,6 +1187,21 @@ int iontrap_restore(iontrap_t* h, const double* x, const double* v, const double
   return h->status;
 }
 
+int iontrap_test_stall(iontrap_t* h, int64_t wait_limit_ns, int32_t cta, int64_t step) {
+  if (!h || wait_limit_ns < 0 || step < 0 || (h->fused != 4 && h->fused != 5)) return IONTRAP_EINVAL;
+  const int ctas = h->fused == 4 ? h->gp.G : h->rp.G;
+  if (cta >= ctas) return IONTRAP_EINVAL;
+  if (h->status) return h->status;
+  DeviceGuard g(h->device);
+  const cudaError_t e = cudaStreamSynchronize(h->stream);  // launches already queued keep their settings
+  if (e != cudaSuccess) return cuda_status(h, e);
+  h->args.wait_ns = (unsigned long long)wait_limit_ns;
+  h->args.stall_on = cta >= 0 ? 1 : 0;
+  h->args.stall_cta = cta >= 0 ? cta : 0;
+  h->args.stall_step = step;
+  return IONTRAP_OK;
+}
+
 int iontrap_trace_step(iontrap_t* h, unsigned long long* marks, int64_t cap, int64_t* n_force, int64_t* n_epi) {
   if (!h || !marks || cap < 1 || h->fused == 4) return IONTRAP_EINVAL;
   int st = iontrap_sync(h);
@@ -1187,7 +1219,7 @@ int iontrap_trace_step(iontrap_t* h, unsigned long long* marks, int64_t cap, int
     a.out = nullptr;
     a.trace = d;
     if (e == cudaSuccess)
-      e = launch_rp(a, h->d_gsync, h->rp.W, h->rp.R, h->rp.NP, h->rp.JP, h->rp.G, kRpTraceSteps, h->stream);
+      e = launch_rp_of(h, a, kRpTraceSteps, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(marks, d, nf * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cudaFree(d);
@@ -1426,13 +1458,19 @@ int iontrap_autotune(iontrap_t* h, double trial_us, iontrap_config* best, double
         GpShape gs;
         if (gp_shape(n, 0, h->p.flags, h->sms, c.threads, 2, 1, c.jsplit, &gs)) cands.push_back(c);
       }
-    // row-persistent shapes: the ions spread over every SM, that count rounded up to a
-    // power of two (parts aligned with warps), or 32 per CTA
+    // row-persistent shapes: the ions spread over every SM and the next three counts
+    // (fewer CTAs, fewer idle lanes: N = 4096 runs 28 ions per CTA faster than 27), that
+    // count rounded up to a power of two (parts aligned with warps), or 32 per CTA
     int64_t r2 = 1;
     while (r2 < cdiv(n, h->sms)) r2 *= 2;
+    std::vector<int64_t> rs;
+    for (int64_t d = 0; d < 4; ++d) rs.push_back(cdiv(n, h->sms) + d);
+    rs.push_back(r2);
+    rs.push_back(32);
+    std::sort(rs.begin(), rs.end());
+    rs.erase(std::unique(rs.begin(), rs.end()), rs.end());
     for (int W : {8, 16})
-      for (int64_t R : {cdiv(n, h->sms), r2, (int64_t)32}) {
-        if (R == r2 && r2 == cdiv(n, h->sms)) continue;
+      for (int64_t R : rs) {
         iontrap_config c{32 * W, 1, 1, (int32_t)R, 5, 0, 0};
         RpShape rs;
         if (rp_shape(n, 0, h->p.flags, h->sms, c.threads, 1, 1, R, &rs)) cands.push_back(c);
@@ -1497,6 +1535,106 @@ int iontrap_autotune(iontrap_t* h, double trial_us, iontrap_config* best, double
   return IONTRAP_OK;
 }
 
+int iontrap_autotune_many(iontrap_t* const* hs, int count, double trial_us) {
+  if (!hs || count < 1 || !(trial_us > 0)) return IONTRAP_EINVAL;
+  for (int k = 0; k < count; ++k)
+    if (!hs[k]) return IONTRAP_EINVAL;
+  // the handles the batched launch takes, as iontrap_step_many selects them
+  std::vector<iontrap_t*> hv;
+  for (int k = 0; k < count; ++k) {
+    const int st = iontrap_sync(hs[k]);
+    if (st) return st;
+    if (!hs[k]->f64 && hs[k]->n <= batched_max_n() && hs[k]->device == hs[0]->device) hv.push_back(hs[k]);
+  }
+  if (hv.empty()) return IONTRAP_OK;
+  DeviceGuard g(hv[0]->device);
+  const int dev = hv[0]->device;
+  struct Ck {
+    std::vector<double> x, v, a;
+    int64_t step = 0;
+  };
+  std::vector<Ck> ck(hv.size());
+  for (size_t i = 0; i < hv.size(); ++i) {
+    const size_t m = 3 * (size_t)hv[i]->n;
+    ck[i].x.resize(m), ck[i].v.resize(m), ck[i].a.resize(m);
+    const int st = iontrap_checkpoint(hv[i], ck[i].x.data(), ck[i].v.data(), ck[i].a.data(), &ck[i].step);
+    if (st) return st;
+  }
+  auto restore_all = [&]() -> int {
+    for (size_t i = 0; i < hv.size(); ++i) {
+      const int st = iontrap_restore(hv[i], ck[i].x.data(), ck[i].v.data(), ck[i].a.data(), ck[i].step);
+      if (st) return st;
+    }
+    return IONTRAP_OK;
+  };
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return IONTRAP_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return IONTRAP_ECUDA;
+  }
+  std::vector<int64_t> steps(hv.size());
+  // us per step of one batched launch of every handle (the batch runs on the first
+  // handle's stream)
+  auto time_batch = [&](int64_t nsteps, double* us) -> int {
+    std::fill(steps.begin(), steps.end(), nsteps);
+    if (cudaEventRecord(e0, hv[0]->stream) != cudaSuccess) return IONTRAP_ECUDA;
+    int st = iontrap_step_many(hv.data(), steps.data(), (int)hv.size());
+    if (cudaEventRecord(e1, hv[0]->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+      return IONTRAP_ECUDA;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    *us = ms * 1e3 / (double)nsteps;
+    if (!st) st = restore_all();
+    return st;
+  };
+  auto set_entry = [&](int b, int C, int NP, float us) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    iontrap_tuning_entry e{};
+    e.precision = IONTRAP_TUNE_BATCHED;
+    e.log2n = b;
+    e.threads = 256, e.ions_per_thread = NP, e.packed = 1, e.splits = C, e.fused = 6, e.pdl = 0, e.graph = 0;
+    e.us_per_step = us;
+    g_tune[TuneKey{dev, IONTRAP_TUNE_BATCHED, b}] = e;
+  };
+  // buckets of the part-major groups present (256 < n), largest first, with their largest n
+  std::map<int, int64_t, std::greater<int>> nmax;
+  for (iontrap_t* h : hv)
+    if (h->n > 256) {
+      const int b = log2_floor(h->n);
+      nmax[b] = std::max(nmax[b], h->n);
+    }
+  int st = IONTRAP_OK;
+  double us = 0.0;
+  st = time_batch(20, &us);  // warm-up and calibration
+  const int64_t nsteps = std::max<int64_t>(20, std::min<int64_t>(1000, (int64_t)(trial_us / std::max(us, 1e-3))));
+  for (const auto& bn : nmax) {
+    if (st) break;
+    const int b = bn.first;
+    std::vector<std::pair<int, int>> cands;
+    for (int C : {2, 4, 8})
+      for (int NP : {0, 2, 4, 6, 8, 12})
+        if (batched_shape_fits(bn.second, C, NP) && batched_shape_fits(std::max<int64_t>(257, 1LL << b), C, NP))
+          cands.push_back({C, NP});
+    std::vector<double> best_us(cands.size(), 1e300);
+    for (int pass = 0; pass < 2 && !st; ++pass)
+      for (size_t c = 0; c < cands.size() && !st; ++c) {
+        set_entry(b, cands[c].first, cands[c].second, 0.f);
+        st = time_batch(nsteps, &us);
+        best_us[c] = std::min(best_us[c], us);
+      }
+    if (st) break;
+    size_t bc = 0;
+    for (size_t c = 1; c < cands.size(); ++c)
+      if (best_us[c] < best_us[bc]) bc = c;
+    if (!cands.empty()) set_entry(b, cands[bc].first, cands[bc].second, (float)best_us[bc]);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!st) st = restore_all();
+  return st;
+}
+
 int iontrap_tuning_get(iontrap_tuning_entry* out, int cap, int* count) {
   if (!count || cap < 0 || (cap > 0 && !out)) return IONTRAP_EINVAL;
   int dev = 0;
@@ -1519,8 +1657,12 @@ int iontrap_tuning_put(const iontrap_tuning_entry* in, int count) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   for (int k = 0; k < count; ++k) {
     const iontrap_tuning_entry& e = in[k];
-    if ((e.precision != 0 && e.precision != 1) || e.log2n < 0 || e.log2n > 40 || e.splits < 1) return IONTRAP_EINVAL;
-    g_tune[TuneKey{dev, e.precision, e.log2n}] = e;
+    if ((e.precision < 0 || e.precision > IONTRAP_TUNE_BATCHED) || e.log2n < 0 || e.log2n > 40 || e.splits < 0)
+      return IONTRAP_EINVAL;
+    if (e.splits == 0)
+      g_tune.erase(TuneKey{dev, e.precision, e.log2n});
+    else
+      g_tune[TuneKey{dev, e.precision, e.log2n}] = e;
   }
   return IONTRAP_OK;
 }

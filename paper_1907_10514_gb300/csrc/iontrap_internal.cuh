@@ -71,6 +71,13 @@ struct StepArgs {
   int unitw;           // every ion has charge +1 e: the pair loop skips the z_j factor (exact)
   int jsplit;          // j-range per CTA (grid.y = ceil(n / jsplit))
   int nsplit;          // ceil(n / jsplit): partials per ion for the epilogue kernel
+  // failure-detection test hook of the persistent forms (iontrap_test_stall): when
+  // stall_on, CTA stall_cta withholds its arrival on the grid-wide step counter at step
+  // stall_step of every launch, so that the other CTAs' bounded waits expire
+  int stall_on;
+  int stall_cta;
+  long long stall_step;
+  unsigned long long wait_ns;  // limit of the persistent forms' bounded waits (0: kWaitLimitNs)
   TrapDev trap;
   SpeciesDev spc[IONTRAP_MAX_SPECIES];
 };

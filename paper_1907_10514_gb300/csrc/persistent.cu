@@ -40,10 +40,10 @@ __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
 
 // Wait of a persistent form's poller until *ctr >= target: the counter alone is polled,
 // the timeout flag and the clock every 64 polls.  ACQ: acquire loads (no fence needed
-// after a successful wait).  Gives up (false) after kWaitLimitNs, setting the timeout
-// flag, or when another CTA has set it.
+// after a successful wait).  Gives up (false) after limit ns, setting the timeout flag,
+// or when another CTA has set it.
 template <bool ACQ>
-__device__ __noinline__ bool poll_wait(const unsigned* ctr, unsigned target, int* err) {
+__device__ __noinline__ bool poll_wait(const unsigned* ctr, unsigned target, int* err, unsigned long long limit) {
   const unsigned long long t0 = globaltimer_ns();
   for (unsigned it = 1;; ++it) {
     unsigned c;
@@ -54,7 +54,7 @@ __device__ __noinline__ bool poll_wait(const unsigned* ctr, unsigned target, int
     if (c >= target) return true;
     if ((it & 63) == 0) {
       if (*(volatile int*)err & ERR_TIMEOUT) return false;
-      if (globaltimer_ns() - t0 > kWaitLimitNs) {
+      if (globaltimer_ns() - t0 > limit) {
         atomicOr(err, ERR_TIMEOUT);
         return false;
       }
@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(32 * W, 16 / W) k_step_f32_gp(const __grid_con
   const TrapDev& tp = A.trap;
   const long long ns0 = *A.step;
   const bool forces = A.mode == MODE_FORCES;  // one force evaluation of the current positions (K = 1)
+  const unsigned long long lim = A.wait_ns ? A.wait_ns : kWaitLimitNs;
   const bool rf = !(tp.flags & (IONTRAP_RF_OFF | IONTRAP_TRAP_OFF | IONTRAP_PSEUDO));
   if (!forces)
     for (long long k = tid; k < P.K; k += T) scos[k] = rf ? cos(tp.Omega * ((double)(ns0 + k + 1) * tp.dt)) : 0.0;
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(32 * W, 16 / W) k_step_f32_gp(const __grid_con
     // positions x_{ns+1} are complete once every CTA has finished step t-1
     bool bad = false;
     if (t > 0 && tid == poller) {
-      bad = !poll_wait<true>(ctr_step, G * (unsigned)t, A.err);
+      bad = !poll_wait<true>(ctr_step, G * (unsigned)t, A.err, lim);
     }
     if (__syncthreads_or(bad)) break;
 
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(32 * W, 16 / W) k_step_f32_gp(const __grid_con
     __syncthreads();
     if (tid == poller) {
       arrive_release(ctr_grp);
-      bad = !poll_wait<true>(ctr_grp, (unsigned)S * (unsigned)(t + 1), A.err);
+      bad = !poll_wait<true>(ctr_grp, (unsigned)S * (unsigned)(t + 1), A.err, lim);
     }
     // while the group's CTAs arrive: the owned components' force-independent terms
     // (trap, drag, laser, kick; the operations and order of accel_ext) and the next
@@ -303,13 +304,13 @@ __global__ void __launch_bounds__(32 * W, 16 / W) k_step_f32_gp(const __grid_con
       }
     }
     __syncthreads();
-    if (tid == poller) arrive_release(ctr_step);
+    if (tid == poller && !(A.stall_on && (int)blockIdx.x == A.stall_cta && t == A.stall_step)) arrive_release(ctr_step);
   }
 
   // once every CTA has counted its last step: clear the counters, advance the step index
   // (not after a wait gave up: the handle's sticky timeout status retires it)
   if (blockIdx.x == 0 && tid == poller) {
-    if (poll_wait<true>(ctr_step, G * (unsigned)P.K, A.err)) {
+    if (poll_wait<true>(ctr_step, G * (unsigned)P.K, A.err, lim)) {
       const int groups = (int)(G / (unsigned)S);
       for (int q = 0; q < groups; ++q) P.sync[32 * (1 + q)] = 0u;
       *ctr_step = 0u;
@@ -447,6 +448,7 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
   const TrapDev& tp = A.trap;
   const long long ns0 = *A.step;
   const bool forces = A.mode == MODE_FORCES;  // one force evaluation of the current positions (K = 1)
+  const unsigned long long lim = A.wait_ns ? A.wait_ns : kWaitLimitNs;
   const bool rf = !(tp.flags & (IONTRAP_RF_OFF | IONTRAP_TRAP_OFF | IONTRAP_PSEUDO));
   for (long long k = tid; k < P.K; k += 32 * W) scos[k] = rf ? cos(tp.Omega * ((double)(ns0 + k + 1) * tp.dt)) : 0.0;
   if (tid == 0)
@@ -520,7 +522,7 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
     const int rb = forces ? (int)(ns & 1) : (int)((ns + 1) & 1);
     bool bad = false;
     if (t > 0 && tid == poller) {
-      bad = !poll_wait<true>(ctr_step, G * (unsigned)t, A.err);
+      bad = !poll_wait<true>(ctr_step, G * (unsigned)t, A.err, lim);
       if (!bad) {
         // the positions the other CTAs wrote (generic stores, ordered by the counter)
         // are read by the copy engine: a proxy fence orders them before the copies.  The
@@ -579,7 +581,7 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
         hi4 = make_float4(sself[slot], sself[R + slot], sself[2 * R + slot], 0.f);
         lo4 = make_float4(sself[3 * R + slot], sself[4 * R + slot], sself[5 * R + slot], 0.f);
       }
-      if (works) bad = !mbar_wait_bounded(&bar[mybatch], (uint32_t)((t - 1) & 1), kWaitLimitNs);
+      if (works) bad = !mbar_wait_bounded(&bar[mybatch], (uint32_t)((t - 1) & 1), lim);
     }
     const float2 nh[3] = {make_float2(-hi4.x, -hi4.x), make_float2(-hi4.y, -hi4.y), make_float2(-hi4.z, -hi4.z)};
     const float2 nl[3] = {make_float2(-lo4.x, -lo4.x), make_float2(-lo4.y, -lo4.y), make_float2(-lo4.z, -lo4.z)};
@@ -624,7 +626,7 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
     if (__syncthreads_or(bad)) {  // a copy run never landed: flag, let every copy finish, stop
       if (tid == poller) {
         atomicOr(A.err, ERR_TIMEOUT);
-        for (int b = 0; b < nb; ++b) mbar_wait_bounded(&bar[b], (uint32_t)((t - 1) & 1), kWaitLimitNs);
+        for (int b = 0; b < nb; ++b) mbar_wait_bounded(&bar[b], (uint32_t)((t - 1) & 1), lim);
       }
       __syncthreads();
       break;
@@ -671,7 +673,7 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
     }
     __syncthreads();
     trace_mark(A.trace, tslot + 3);
-    if (tid == poller) arrive_release(ctr_step);
+    if (tid == poller && !(A.stall_on && (int)blockIdx.x == A.stall_cta && t == A.stall_step)) arrive_release(ctr_step);
     // the next step's trap and drag and the noise after it, while the other CTAs finish
     if (t + 1 < P.K && !forces) {
       if (own) ext = ext_det(t + 1);
@@ -684,7 +686,7 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
   // A launch that gave up on a wait leaves both alone: its FP64 state is still the one it
   // started from, and the handle's sticky timeout status retires the counter with it.
   if (blockIdx.x == 0 && tid == poller) {
-    if (poll_wait<true>(ctr_step, G * (unsigned)P.K, A.err)) {
+    if (poll_wait<true>(ctr_step, G * (unsigned)P.K, A.err, lim)) {
       *ctr_step = 0u;
       if (!forces) *A.step = ns0 + P.K;
       __threadfence();

@@ -37,6 +37,7 @@ IONTRAP_REC_VAVG = 4
 
 IONTRAP_PREC_FP32 = 0
 IONTRAP_PREC_FP64 = 1
+IONTRAP_TUNE_BATCHED = 2
 
 IONTRAP_MAX_SPECIES = 16
 
@@ -120,6 +121,7 @@ SIGNATURES = {
                                               ctypes.c_int64, _vp, _vp]),
     "iontrap_device_bytes": (ctypes.c_int, [_vp, _i64p]),
     "iontrap_autotune": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.POINTER(iontrap_config), _dp]),
+    "iontrap_autotune_many": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_double]),
     "iontrap_tuning_get": (ctypes.c_int, [ctypes.POINTER(iontrap_tuning_entry), ctypes.c_int, _ip]),
     "iontrap_tuning_put": (ctypes.c_int, [ctypes.POINTER(iontrap_tuning_entry), ctypes.c_int]),
     "iontrap_estimate_bytes": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, _i64p]),
@@ -132,6 +134,7 @@ SIGNATURES = {
     "iontrap_server_stats": (ctypes.c_int, [_vp, ctypes.POINTER(iontrap_server_counters)]),
     "iontrap_server_destroy": (None, [_vp]),
     "iontrap_trace_step": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int64, _i64p, _i64p]),
+    "iontrap_test_stall": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64]),
     "iontrap_alu_probe": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_longlong, _dp, _dp]),
 }
 
@@ -288,15 +291,22 @@ def iontrap_sync(h) -> None:
     _check(_lib.iontrap_sync(h), "iontrap_sync")
 
 
-def iontrap_state(h, n: int, x_out: Optional[np.ndarray] = None, v_out: Optional[np.ndarray] = None):
-    """Returns (x, v, step, t); x and v are (3, n) float64 arrays."""
+def iontrap_state(h, n: int, x_out: Optional[np.ndarray] = None, v_out: Optional[np.ndarray] = None,
+                  accept=()):
+    """Returns (x, v, step, t); x and v are (3, n) float64 arrays.  Statuses listed in
+    ``accept`` (e.g. IONTRAP_ETIMEOUT after a failed launch) do not raise."""
     x = np.empty((3, n)) if x_out is None else x_out
     v = np.empty((3, n)) if v_out is None else v_out
     step = ctypes.c_int64()
     t = ctypes.c_double()
-    _check(_lib.iontrap_state(h, _ptr(x), _ptr(v), ctypes.byref(step), ctypes.byref(t)),
-           "iontrap_state")
+    code = _lib.iontrap_state(h, _ptr(x), _ptr(v), ctypes.byref(step), ctypes.byref(t))
+    if code not in accept:
+        _check(code, "iontrap_state")
     return x, v, int(step.value), float(t.value)
+
+
+def iontrap_test_stall(h, wait_limit_ns: int, cta: int, step: int) -> None:
+    _check(_lib.iontrap_test_stall(h, int(wait_limit_ns), int(cta), int(step)), "iontrap_test_stall")
 
 
 def iontrap_forces(h, n: int) -> np.ndarray:
@@ -397,6 +407,12 @@ def iontrap_autotune(h, trial_us: float = 3000.0):
     us = ctypes.c_double()
     _check(_lib.iontrap_autotune(h, float(trial_us), ctypes.byref(c), ctypes.byref(us)), "iontrap_autotune")
     return (c.threads, c.ions_per_thread, c.packed, c.jsplit, c.fused, c.pdl, c.graph), us.value
+
+
+def iontrap_autotune_many(handles: Sequence, trial_us: float = 3000.0) -> None:
+    arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h
+                                             for h in handles])
+    _check(_lib.iontrap_autotune_many(arr, len(handles), float(trial_us)), "iontrap_autotune_many")
 
 
 _TUNE_FIELDS = [f for f, _ in iontrap_tuning_entry._fields_]

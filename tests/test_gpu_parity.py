@@ -482,6 +482,55 @@ def test_batched_alone_equals_mixed_bitwise(it):
         assert np.array_equal(xa, xm) and np.array_equal(va, vm)
 
 
+def test_batched_tuned_bucket_changes_the_shape(it):
+    """A tuning-table entry for an N bucket of the batched launch changes that bucket's
+    group shape (CTAs per group, j-parts): the summation order changes, so the bits do,
+    while the trajectory stays within the oracle bar and an ensemble's result stays the
+    same alone or in a mix.  iontrap_autotune_many fills the table per bucket and leaves
+    every state as it found it."""
+    sizes = [300, 700, 1500]
+    ws = [_cloud(n, 60 + n) for n in sizes]
+    base = [_run_many(it, [w], [60])[0] for w in ws]
+    for w, (x, v, step, _) in zip(ws, base):
+        q, m, p = _oracle_side(w)
+        xo, vo, _ = oracle.run(w.x0, w.v0, q, m, p, 60)
+        assert step == 60 and rel_rms(x, xo) < FP32_TRAJ_TOL
+    keep = [e for e in it.iontrap_tuning_get() if e["precision"] == it.IONTRAP_TUNE_BATCHED]
+    entries = [dict(precision=it.IONTRAP_TUNE_BATCHED, log2n=8, threads=256, ions_per_thread=3, packed=1, splits=4,
+                    fused=6, pdl=0, graph=0, us_per_step=0.0),
+               dict(precision=it.IONTRAP_TUNE_BATCHED, log2n=9, threads=256, ions_per_thread=6, packed=1, splits=8,
+                    fused=6, pdl=0, graph=0, us_per_step=0.0),
+               dict(precision=it.IONTRAP_TUNE_BATCHED, log2n=10, threads=256, ions_per_thread=2, packed=1, splits=8,
+                    fused=6, pdl=0, graph=0, us_per_step=0.0)]
+    try:
+        it.iontrap_tuning_put(entries)
+        tuned = [_run_many(it, [w], [60])[0] for w in ws]
+        mixed = _run_many(it, ws, [60, 60, 60])
+        for w, (xb, _, _, _), (xt, vt, st, _), (xm, vm, sm, _) in zip(ws, base, tuned, mixed):
+            q, m, p = _oracle_side(w)
+            xo, _, _ = oracle.run(w.x0, w.v0, q, m, p, 60)
+            assert st == sm == 60
+            assert not np.array_equal(xt, xb), w.n  # another summation order
+            assert rel_rms(xt, xo) < FP32_TRAJ_TOL, w.n
+            assert np.array_equal(xt, xm) and np.array_equal(vt, vm), w.n
+        # the autotuner over a small mix: states untouched, one entry per bucket present
+        sims = [_sim(it, w, 0) for w in ws]
+        try:
+            before = [s.checkpoint() for s in sims]
+            it.iontrap_autotune_many([s.handle for s in sims], trial_us=300.0)
+            for s, b in zip(sims, before):
+                a = s.checkpoint()
+                assert all(np.array_equal(u, v) for u, v in zip(a[:3], b[:3])) and a[3] == b[3]
+        finally:
+            for s in sims:
+                s.close()
+        got = {e["log2n"]: e for e in it.iontrap_tuning_get() if e["precision"] == it.IONTRAP_TUNE_BATCHED}
+        assert set(got) == {8, 9, 10}
+        assert all(e["splits"] in (2, 4, 8) and e["us_per_step"] > 0 for e in got.values())
+    finally:
+        it.iontrap_tuning_put([dict(e, splits=0) for e in entries] + keep)
+
+
 @pytest.mark.parametrize("cfg", [(64, 1, 0, 3), (128, 2, 1, 3), (128, 1, 0, 2), (64, 2, 1, 1)])
 def test_cluster_forms_trajectory_matches_oracle(it, cfg):
     """The cluster forms (and the last-CTA form) over 100 steps on a 3000-ion cloud,
