@@ -218,6 +218,13 @@ def run_gpu(args):
     import iongen
     import paper_1907_10514_gb300 as it
 
+    if args.only == "serve":  # the serving measurement alone (e.g. at full step budgets)
+        with ClockSampler(dev) as clk:
+            sv = serve_measurement(it, torch, args, rank, ws)
+        if rank == 0:
+            print(json.dumps({"leg": "serve", "n_gpus": ws, "serve": sv, "clocks": clk.summary()}))
+        return
+
     w = iongen.mix_n4096()
     n = w.n
     nsteps = STEPS_PER_BENCH_STEP
@@ -811,6 +818,8 @@ def main():
     ap.add_argument("--serve-fp64-cap-s", type=float, default=20.0)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--only", choices=["serve"], default=None,
+                    help="run one measurement leg alone and print its JSON (not the bench line)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
