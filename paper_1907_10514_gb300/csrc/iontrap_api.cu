@@ -399,14 +399,30 @@ void default_config(int64_t n, int f64, int sms, int* T, int* I, int* packed, in
   // Wherever its staged j fit in shared memory (n up to about 7000): the row-persistent
   // form with the ions spread over every SM measured fastest of all (us/step on GB300
   // against the choices above: n = 1024: 5.3 vs 13.4; 2048: 6.7 vs 9.7; 3000: 9.7 vs 13.0;
-  // 4096: 14.6 vs 17.3; 6000: 25.9 vs 30.6)
+  // 4096: 14.6 vs 17.3; 6000: 25.9 vs 30.6).  Ions per CTA: of ceil(n / SMs) and the next
+  // three counts, the one with the shortest j-part (the pair loop's length), then the
+  // most threads in the loop (n = 4096: 28 ions, 18 parts of 228 j and 504 busy threads,
+  // measured 12.9 against 13.3 us/step for 27 ions and 486 threads)
   if (!f64 && allow_persistent) {
     const int W = n < 2048 ? 8 : 16;
-    const int64_t R = cdiv(n, sms);
-    RpShape rs;
-    if (rp_shape(n, 0, 0, sms, 32 * W, 1, 1, R, &rs)) {
+    RpShape best{};
+    bool found = false;
+    for (int64_t R = cdiv(n, sms); R < cdiv(n, sms) + 4; ++R) {
+      RpShape rs;
+      if (!rp_shape(n, 0, 0, sms, 32 * W, 1, 1, R, &rs)) continue;
+      if (!found || rs.JP < best.JP || (rs.JP == best.JP && rs.R * rs.NP > best.R * best.NP)) best = rs;
+      found = true;
+    }
+    if (found) {
       *T = 32 * W, *I = 1, *packed = 1, *fused = 5;
-      *jsplit = (int)R;
+      *jsplit = best.R;
+    }
+    // up to 128 ions: all of them in one CTA of 16 warps, whose pair work (at most 16256
+    // pairs, ~1.2 us on one SM) costs less than a grid-wide barrier between steps
+    RpShape one;
+    if (n <= 128 && rp_shape(n, 0, 0, sms, 512, 1, 1, n, &one)) {
+      *T = 512, *I = 1, *packed = 1, *fused = 5;
+      *jsplit = (int)n;
     }
   }
 }
@@ -1467,6 +1483,7 @@ int iontrap_autotune(iontrap_t* h, double trial_us, iontrap_config* best, double
     for (int64_t d = 0; d < 4; ++d) rs.push_back(cdiv(n, h->sms) + d);
     rs.push_back(r2);
     rs.push_back(32);
+    if (n <= 170) rs.push_back(n);  // every ion in one CTA
     std::sort(rs.begin(), rs.end());
     rs.erase(std::unique(rs.begin(), rs.end()), rs.end());
     for (int W : {8, 16})

@@ -430,6 +430,10 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
   const int R = P.R, NP = P.NP, JP = P.JP;
   const long long r0 = (long long)blockIdx.x * R;
   const int Rg = (int)max(0LL, min((long long)R, n - r0));
+  // one CTA holds every ion (n <= 3 * 32 W): the new positions go straight into its own
+  // shared memory and the step ends at a CTA barrier -- no poll, no bulk copies (the step
+  // counter still counts the arrivals, and the launch's last wait checks them)
+  const bool solo = G == 1u;
   float* sall = reinterpret_cast<float*>(s_dyn);
   float* ps = sall + (size_t)NP * 7 * JP;
   float* pc = ps + NP * 3 * R;
@@ -521,7 +525,7 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
     const long long ns = ns0 + t;
     const int rb = forces ? (int)(ns & 1) : (int)((ns + 1) & 1);
     bool bad = false;
-    if (t > 0 && tid == poller) {
+    if (t > 0 && tid == poller && !solo) {
       bad = !poll_wait<true>(ctr_step, G * (unsigned)t, A.err, lim);
       if (!bad) {
         // the positions the other CTAs wrote (generic stores, ordered by the counter)
@@ -581,7 +585,7 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
         hi4 = make_float4(sself[slot], sself[R + slot], sself[2 * R + slot], 0.f);
         lo4 = make_float4(sself[3 * R + slot], sself[4 * R + slot], sself[5 * R + slot], 0.f);
       }
-      if (works) bad = !mbar_wait_bounded(&bar[mybatch], (uint32_t)((t - 1) & 1), lim);
+      if (works && !solo) bad = !mbar_wait_bounded(&bar[mybatch], (uint32_t)((t - 1) & 1), lim);
     }
     const float2 nh[3] = {make_float2(-hi4.x, -hi4.x), make_float2(-hi4.y, -hi4.y), make_float2(-hi4.z, -hi4.z)};
     const float2 nl[3] = {make_float2(-lo4.x, -lo4.x), make_float2(-lo4.y, -lo4.y), make_float2(-lo4.z, -lo4.z)};
@@ -657,6 +661,11 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
             reinterpret_cast<float*>(A.hi[rb ^ 1] + ie)[3] = sd.w;
             reinterpret_cast<float*>(A.lo[rb ^ 1] + ie)[3] = 0.0f;
           }
+        } else if (solo) {  // the next step's positions, in place (every read of them is done)
+          sall[ieo + oc * JP] = h;
+          sall[ieo + (3 + oc) * JP] = l;
+          sself[oc * R + oq] = h;
+          sself[(3 + oc) * R + oq] = l;
         } else {  // the next step's copies: part-major global, own ions in shared
           float* g = gsoa + (rb ? 0 : soa_len) + ieo;
           g[oc * JP] = h;

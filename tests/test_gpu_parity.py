@@ -597,6 +597,32 @@ def test_row_persistent_form_trajectory_matches_oracle(it, n, W, R, steps):
     assert step == steps and rel_rms(x, xo) < FP32_TRAJ_TOL and rel_rms(v, vo) < 10 * FP32_TRAJ_TOL
 
 
+@pytest.mark.parametrize("n", [1, 2, 37, 64, 100, 128, 170])
+def test_single_cta_row_persistent_form(it, n):
+    """Up to 170 ions the row-persistent form can hold every ion in one CTA, which then
+    exchanges positions through its own shared memory (no grid barrier); the default for
+    N <= 128.  Against the oracle over 100 steps, and launch splits bit for bit."""
+    w = _cloud(n, 900 + n)
+    q, m, p = _oracle_side(w)
+    xo, vo, _ = oracle.run(w.x0, w.v0, q, m, p, 100)
+    cfg = (512, 1, 1, n, 5)
+    with _sim(it, w, 0) as a, _sim(it, w, 0) as b:
+        if n <= 128:
+            assert a.config()[:5] == cfg  # the default
+        for s in (a, b):
+            s.set_config(*cfg)
+        a.step(100)
+        for k in (1, 13, 86):
+            b.step(k)
+        xa, va, sa, _ = a.state()
+        xb, vb, sb, _ = b.state()
+    assert sa == sb == 100 and np.array_equal(xa, xb) and np.array_equal(va, vb)
+    if n > 1:
+        assert rel_rms(xa, xo) < FP32_TRAJ_TOL and rel_rms(va, vo) < 10 * FP32_TRAJ_TOL
+    else:
+        assert rel_rms(xa, xo) < 1e-9
+
+
 def test_row_persistent_form_bitwise_across_launches_and_restore(it):
     """Launch splits of the row-persistent form give the bits of one launch; a checkpoint
     restored into a second handle continues bit for bit; unit-charge clouds take the loop
