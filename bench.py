@@ -51,7 +51,11 @@ NOMINAL_SM_MHZ = 2070.0
 # kernel from one ncu capture, keyed by a fingerprint of the CUDA sources the kernel is
 # built from and by its launch shape (threads, ions per thread, packed, jsplit, fused); the
 # bench reports it only while both still match, and null otherwise.
-KERNEL_DRAM_TRAFFIC = {}
+KERNEL_DRAM_TRAFFIC = {
+    # row-persistent form, 28 ions per CTA: 506 112 B read + 2 304 B written over the second
+    # 20-timestep launch of mix_n4096 (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum)
+    ("4e235356952e63db", (512, 1, 1, 28, 5)): 25420.8,
+}
 KERNEL_SOURCES = ("persistent.cu", "iontrap_internal.cuh")
 
 
@@ -355,7 +359,8 @@ def run_gpu(args):
                      "unit": "Gpair/s", "frac": achieved_gpairs / peak_gpairs,
                      "traffic": traffic,
                      "traffic_unit": "DRAM bytes per timestep (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
-                     "traffic_source": (f"ncu capture of kernel sources {fp} at this launch shape" if traffic is not None
+                     "traffic_source": (f"ncu capture (20-timestep launch) of kernel sources {fp} at this launch shape"
+                                        if traffic is not None
                                         else f"no ncu capture of kernel sources {fp} at launch shape {list(cfg[:5])}"),
                      "basis": f"{sms} SMs x {NOMINAL_SM_MHZ:.0f} MHz x {FP32_LANES_PER_SM} FP32 lanes / "
                               f"{opp} FP32 instr per ordered pair (MUFU roof "
@@ -393,9 +398,12 @@ def extra_measurements(it, torch, stream, sms, args):
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1)
+        err64 = sampled_force_error(it, s, w)
     out["fp64_form_mix_n4096"] = {"ion_steps_per_s": n * k / (ms / 1e3),
                                   "pair_interactions_per_s": n * (n - 1) * k / (ms / 1e3),
-                                  "us_per_timestep": 1e3 * ms / k, "timesteps": k}
+                                  "us_per_timestep": 1e3 * ms / k, "timesteps": k,
+                                  "force_rel_rms_vs_oracle": err64,
+                                  "error_sample": "256 ions of the final state"}
     # the same workload with species-selective cooling (Sec. 3): Ca+ laser-cooled along x on
     # top of its bath, NH3+ in a bath of its own; forces changed through iontrap_set_params
     pc = it.make_params(w.trap, precision=it.IONTRAP_PREC_FP32)
@@ -413,7 +421,9 @@ def extra_measurements(it, torch, stream, sms, args):
         ms = e0.elapsed_time(e1)
         out["mix_n4096_species_cooling"] = {"ion_steps_per_s": n * k / (ms / 1e3), "us_per_timestep": 1e3 * ms / k,
                                             "timesteps": k, "tile": list(s.config()),
-                                            "cooling": "Ca+: bath 1e5/s 1 mK + laser (1e5, 0, 0)/s; NH3+: bath 2e5/s 2 mK"}
+                                            "cooling": "Ca+: bath 1e5/s 1 mK + laser (1e5, 0, 0)/s; NH3+: bath 2e5/s 2 mK",
+                                            "force_rel_rms_vs_oracle": sampled_force_error(it, s, w),
+                                            "error_sample": "256 ions of the final state"}
     # the same workload recording x and the secular velocity (average over one RF period)
     # every RF period into a device buffer (dump + timeAvg, Sec. 3 "Writing/reading data")
     with it.Simulation(w.species, w.species_of_ion, w.x0, w.v0, pc, stream=stream) as s:
@@ -428,9 +438,14 @@ def extra_measurements(it, torch, stream, sms, args):
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1)
+        xs = s.state()[0]
+        rec_last = buf.view(k // 20, 2, 3, n)[-1, 0].cpu().numpy()
         out["mix_n4096_record_every_rf_period"] = {"ion_steps_per_s": n * k / (ms / 1e3), "us_per_timestep": 1e3 * ms / k,
                                                    "timesteps": k, "records": k // 20,
-                                                   "fields": "x and the velocity averaged over 20 steps"}
+                                                   "fields": "x and the velocity averaged over 20 steps",
+                                                   "last_record_equals_state": bool(np.array_equal(rec_last, xs)),
+                                                   "force_rel_rms_vs_oracle": sampled_force_error(it, s, w),
+                                                   "error_sample": "256 ions of the final state"}
     out.update(modes_measurements(it, stream))
     wc = iongen.crystal_n32768()
     nc = wc.n
@@ -496,10 +511,15 @@ def modes_measurements(it, stream):
     with it.Simulation([iongen.CA40], np.zeros(nh, np.uint8), xh, None, p, stream=stream) as s:
         s.hessian()
         t0 = time.perf_counter()
-        s.hessian()
+        H = s.hessian()
         wall = time.perf_counter() - t0
+    import oracle
+    q, mm, qm0 = oracle.ion_arrays([iongen.CA40], np.zeros(nh, np.uint8))
+    Ho = oracle.hessian(xh, q, mm, oracle.params(trap, qm0, oracle.PSEUDO))
     out["hessian_n2048"] = {"seconds": wall, "bytes": 9 * nh * nh * 8,
+                            "max_abs_dev_over_max_abs_vs_oracle": float(np.abs(H - Ho).max() / np.abs(Ho).max()),
                             "note": "FP64 device kernels + device-to-host copy of the 3n x 3n matrix"}
+    del H, Ho
     return out
 
 
@@ -771,12 +791,16 @@ def oracle_timing(args):
     full, and for the N = 32768 crystal 8 force evaluations plus a 10-step run."""
     import iongen
     import oracle
-    out = {"cores": oracle.threads()}
+    out = {"cores": oracle.threads(), "cpu_model": None}
     try:
-        out["cpu_model"] = next(l.split(":", 1)[1].strip() for l in open("/proc/cpuinfo")
-                                if l.lower().startswith(("model name", "cpu part")))
+        lines = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout.splitlines()
+        out["cpu_model"] = next(l.split(":", 1)[1].strip() for l in lines if l.startswith("Model name"))
     except Exception:
-        out["cpu_model"] = None
+        try:
+            out["cpu_model"] = next(l.split(":", 1)[1].strip() for l in open("/proc/cpuinfo")
+                                    if l.lower().startswith(("model name", "cpu part")))
+        except Exception:
+            pass
     for name, gen in (("plain_n64", iongen.plain_n64), ("mix_n4096", iongen.mix_n4096)):
         w = gen()
         q, m, qm0 = oracle.ion_arrays(w.species, w.species_of_ion)

@@ -447,7 +447,8 @@ int iontrap_forces_noalloc(const iontrap_species *species, int n_species, const 
  * and its step index is not advanced; in form 5 the FP64 state is the one the launch
  * started from, in form 4 it may hold some of the launch's steps.  cta < 0 turns the stall
  * off.  Synchronous (waits for queued work).  EINVAL when the handle is not in form 4 or
- * 5, or cta is not below the launch's CTA count. */
+ * 5, when its launch has a single CTA (form 5 up to 170 ions: no cross-CTA wait), or when
+ * cta is not below the launch's CTA count. */
 int iontrap_test_stall(iontrap_t *h, int64_t wait_limit_ns, int32_t cta, int64_t step);
 
 /* Profiling hook: run ONE step with per-CTA phase timestamps (%globaltimer, ns) and copy

@@ -417,10 +417,11 @@ void default_config(int64_t n, int f64, int sms, int* T, int* I, int* packed, in
       *T = 32 * W, *I = 1, *packed = 1, *fused = 5;
       *jsplit = best.R;
     }
-    // up to 128 ions: all of them in one CTA of 16 warps, whose pair work (at most 16256
-    // pairs, ~1.2 us on one SM) costs less than a grid-wide barrier between steps
+    // up to 112 ions: all of them in one CTA of 16 warps, whose pair work costs less than
+    // a grid-wide barrier between steps (us/step, one CTA against the ions spread over
+    // every SM: n = 16: 2.8 vs 5.7; 64: 3.3 vs 5.7; 100: 5.0 vs 5.8; 128: 5.8 vs 5.8)
     RpShape one;
-    if (n <= 128 && rp_shape(n, 0, 0, sms, 512, 1, 1, n, &one)) {
+    if (n <= 112 && rp_shape(n, 0, 0, sms, 512, 1, 1, n, &one)) {
       *T = 512, *I = 1, *packed = 1, *fused = 5;
       *jsplit = (int)n;
     }
@@ -1206,7 +1207,7 @@ int iontrap_restore(iontrap_t* h, const double* x, const double* v, const double
 int iontrap_test_stall(iontrap_t* h, int64_t wait_limit_ns, int32_t cta, int64_t step) {
   if (!h || wait_limit_ns < 0 || step < 0 || (h->fused != 4 && h->fused != 5)) return IONTRAP_EINVAL;
   const int ctas = h->fused == 4 ? h->gp.G : h->rp.G;
-  if (cta >= ctas) return IONTRAP_EINVAL;
+  if (cta >= ctas || ctas < 2) return IONTRAP_EINVAL;  // one CTA waits on no other
   if (h->status) return h->status;
   DeviceGuard g(h->device);
   const cudaError_t e = cudaStreamSynchronize(h->stream);  // launches already queued keep their settings

@@ -431,8 +431,8 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
   const long long r0 = (long long)blockIdx.x * R;
   const int Rg = (int)max(0LL, min((long long)R, n - r0));
   // one CTA holds every ion (n <= 3 * 32 W): the new positions go straight into its own
-  // shared memory and the step ends at a CTA barrier -- no poll, no bulk copies (the step
-  // counter still counts the arrivals, and the launch's last wait checks them)
+  // shared memory and the step ends at a CTA barrier -- no step counter, no poll, no bulk
+  // copies
   const bool solo = G == 1u;
   float* sall = reinterpret_cast<float*>(s_dyn);
   float* ps = sall + (size_t)NP * 7 * JP;
@@ -682,7 +682,8 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
     }
     __syncthreads();
     trace_mark(A.trace, tslot + 3);
-    if (tid == poller && !(A.stall_on && (int)blockIdx.x == A.stall_cta && t == A.stall_step)) arrive_release(ctr_step);
+    if (tid == poller && !solo && !(A.stall_on && (int)blockIdx.x == A.stall_cta && t == A.stall_step))
+      arrive_release(ctr_step);
     // the next step's trap and drag and the noise after it, while the other CTAs finish
     if (t + 1 < P.K && !forces) {
       if (own) ext = ext_det(t + 1);
@@ -695,7 +696,7 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
   // A launch that gave up on a wait leaves both alone: its FP64 state is still the one it
   // started from, and the handle's sticky timeout status retires the counter with it.
   if (blockIdx.x == 0 && tid == poller) {
-    if (poll_wait<true>(ctr_step, G * (unsigned)P.K, A.err, lim)) {
+    if (solo || poll_wait<true>(ctr_step, G * (unsigned)P.K, A.err, lim)) {
       *ctr_step = 0u;
       if (!forces) *A.step = ns0 + P.K;
       __threadfence();

@@ -601,13 +601,13 @@ def test_row_persistent_form_trajectory_matches_oracle(it, n, W, R, steps):
 def test_single_cta_row_persistent_form(it, n):
     """Up to 170 ions the row-persistent form can hold every ion in one CTA, which then
     exchanges positions through its own shared memory (no grid barrier); the default for
-    N <= 128.  Against the oracle over 100 steps, and launch splits bit for bit."""
+    N <= 112.  Against the oracle over 100 steps, and launch splits bit for bit."""
     w = _cloud(n, 900 + n)
     q, m, p = _oracle_side(w)
     xo, vo, _ = oracle.run(w.x0, w.v0, q, m, p, 100)
     cfg = (512, 1, 1, n, 5)
     with _sim(it, w, 0) as a, _sim(it, w, 0) as b:
-        if n <= 128:
+        if n <= 112:
             assert a.config()[:5] == cfg  # the default
         for s in (a, b):
             s.set_config(*cfg)
