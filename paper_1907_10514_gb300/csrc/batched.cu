@@ -282,6 +282,7 @@ __global__ void __launch_bounds__(kBRThreads, 2)
     k_batched_rp(BatchEns* __restrict__ E, const BatchRpCta* __restrict__ J, int K) {
   extern __shared__ __align__(16) float4 sm[];
   __shared__ double s_springs[IONTRAP_MAX_SPECIES][3];
+  __shared__ int s_next;  // the step's next (ion, part) item past the first round
   const int tid = threadIdx.x;
   const BatchRpCta job = J[blockIdx.x];
   BatchEns* ens = job.e >= 0 ? E + job.e : nullptr;
@@ -351,6 +352,7 @@ __global__ void __launch_bounds__(kBRThreads, 2)
                               : cos(tp.Omega * ((double)(n0 + k + 1) * tp.dt));
       trap_springs(tp, ens->spc[tid], cosv, s_springs[tid]);
     }
+    if (tid == 0) s_next = kBRThreads;
     __syncthreads();
     // the force-independent part of the acceleration, ahead of the pair work
     double ext[3];
@@ -358,7 +360,10 @@ __global__ void __launch_bounds__(kBRThreads, 2)
     if (active) {
       const float* sb = buf + cur * blen;
       const bool unitw = ens->unitw != 0;
-      for (int m = tid; m < R * NP; m += kBRThreads) {
+      // the first round of items by thread index, the rest to whichever thread is free
+      // (the owners start late: they evaluate the trap, drag and noise first); each item's
+      // sum is its own, so the bits do not depend on which thread takes it
+      for (int m = tid; m < R * NP; m = atomicAdd(&s_next, 1)) {
         const int p = m / R, s = m - p * R;
         const int i = r0 + s;
         if (i >= n) continue;
