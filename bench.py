@@ -333,6 +333,13 @@ def run_gpu(args):
 
     fp = kernel_fingerprint()
     traffic = KERNEL_DRAM_TRAFFIC.get((fp, tuple(cfg[:5])))
+    # the same roof at the pipe rates the probe measured for this loop's packed mix
+    # (opp - 5 FADD2/FMUL2 lane-ops at the FADD2 rate, 5 FFMA2 at the FFMA2 rate per pair)
+    measured_roof = None
+    pr = extra.get("alu_probe_lane_ops_per_clk_per_sm") if extra else None
+    if pr and pr.get("fadd2") and pr.get("ffma2"):
+        lanes = opp / ((opp - 5) / pr["fadd2"] + 5 / pr["ffma2"])
+        measured_roof = sms * NOMINAL_SM_MHZ * 1e6 * lanes / opp / 1e9
     peaks = _peaks()
     line = {
         "metric": "ion-steps/s", "value": value, "unit": "ion-steps/s", "n_gpus": ws,
@@ -367,6 +374,10 @@ def run_gpu(args):
                               f"{MUFU_PER_SM}/clk/SM not binding); achieved = N(N-1) per timestep / "
                               "mean time per timestep over the timed region",
                      "peak_source": "derived from SM count, nominal max SM clock and FP32 lane count",
+                     "peak_at_measured_pipe_rates": measured_roof,
+                     "frac_of_measured_pipe_rates": (achieved_gpairs / measured_roof) if measured_roof else None,
+                     "measured_pipe_rates_basis": "the loop's packed mix (FADD2/FMUL2 and 5 FFMA2 per pair) at the "
+                                                  "lane rates iontrap_alu_probe measured in this run",
                      "hbm_peak_gbs_measured": peaks.get("hbm_gbs")},
         "clocks": clk.summary(),
     }

@@ -360,7 +360,9 @@ void default_config(int64_t n, int f64, int sms, int* T, int* I, int* packed, in
   // least two CTAs per SM) and a small preference for fewer splits (less partial
   // traffic); at most 64 splits, at least 32 j per split.
   const int64_t iblocks = cdiv(n, (int64_t)(*T) * (*I));
-  const int64_t s_max = std::max<int64_t>(1, std::min<int64_t>(64, n / 32));
+  // (the FP64 form, whose pair term runs at the FP64 rate, spreads small n more thinly:
+  // at least 8 j per split instead of 32)
+  const int64_t s_max = std::max<int64_t>(1, std::min<int64_t>(64, n / (f64 ? 8 : 32)));
   int64_t S = 1;
   double best = -1e30;
   for (int64_t cand = 1; cand <= s_max; ++cand) {
@@ -374,6 +376,9 @@ void default_config(int64_t n, int f64, int sms, int* T, int* I, int* packed, in
       S = cand;
     }
   }
+  // the FP64 form at small n: every split it may take (its pair term is latency-bound on
+  // few SMs; n = 64: 8 CTAs of 8 j instead of one)
+  if (f64 && iblocks * s_max <= sms) S = s_max;
   int64_t js = cdiv(n, S);
   if (f64) js = std::min<int64_t>(js, kMaxJsplitF64);
   if (!*fused && cdiv(n, js) > kMaxSplitsUnfused) js = cdiv(n, kMaxSplitsUnfused);
@@ -1446,7 +1451,7 @@ int iontrap_autotune(iontrap_t* h, double trial_us, iontrap_config* best, double
     std::sort(splits.begin(), splits.end());
     splits.erase(std::unique(splits.begin(), splits.end()), splits.end());
     for (int64_t S : splits) {
-      if (S < 1 || S > 64 || S > std::max<int64_t>(1, n / 32)) continue;
+      if (S < 1 || S > 64 || S > std::max<int64_t>(1, n / (h->f64 ? 8 : 32))) continue;
       int64_t js = cdiv(n, S);
       if (h->f64 && js > kMaxJsplitF64) continue;
       for (int fused = 2; fused >= (h->f64 ? 1 : 0); --fused) {
