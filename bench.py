@@ -595,10 +595,10 @@ def aggregate_batched(parts):
             "launches_per_rank": 2 * ((steps + 999) // 1000)}
 
 
-def _serve_run(it, torch, work, arrivals, budget_bytes, keep=()):
+def _serve_run(it, torch, work, arrivals, budget_bytes, keep=(), chunk_steps=100):
     """Submit each request at its arrival time (s after the start) to a fresh serving
     loop and poll it; returns (latencies s, wall s, {index: final x} for ``keep``)."""
-    srv = it.iontrap_server_create(mem_budget_bytes=budget_bytes, max_resident=4096, chunk_steps=100)
+    srv = it.iontrap_server_create(mem_budget_bytes=budget_bytes, max_resident=4096, chunk_steps=chunk_steps)
     lat = [None] * len(work)
     kept, index, ns = {}, {}, {}
     try:
@@ -691,14 +691,14 @@ def serve_measurement(it, torch, args, rank=0, world=1):
     budget = args.serve_budget_mb << 20
     # sampled results whose error against the oracle is stated (their final state's forces)
     keep = set(np.random.default_rng(11).choice(len(work), min(6, len(work)), replace=False).tolist())
-    lat, wall, kept = _serve_run(it, torch, work, arrivals, budget, keep)
+    lat, wall, kept = _serve_run(it, torch, work, arrivals, budget, keep, args.serve_chunk_steps)
     cap_mine = sum(pairs_of) / wall
     # the companion run: the same requests, arrivals stretched so that the offered load is
     # 0.7 of the capacity the first run sustained
     span = max(arrivals) if arrivals else 0.0
     stretch = (sum(pairs_of) / (0.7 * cap_mine)) / span if span > 0 else 1.0
     arr07 = [a * stretch for a in arrivals]
-    lat07, wall07, _ = _serve_run(it, torch, work, arr07, budget)
+    lat07, wall07, _ = _serve_run(it, torch, work, arr07, budget, (), args.serve_chunk_steps)
     lat64, wall64 = _fifo_fp64(it, torch, work, arrivals, args.serve_fp64_cap_s)
     errs = []
     for i, (x, step, status) in sorted(kept.items()):
@@ -722,7 +722,7 @@ def serve_measurement(it, torch, args, rank=0, world=1):
         return None
     meta = {"requests": K, "step_scale": scale, "mem_budget_bytes": budget, "full_stream_requests": len(full),
             "full_stream_offered_pairs_per_s": full_pairs / full[-1].arrival_s, "arrival_span_s": reqs[-1].arrival_s,
-            "fp64_cap_s": args.serve_fp64_cap_s}
+            "fp64_cap_s": args.serve_fp64_cap_s, "chunk_steps": args.serve_chunk_steps}
     return aggregate_serve(parts, meta)
 
 
@@ -755,7 +755,8 @@ def aggregate_serve(parts, meta):
     return {"requests": meta["requests"], "ranks": len(parts), "requests_per_rank": [p["n"] for p in parts],
             "step_scale": meta["step_scale"],
             "step_budgets": f"the stream's budgets (1e3 .. 1e5) divided by {meta['step_scale']:g}",
-            "mem_budget_bytes": meta["mem_budget_bytes"], "full_stream_requests": meta["full_stream_requests"],
+            "mem_budget_bytes": meta["mem_budget_bytes"], "chunk_steps": meta.get("chunk_steps"),
+            "full_stream_requests": meta["full_stream_requests"],
             "full_stream_offered_pairs_per_s": meta["full_stream_offered_pairs_per_s"],
             "unstable_trap_redraws": sum(p["redraws"] for p in parts),
             "at_generated_arrivals": primary, "at_0.7_capacity": comp, "fp64_fifo_same_requests": fifo,
@@ -851,6 +852,7 @@ def main():
     ap.add_argument("--serve-step-scale", type=float, default=20.0)
     ap.add_argument("--serve-budget-mb", type=int, default=2048)
     ap.add_argument("--serve-fp64-cap-s", type=float, default=20.0)
+    ap.add_argument("--serve-chunk-steps", type=int, default=100)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--only", choices=["serve"], default=None,
