@@ -258,8 +258,9 @@ int iontrap_restore(iontrap_t *h, const double *x, const double *v, const double
  * batched ensemble's result depends only on its own inputs: it is bitwise the same
  * alone or in any mix (its summation order differs from iontrap_step's, so the two
  * agree to the FP32 force tolerance, not bit for bit).  Returns the first failing
- * handle's status.  Calls on different streams share one set of launch tables and are
- * serialised by the library. */
+ * handle's status.  The launch runs on the stream of the first batched handle; the
+ * library keeps one set of launch tables per stream, so calls on different streams run
+ * side by side, and calls on one stream are ordered. */
 int iontrap_step_many(iontrap_t *const *hs, const int64_t *n_steps, int count);
 
 /* Free the handle's device memory, graph and owned stream.  NULL is a no-op. */
@@ -375,8 +376,10 @@ int iontrap_estimate_bytes(int64_t n, int precision, int64_t *bytes);
  * iontrap_server_poll is one scheduling round: retire requests whose last chunk
  * finished (final state copied to the host, memory returned), admit waiting requests
  * that fit, and enqueue the next chunk (chunk_steps) of every idle resident request --
- * FP32-form requests with n <= 2048 together through the batched kernel on the
- * server's stream, the others each on a stream of its own, so the work overlaps.  A
+ * FP32-form requests with n <= 2048 through the batched kernel, one launch per size class
+ * (up to 64, 256, 512, 1024, 2048 ions) on a stream of its own, smaller classes at higher
+ * stream priority, so that a small request's chunk does not wait for a large one's; the
+ * others each on a stream of their own -- so the work overlaps.  A
  * request's result does not depend on what else is resident (batched ones are bitwise
  * independent of the mix).  Poll is non-blocking except for the host copies of
  * admission and retirement.  A server and its requests are used from one host thread. */

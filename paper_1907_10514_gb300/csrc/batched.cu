@@ -22,6 +22,10 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <utility>
 #include <vector>
 
 #include "iontrap_internal.cuh"
@@ -624,7 +628,8 @@ static BatchPlan plan_batch(const std::vector<long long>& n, int dev) {
   return plan;
 }
 
-// Device buffers of the batched launcher, grown on demand (one set per process).
+// Device buffers of the batched launcher, grown on demand: one set per (device, calling
+// stream), so that batched launches on different streams run side by side.
 struct BatchBuffers {
   BatchEns* d_ens = nullptr;
   size_t ens_cap = 0;
@@ -636,8 +641,17 @@ struct BatchBuffers {
   cudaEvent_t fork = nullptr, join = nullptr;
   cudaEvent_t done = nullptr;   // recorded after the previous launches, which read the tables
   bool pending = false;
+  std::mutex mu;                // one call at a time uses a set
 };
-static BatchBuffers g_bb;
+static std::mutex g_bb_mu;
+static std::map<std::pair<int, cudaStream_t>, std::unique_ptr<BatchBuffers>> g_bbs;
+
+static BatchBuffers& buffers_for(int dev, cudaStream_t stream) {
+  std::lock_guard<std::mutex> lock(g_bb_mu);
+  std::unique_ptr<BatchBuffers>& b = g_bbs[{dev, stream}];
+  if (!b) b.reset(new BatchBuffers());
+  return *b;
+}
 
 int batched_max_n() { return kBMaxN; }
 
@@ -676,16 +690,20 @@ cudaError_t launch_batched(const std::vector<BatchEns>& ens_in, const std::vecto
   cudaError_t derr = cudaGetDevice(&dev);
   if (derr != cudaSuccess) return derr;
   BatchPlan plan = plan_batch(n, dev);
+  BatchBuffers& g_bb = buffers_for(dev, stream);
+  std::lock_guard<std::mutex> set_lock(g_bb.mu);
   cudaError_t err = cudaSuccess;
   if (!g_bb.done) {
+    int prio = 0;  // the side stream runs at the calling stream's priority
+    if (stream) cudaStreamGetPriority(stream, &prio);
     err = cudaEventCreateWithFlags(&g_bb.done, cudaEventDisableTiming);
     if (err == cudaSuccess) err = cudaEventCreateWithFlags(&g_bb.fork, cudaEventDisableTiming);
     if (err == cudaSuccess) err = cudaEventCreateWithFlags(&g_bb.join, cudaEventDisableTiming);
-    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&g_bb.side, cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaStreamCreateWithPriority(&g_bb.side, cudaStreamNonBlocking, prio);
     if (err != cudaSuccess) return err;
   }
-  // The tables are shared by all calls: wait until the previous launches, which may run
-  // on another (possibly since destroyed) stream, have finished reading them.
+  // The tables of this stream are shared by its calls: wait until the previous launches
+  // have finished reading them.
   if (g_bb.pending) {
     err = cudaEventSynchronize(g_bb.done);
     if (err != cudaSuccess) return err;

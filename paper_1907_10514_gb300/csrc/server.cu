@@ -9,13 +9,16 @@
 //      memory returned to the budget;
 //   2. waiting requests are admitted, first come first served, while they fit;
 //   3. every idle resident request gets its next chunk of steps: requests the batched
-//      kernel accepts (FP32 form, N <= 2048) go together into one iontrap_step_many on
-//      the server's batch stream; the others each run on their own stream, so their work
-//      overlaps with the batch and with each other.
+//      kernel accepts (FP32 form, N <= 2048) go into one iontrap_step_many per size class
+//      (up to 64, 256, 512, 1024 and 2048 ions), each class on a stream of its own --
+//      smaller classes at higher stream priority -- so that a small request's chunk does
+//      not wait for a large one's; the others each run on their own stream, so their work
+//      overlaps with the batches and with each other.
 // A request's trajectory does not depend on what else is resident: batched requests are
 // bitwise independent of the mix, the others run alone on their stream.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <deque>
@@ -52,6 +55,7 @@ struct Request {
   iontrap_t* h = nullptr;
   cudaStream_t own = nullptr;  // stream of a request stepped on its own
   bool batched = false;
+  int lane = 0;  // batched size class
   int64_t bytes = 0;
   std::shared_ptr<Event> ev;
   int status = IONTRAP_OK;
@@ -68,14 +72,22 @@ int64_t estimate_bytes(int64_t n, int precision) {
 
 }  // namespace
 
+// Batched size classes: the largest ensemble of each (ions).
+constexpr int kLanes = 5;
+constexpr int64_t kLaneMax[kLanes] = {64, 256, 512, 1024, 2048};
+
+struct Lane {
+  cudaStream_t stream = nullptr;
+  std::shared_ptr<Event> ev;  // the class's batch in flight
+  bool inflight = false;
+};
+
 struct iontrap_server {
   iontrap_server_config cfg{};
-  cudaStream_t batch = nullptr;
+  Lane lanes[kLanes];
   std::deque<std::unique_ptr<Request>> waiting;
   std::vector<std::unique_ptr<Request>> resident;
   std::map<int64_t, std::unique_ptr<Request>> completed;
-  std::shared_ptr<Event> batch_ev;
-  int64_t batch_inflight = 0;
   int64_t next_id = 1;
   int64_t bytes_in_use = 0;
   int64_t completed_total = 0;
@@ -111,9 +123,16 @@ int iontrap_server_create(const iontrap_server_config* cfg, iontrap_server_t** o
   if (s->cfg.mem_budget_bytes <= 0) s->cfg.mem_budget_bytes = (int64_t)2 << 30;
   if (s->cfg.max_resident <= 0) s->cfg.max_resident = 4096;
   if (s->cfg.chunk_steps <= 0) s->cfg.chunk_steps = 100;
-  if (cudaStreamCreateWithFlags(&s->batch, cudaStreamNonBlocking) != cudaSuccess) {
-    delete s;
-    return IONTRAP_ECUDA;
+  // stream priorities: the smallest class highest (lower numbers are higher priorities)
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) least = greatest = 0;
+  for (int c = 0; c < kLanes; ++c) {
+    const int prio = std::min(least, greatest + c);
+    if (cudaStreamCreateWithPriority(&s->lanes[c].stream, cudaStreamNonBlocking, prio) != cudaSuccess) {
+      for (int d = 0; d < c; ++d) cudaStreamDestroy(s->lanes[d].stream);
+      delete s;
+      return IONTRAP_ECUDA;
+    }
   }
   *out = s;
   return IONTRAP_OK;
@@ -137,7 +156,8 @@ int iontrap_server_submit(iontrap_server_t* s, const iontrap_species* species, i
   }
   r->p = *p;
   r->steps = n_steps;
-  r->batched = p->precision == IONTRAP_PREC_FP32 && n <= 2048;
+  r->batched = p->precision == IONTRAP_PREC_FP32 && n <= kLaneMax[kLanes - 1];
+  while (r->lane + 1 < kLanes && n > kLaneMax[r->lane]) ++r->lane;
   r->bytes = estimate_bytes(n, p->precision);
   *id = r->id;
   s->waiting.push_back(std::move(r));
@@ -152,11 +172,12 @@ int iontrap_server_poll(iontrap_server_t* s, int64_t* completed_ids, int64_t cap
     ++*n_completed;
   };
   // 1. finished chunks
-  if (s->batch_inflight && cudaEventQuery(s->batch_ev->ev) == cudaSuccess) s->batch_inflight = 0;
+  for (Lane& l : s->lanes)
+    if (l.inflight && cudaEventQuery(l.ev->ev) == cudaSuccess) l.inflight = false;
   for (size_t k = 0; k < s->resident.size();) {
     auto& r = s->resident[k];
     if (r->inflight) {
-      const bool fin = r->batched ? (s->batch_inflight == 0) : (cudaEventQuery(r->ev->ev) == cudaSuccess);
+      const bool fin = r->batched ? !s->lanes[r->lane].inflight : (cudaEventQuery(r->ev->ev) == cudaSuccess);
       if (fin) {
         r->done += r->inflight;
         r->inflight = 0;
@@ -179,7 +200,7 @@ int iontrap_server_poll(iontrap_server_t* s, int64_t* completed_ids, int64_t cap
          (s->bytes_in_use + s->waiting.front()->bytes <= s->cfg.mem_budget_bytes || s->resident.empty())) {
     auto r = std::move(s->waiting.front());
     s->waiting.pop_front();
-    cudaStream_t st = s->batch;
+    cudaStream_t st = s->lanes[r->lane].stream;
     if (!r->batched) {
       if (cudaStreamCreateWithFlags(&r->own, cudaStreamNonBlocking) != cudaSuccess) r->status = IONTRAP_ECUDA;
       st = r->own;
@@ -202,13 +223,16 @@ int iontrap_server_poll(iontrap_server_t* s, int64_t* completed_ids, int64_t cap
     s->bytes_in_use += r->bytes;
     s->resident.push_back(std::move(r));
   }
-  // 3. next chunks: the batched group together, the others each on its stream
-  if (!s->batch_inflight) {
+  // 3. next chunks: each batched size class together on its stream, the others each on
+  // its own stream
+  for (int c = 0; c < kLanes; ++c) {
+    Lane& l = s->lanes[c];
+    if (l.inflight) continue;
     std::vector<iontrap_t*> hs;
     std::vector<int64_t> ns;
     std::vector<Request*> rs;
     for (auto& r : s->resident)
-      if (r->batched && !r->inflight && r->done < r->steps) {
+      if (r->batched && r->lane == c && !r->inflight && r->done < r->steps) {
         hs.push_back(r->h);
         ns.push_back(std::min<int64_t>(s->cfg.chunk_steps, r->steps - r->done));
         rs.push_back(r.get());
@@ -216,9 +240,9 @@ int iontrap_server_poll(iontrap_server_t* s, int64_t* completed_ids, int64_t cap
     if (!hs.empty()) {
       const int st = iontrap_step_many(hs.data(), ns.data(), (int)hs.size());
       auto ev = std::make_shared<Event>();
-      cudaEventRecord(ev->ev, s->batch);
-      s->batch_ev = ev;
-      s->batch_inflight = 1;
+      cudaEventRecord(ev->ev, l.stream);
+      l.ev = ev;
+      l.inflight = true;
       for (size_t k = 0; k < rs.size(); ++k) {
         rs[k]->inflight = ns[k];
         if (st && !rs[k]->status) rs[k]->status = st;
@@ -264,14 +288,16 @@ int iontrap_server_stats(const iontrap_server_t* s, iontrap_server_counters* out
 
 void iontrap_server_destroy(iontrap_server_t* s) {
   if (!s) return;
-  cudaStreamSynchronize(s->batch);
+  for (Lane& l : s->lanes) cudaStreamSynchronize(l.stream);
   for (auto& r : s->resident) {
     if (r->own) cudaStreamSynchronize(r->own);
     if (r->h) iontrap_destroy(r->h);
     if (r->own) cudaStreamDestroy(r->own);
   }
-  s->batch_ev.reset();
-  cudaStreamDestroy(s->batch);
+  for (Lane& l : s->lanes) {
+    l.ev.reset();
+    cudaStreamDestroy(l.stream);
+  }
   delete s;
 }
 
