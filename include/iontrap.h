@@ -259,8 +259,9 @@ int iontrap_restore(iontrap_t *h, const double *x, const double *v, const double
  * alone or in any mix (its summation order differs from iontrap_step's, so the two
  * agree to the FP32 force tolerance, not bit for bit).  Returns the first failing
  * handle's status.  The launch runs on the stream of the first batched handle; the
- * library keeps one set of launch tables per stream, so calls on different streams run
- * side by side, and calls on one stream are ordered. */
+ * library keeps a set of launch tables for each of the last 16 streams used, so calls on
+ * different streams run side by side (a 17th stream waits for the least recently used
+ * set's launches), and calls on one stream are ordered. */
 int iontrap_step_many(iontrap_t *const *hs, const int64_t *n_steps, int count);
 
 /* Free the handle's device memory, graph and owned stream.  NULL is a no-op. */

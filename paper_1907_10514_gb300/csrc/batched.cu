@@ -22,10 +22,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
-#include <map>
-#include <memory>
 #include <mutex>
-#include <utility>
 #include <vector>
 
 #include "iontrap_internal.cuh"
@@ -642,15 +639,52 @@ struct BatchBuffers {
   cudaEvent_t done = nullptr;   // recorded after the previous launches, which read the tables
   bool pending = false;
   std::mutex mu;                // one call at a time uses a set
+  int dev = -1;                 // owner of the set: (device, stream), and when it was last used
+  cudaStream_t stream = nullptr;
+  unsigned long long used = 0;
 };
+// At most kBatchSets sets; a stream without one takes the least recently used set, which
+// first waits for the launches that read its tables (and gets a side stream of the new
+// stream's priority).
+constexpr int kBatchSets = 16;
 static std::mutex g_bb_mu;
-static std::map<std::pair<int, cudaStream_t>, std::unique_ptr<BatchBuffers>> g_bbs;
+static BatchBuffers g_bbs[kBatchSets];
+static unsigned long long g_bb_clock = 0;
 
 static BatchBuffers& buffers_for(int dev, cudaStream_t stream) {
   std::lock_guard<std::mutex> lock(g_bb_mu);
-  std::unique_ptr<BatchBuffers>& b = g_bbs[{dev, stream}];
-  if (!b) b.reset(new BatchBuffers());
-  return *b;
+  BatchBuffers* pick = nullptr;
+  for (BatchBuffers& b : g_bbs)
+    if (b.dev == dev && b.stream == stream) pick = &b;
+  if (!pick) {
+    pick = &g_bbs[0];
+    for (BatchBuffers& b : g_bbs)
+      if (b.used < pick->used) pick = &b;
+    std::lock_guard<std::mutex> set_lock(pick->mu);
+    if (pick->pending) cudaEventSynchronize(pick->done);
+    pick->pending = false;
+    if (pick->dev != dev && pick->done) {  // buffers of another device: start afresh on this one
+      int cur = -1;
+      cudaGetDevice(&cur);
+      cudaSetDevice(pick->dev);
+      cudaFree(pick->d_ens), cudaFree(pick->d_cta), cudaFree(pick->d_rp);
+      cudaStreamDestroy(pick->side);
+      cudaEventDestroy(pick->fork), cudaEventDestroy(pick->join), cudaEventDestroy(pick->done);
+      cudaSetDevice(cur);
+      pick->d_ens = nullptr, pick->d_cta = nullptr, pick->d_rp = nullptr;
+      pick->ens_cap = pick->cta_cap = pick->rp_cap = 0;
+      pick->side = nullptr, pick->fork = pick->join = pick->done = nullptr;
+    } else if (pick->side) {  // same device: the side stream takes the new stream's priority
+      cudaStreamDestroy(pick->side);
+      int prio = 0;
+      if (stream) cudaStreamGetPriority(stream, &prio);
+      if (cudaStreamCreateWithPriority(&pick->side, cudaStreamNonBlocking, prio) != cudaSuccess) pick->side = nullptr;
+    }
+    pick->dev = dev;
+    pick->stream = stream;
+  }
+  pick->used = ++g_bb_clock;
+  return *pick;
 }
 
 int batched_max_n() { return kBMaxN; }
@@ -694,12 +728,15 @@ cudaError_t launch_batched(const std::vector<BatchEns>& ens_in, const std::vecto
   std::lock_guard<std::mutex> set_lock(g_bb.mu);
   cudaError_t err = cudaSuccess;
   if (!g_bb.done) {
-    int prio = 0;  // the side stream runs at the calling stream's priority
-    if (stream) cudaStreamGetPriority(stream, &prio);
     err = cudaEventCreateWithFlags(&g_bb.done, cudaEventDisableTiming);
     if (err == cudaSuccess) err = cudaEventCreateWithFlags(&g_bb.fork, cudaEventDisableTiming);
     if (err == cudaSuccess) err = cudaEventCreateWithFlags(&g_bb.join, cudaEventDisableTiming);
-    if (err == cudaSuccess) err = cudaStreamCreateWithPriority(&g_bb.side, cudaStreamNonBlocking, prio);
+    if (err != cudaSuccess) return err;
+  }
+  if (!g_bb.side) {  // the side stream runs at the calling stream's priority
+    int prio = 0;
+    if (stream) cudaStreamGetPriority(stream, &prio);
+    err = cudaStreamCreateWithPriority(&g_bb.side, cudaStreamNonBlocking, prio);
     if (err != cudaSuccess) return err;
   }
   // The tables of this stream are shared by its calls: wait until the previous launches
