@@ -713,7 +713,8 @@ def serve_measurement(it, torch, args, rank=0, world=1):
         ref = oracle.coulomb_accel(x, q, m, idx=idx)
         err = float(np.sqrt(((f[:, idx] - ref) ** 2).sum() / max((ref ** 2).sum(), 1e-300))) if w.n > 1 else 0.0
         errs.append({"request": mine[i], "n": w.n, "steps": w.steps, "force_rel_rms_vs_oracle": err})
-    mine_out = {"lat": lat, "wall": wall, "lat07": lat07, "wall07": wall07, "arr07": arr07, "lat64": lat64,
+    mine_out = {"ns": [w.n for w in work], "lat": lat, "wall": wall, "lat07": lat07, "wall07": wall07, "arr07": arr07,
+                "lat64": lat64,
                 "wall64": wall64, "arrivals": arrivals, "pairs": sum(pairs_of),
                 "ion_steps": sum(w.n * w.steps for w in work), "errs": errs,
                 "redraws": sum(reqs[k].redraws for k in mine), "n": len(work)}
@@ -741,6 +742,14 @@ def aggregate_serve(parts, meta):
     comp = {"wall_s": wall07, "arrival_span_s": span07, "offered_pairs_per_s": pairs / span07,
             "pair_interactions_per_s": pairs / wall07, "ion_steps_per_s": ion_steps / wall07}
     comp.update(_pct(cat("lat07")))
+    # the same percentiles by request size: batched small, batched large, single-simulation
+    ns = cat("ns") if all("ns" in p for p in parts) else None
+    if ns:
+        for name, lo, hi in (("n_le_256", 1, 256), ("n_257_2048", 257, 2048), ("n_gt_2048", 2049, 1 << 40)):
+            for run, key in ((primary, "lat"), (comp, "lat07")):
+                sel = [l for l, n in zip(cat(key), ns) if lo <= n <= hi]
+                if sel:
+                    run.setdefault("by_size", {})[name] = dict(_pct(sel), requests=len(sel))
     # the FP64 FIFO: a request not started within the cap counts as waiting until its
     # rank's run ended, so its percentiles are then lower bounds
     lat64 = [(l if l is not None else p["wall64"] - p["arrivals"][k])

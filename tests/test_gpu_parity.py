@@ -482,6 +482,29 @@ def test_batched_alone_equals_mixed_bitwise(it):
         assert np.array_equal(xa, xm) and np.array_equal(va, vm)
 
 
+def test_batched_launches_on_many_streams(it):
+    """Batched launches from more streams than the launcher keeps table sets for (16): the
+    least recently used set is taken over after its launches; every ensemble ends with the
+    bits one mixed launch gives it."""
+    import torch
+    sizes = [40, 300, 700, 1100] * 5
+    ws = [_cloud(n, 80 + k) for k, n in enumerate(sizes)]
+    streams = [torch.cuda.Stream() for _ in ws]
+    sims = [it.Simulation(w.species, w.species_of_ion, w.x0, w.v0, it.make_params(w.trap), stream=st)
+            for w, st in zip(ws, streams)]
+    try:
+        for _ in range(2):
+            for sm in sims:
+                it.iontrap_step_many([sm.handle], [30])
+        got = [sm.state() for sm in sims]
+    finally:
+        for sm in sims:
+            sm.close()
+    mixed = _run_many(it, ws, [60] * len(ws))
+    for (xa, va, sa, _), (xm, vm, sm_, _) in zip(got, mixed):
+        assert sa == sm_ == 60 and np.array_equal(xa, xm) and np.array_equal(va, vm)
+
+
 def test_batched_tuned_bucket_changes_the_shape(it):
     """A tuning-table entry for an N bucket of the batched launch changes that bucket's
     group shape (CTAs per group, j-parts): the summation order changes, so the bits do,

@@ -52,7 +52,8 @@ def _serve_record(rank, n):
     return {"lat": lat, "wall": 2.0 + rank, "lat07": [l / 2 for l in lat], "wall07": 3.0 + rank,
             "arr07": [0.1 * k for k in range(n)], "lat64": [0.5] + [None] * (n - 1), "wall64": 4.0,
             "arrivals": [0.01 * k for k in range(n)], "pairs": 1000 * (rank + 1), "ion_steps": 100 * (rank + 1),
-            "errs": [{"request": rank, "n": 8, "force_rel_rms_vs_oracle": 1e-7}], "redraws": rank, "n": n}
+            "errs": [{"request": rank, "n": 8, "force_rel_rms_vs_oracle": 1e-7}], "redraws": rank, "n": n,
+            "ns": [(100, 1000, 5000)[k % 3] for k in range(n)]}
 
 
 def _router_worker(rank, world, port, out):
@@ -97,6 +98,11 @@ def test_gloo_two_ranks_route_ensembles_and_requests():
     assert prim["wall_s"] == 3.0 and prim["pair_interactions_per_s"] == 3000 / 3.0
     lat = sorted([0.01 * (r + 1) * (k + 1) for r in range(2) for k in range(50)])
     assert abs(prim["p50_ms"] - 1e3 * (lat[49] + lat[50]) / 2) < 1e-9
+    by = prim["by_size"]
+    assert [by[k]["requests"] for k in ("n_le_256", "n_257_2048", "n_gt_2048")] == [34, 34, 32]
+    small = sorted(0.01 * (r + 1) * (k + 1) for r in range(2) for k in range(0, 50, 3))
+    assert abs(by["n_le_256"]["p50_ms"] - 1e3 * (small[16] + small[17]) / 2) < 1e-9
+    assert sv["at_0.7_capacity"]["by_size"]["n_gt_2048"]["requests"] == 32
     fifo = sv["fp64_fifo_same_requests"]
     assert fifo["served"] == 2 and fifo["not_served"] == 98 and fifo["percentiles_are_lower_bounds"]
     assert len(sv["per_result_error"]) == 2
