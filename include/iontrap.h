@@ -328,18 +328,23 @@ typedef struct {
                                     segment and integrates an equal share of its group; no
                                     CUDA graph, pdl ignored; not with IONTRAP_COULOMB_OFF.
                                  5: row-persistent: one cooperative launch runs up to 1000
-                                    steps (threads = 256 or 512, ions_per_thread = 1,
+                                    steps (threads = 256 or 512, ions_per_thread = 1 or 2,
                                     packed = 1, jsplit = R ions per CTA with 3 R <= threads,
                                     ceil(n / R) CTAs resident at once, all n positions staged
                                     in shared memory: n up to about 7000); each CTA sums its R
                                     ions over every j, thread t taking ion t % R against j-part
-                                    t / R, merges the part partials in shared memory and
+                                    t / R (with two ions per thread the ions s and s + RT,
+                                    RT = ceil(R/2), s = t % RT, against part t / RT: every j
+                                    read from shared memory serves two pairs), merges the
+                                    part partials in shared memory and
                                     integrates; one grid-wide counter per step; after a
                                     launch's first step the positions arrive by bulk TMA
                                     copies of a part-major global copy that the owners
                                     write (kept in the handle's partial-sum scratch); the evaluation
                                     at creation uses form 1 over 512-ion j-ranges; not with
                                     IONTRAP_COULOMB_OFF.
+                                 Form 5 gives results within the FP32 tolerances of the other
+                                 forms, bitwise reproducible for a given shape.
                                  The FP64 form supports 1 only. */
     int32_t pdl;              /* 1: consecutive step kernels use programmatic dependent launch
                                  (default 0: measured slower on GB300 for these grids) */

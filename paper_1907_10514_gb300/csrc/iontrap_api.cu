@@ -48,9 +48,9 @@ cudaError_t launch_gp(const StepArgs& a, unsigned* sync, int W, int S, int G, in
                       cudaStream_t st);
 int gp_max_ctas(int W, int S, int Lmax, int max_lmax, long long max_k, int sms);
 size_t rp_scratch_bytes(int NP, int JP);
-cudaError_t launch_rp(const StepArgs& a, unsigned* sync, int W, int R, int NP, int JP, int G, long long K,
+cudaError_t launch_rp(const StepArgs& a, unsigned* sync, int W, int R, int NP, int JP, int I, int G, long long K,
                       cudaStream_t st);
-int rp_max_ctas(int W, int R, int NP, int JP, long long max_k, int sms);
+int rp_max_ctas(int W, int R, int NP, int JP, int I, long long max_k, int sms);
 size_t rp_smem_bytes(int W, int R, int NP, int JP, long long K);
 }  // namespace it
 
@@ -76,6 +76,7 @@ struct GpShape {
 // row-persistent form (fused = 5): W warps, R ions per CTA, G CTAs, NP j-parts of JP entries
 struct RpShape {
   int W = 0, R = 0, G = 0, NP = 0, JP = 0;
+  int I = 1;  // ions per thread
 };
 static constexpr int64_t kRpInitJsplit = 512;  // j-range per CTA of its creation-time / force evaluation
 
@@ -327,18 +328,21 @@ bool tuned_config(int64_t n, int f64, int dev, iontrap_config* c) {
 // four j, 16-byte aligned arrays), with JP / 4 odd when a warp spans several parts (R not
 // a multiple of 32), so that their loads start in distinct banks; the launch must fit in
 // shared memory and on the GPU at once.
+// With two ions per thread (I = 2) the parts are NP = 32 W / ceil(R / 2).
 bool rp_shape(int64_t n, int f64, unsigned flags, int sms, int T, int I, int packed, int64_t R, RpShape* out) {
-  if (f64 || (flags & IONTRAP_COULOMB_OFF) || (T != 256 && T != 512) || I != 1 || packed != 1 || R < 1 || R > n)
+  if (f64 || (flags & IONTRAP_COULOMB_OFF) || (T != 256 && T != 512) || (I != 1 && I != 2) || packed != 1 || R < 1 ||
+      R > n)
     return false;
   const int W = T / 32;
   if (3 * R > 32 * W) return false;
-  const int64_t NP = (32 * W) / R;
+  const int64_t RT = cdiv(R, I);
+  const int64_t NP = (32 * W) / RT;
   int64_t q4 = cdiv(cdiv(n, NP), 4);
-  if (R % 32 != 0 && !(q4 & 1)) ++q4;
+  if (RT % 32 != 0 && !(q4 & 1)) ++q4;
   const int64_t JP = 4 * q4, G = cdiv(n, R);
   if (rp_smem_bytes(W, (int)R, (int)NP, (int)JP, kGpMaxSteps) > 227 * 1024) return false;
-  if (G > rp_max_ctas(W, (int)R, (int)NP, (int)JP, kGpMaxSteps, sms)) return false;
-  out->W = W, out->R = (int)R, out->G = (int)G, out->NP = (int)NP, out->JP = (int)JP;
+  if (G > rp_max_ctas(W, (int)R, (int)NP, (int)JP, I, kGpMaxSteps, sms)) return false;
+  out->W = W, out->R = (int)R, out->G = (int)G, out->NP = (int)NP, out->JP = (int)JP, out->I = I;
   return true;
 }
 
@@ -563,7 +567,7 @@ int alloc_scratch(iontrap* h) {
 
 // One row-persistent launch of K steps on the handle's buffers.
 cudaError_t launch_rp_of(iontrap* h, const StepArgs& a, long long K, cudaStream_t st) {
-  return launch_rp(a, h->d_gsync, h->rp.W, h->rp.R, h->rp.NP, h->rp.JP, h->rp.G, K, st);
+  return launch_rp(a, h->d_gsync, h->rp.W, h->rp.R, h->rp.NP, h->rp.JP, h->rp.I, h->rp.G, K, st);
 }
 
 // Launch one step kernel with programmatic dependent launch, so that consecutive steps
@@ -1492,12 +1496,14 @@ int iontrap_autotune(iontrap_t* h, double trial_us, iontrap_config* best, double
     if (n <= 170) rs.push_back(n);  // every ion in one CTA
     std::sort(rs.begin(), rs.end());
     rs.erase(std::unique(rs.begin(), rs.end()), rs.end());
+    // (one or two ions per thread)
     for (int W : {8, 16})
-      for (int64_t R : rs) {
-        iontrap_config c{32 * W, 1, 1, (int32_t)R, 5, 0, 0};
-        RpShape rs;
-        if (rp_shape(n, 0, h->p.flags, h->sms, c.threads, 1, 1, R, &rs)) cands.push_back(c);
-      }
+      for (int I : {1, 2})
+        for (int64_t R : rs) {
+          iontrap_config c{32 * W, I, 1, (int32_t)R, 5, 0, 0};
+          RpShape rs;
+          if (rp_shape(n, 0, h->p.flags, h->sms, c.threads, I, 1, R, &rs)) cands.push_back(c);
+        }
   }
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return IONTRAP_ECUDA;

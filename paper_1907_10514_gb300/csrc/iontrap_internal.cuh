@@ -286,6 +286,36 @@ __device__ __forceinline__ void rp_chunk(const float* __restrict__ sj, const flo
   }
 }
 
+// Two ions per thread: the j data loaded from shared memory serves both ions, each summed
+// exactly as rp_chunk sums one (two j per packed instruction with the ion in both halves;
+// acc[k] holds ion k's even and odd j).
+template <bool DIAG, bool UNITW>
+__device__ __forceinline__ void rp_chunk_i2(const float* __restrict__ sj, const float* __restrict__ sw, int JP, int qn,
+                                            int jbase, int ia, int ib, const float2 (&nh)[2][3],
+                                            const float2 (&nl)[2][3], float2 (&acc)[2][3]) {
+#pragma unroll 1
+  for (int q = 0; q < qn; q += 4) {
+    const float4 hx = *reinterpret_cast<const float4*>(sj + q);
+    const float4 hy = *reinterpret_cast<const float4*>(sj + JP + q);
+    const float4 hz = *reinterpret_cast<const float4*>(sj + 2 * JP + q);
+    const float4 lx = *reinterpret_cast<const float4*>(sj + 3 * JP + q);
+    const float4 ly = *reinterpret_cast<const float4*>(sj + 4 * JP + q);
+    const float4 lz = *reinterpret_cast<const float4*>(sj + 5 * JP + q);
+    float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!UNITW) w = *reinterpret_cast<const float4*>(sw + q);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int i = k ? ib : ia;
+      rp_pair2<DIAG, UNITW>(make_float2(hx.x, hx.y), make_float2(hy.x, hy.y), make_float2(hz.x, hz.y),
+                            make_float2(lx.x, lx.y), make_float2(ly.x, ly.y), make_float2(lz.x, lz.y),
+                            make_float2(w.x, w.y), jbase + q, i, nh[k], nl[k], acc[k]);
+      rp_pair2<DIAG, UNITW>(make_float2(hx.z, hx.w), make_float2(hy.z, hy.w), make_float2(hz.z, hz.w),
+                            make_float2(lx.z, lx.w), make_float2(ly.z, ly.w), make_float2(lz.z, lz.w),
+                            make_float2(w.z, w.w), jbase + q + 2, i, nh[k], nl[k], acc[k]);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ split partials
 // RF phase at the force time of a launch in the given mode.
 __device__ __forceinline__ double force_time_cos(const StepArgs& A, long long ns) {

@@ -379,13 +379,17 @@ int gp_max_ctas(int W, int S, int Lmax, int max_lmax, long long max_k, int sms) 
 // ------------------------------------------------------------------ row-persistent form (fused = 5)
 // One cooperative launch advances K steps.  CTA g owns the ions [g R, min((g+1) R, n)) and
 // sums their Coulomb term over every j itself.  Its threads are laid out part-major:
-// thread t < R NP takes ion t % R against j-part t / R, the part p covering
-// j in [p JP, (p+1) JP) (NP = 32 W / R parts, so nearly every thread works whatever R);
-// the j data of all parts is staged into shared memory as structure-of-arrays floats and
-// the pair loop runs two j at a time on packed FP32x2 instructions with the thread's ion in
-// both halves (four j per 16-byte shared load).  The NP part partials (sum, compensation)
-// of an ion merge in part order in shared memory, and one thread per owned ion component
-// integrates it exactly as the grid-persistent form does.  One grid-wide step counter per
+// with one ion per thread (IPT = 1), thread t < R NP takes ion t % R against j-part t / R,
+// the part p covering j in [p JP, (p+1) JP) (NP = 32 W / R parts, so nearly every thread
+// works whatever R); with two (IPT = 2), thread t < RT NP (RT = ceil(R / 2)) takes the
+// ions s and s + RT, s = t % RT, against part t / RT.  The j data of all parts is staged
+// into shared memory as structure-of-arrays floats (four j per 16-byte shared load) and
+// the pair loop runs two j at a time on packed FP32x2 instructions with an ion in both
+// halves; a thread with two ions sums each of them that way against the same loaded j
+// (half the shared-memory loads per pair; the loop stays bound by the FP32 pipe, and
+// the choice between one and two ions per thread is the autotuner's).  The NP part
+// partials (sum, compensation) of an ion merge in part order in shared memory, and one
+// thread per owned ion component integrates it exactly as the grid-persistent form does.  One grid-wide step counter per
 // step; no partial sum leaves the SM.  The next step's force-independent terms are
 // evaluated right after the CTA has counted itself, while the others finish.
 //
@@ -398,15 +402,16 @@ int gp_max_ctas(int W, int S, int Lmax, int max_lmax, long long max_k, int sms) 
 // float4 pair stream, which only the next launch reads, are written in a launch's last
 // step (a launch stopped by a timeout leaves the state it started from).
 //
-// Summation order depends on (n, R, W) only: per part, j ascending in 128-j chunks summed
-// as even and odd j (the two halves added), chunks Kahan-added; parts Kahan-merged in
-// order.  Each (i, j) term is the same FP32 value as in the other forms.
+// Summation order depends on (n, R, W, IPT) only: per part, j ascending in 128-j chunks
+// summed as even and odd j (the two halves added), chunks Kahan-added; parts
+// Kahan-merged in order.  Each (i, j) term is the same FP32 value as in
+// the other forms.
 
 struct RpArgs {
   unsigned* sync;  // [0]: step arrivals of all CTAs (zero between launches)
   long long K;     // steps in this launch
   int R;           // ions per CTA
-  int NP;          // j-parts per CTA: 32 W / R
+  int NP;          // j-parts per CTA: 32 W / ceil(R / IPT)
   int JP;          // j entries per part: a multiple of 4 with JP / 4 odd (the parts of one
                    // warp read from distinct shared-memory banks); entries past n are padding
 };
@@ -417,7 +422,7 @@ struct RpArgs {
 constexpr int kRpBatches = 8;
 constexpr long long kRpRunBytes = 16 * 1024;
 
-template <int W>
+template <int W, int IPT>
 __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant__ StepArgs A, const RpArgs P) {
   // dynamic shared memory: per part 7 x JP floats (SoA j data); partial sums and
   // compensations [NP][3][R] floats each; the RF phase of the K steps; the owned ions'
@@ -472,10 +477,13 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
   // every generic writer of data the copy engine reads fences against the async proxy
   if (blockIdx.x == 0 && P.K > 1) asm volatile("fence.proxy.async.global;" ::: "memory");
 
-  // this thread's pair work: ion slot and j-part
-  const int part = tid / R, slot = tid - part * R;
+  // this thread's pair work: ion slot (slots slot and slot + RT with two ions per thread)
+  // and j-part
+  const int RT = (R + IPT - 1) / IPT;
+  const int part = tid / RT, slot = tid - part * RT;
   const bool works = part < NP;
-  const int ii = (int)(r0 + slot);
+  const int ii = (int)(r0 + slot), ib = (int)(r0 + slot + RT);
+  const bool hasb = IPT == 2 && slot + RT < Rg;
   const int mybatch = works ? ((part + 1) * nb - 1) / NP : 0;  // the copy run holding this part
   // owned items: thread k < 3 Rg integrates component c = k / Rg of ion r0 + k % Rg
   const int rq = max(Rg, 1);
@@ -559,7 +567,7 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
 
     // positions x_{ns+1} of every part: entry e is j = e, part e / JP.  The first step of
     // a launch stages them from the pair stream; later steps wait for their copy run.
-    float4 hi4 = make_float4(0.f, 0.f, 0.f, 0.f), lo4 = hi4;
+    float4 hi4 = make_float4(0.f, 0.f, 0.f, 0.f), lo4 = hi4, hib = hi4, lob = hi4;
     if (t == 0) {
       const float4* __restrict__ ghi = A.hi[rb];
       const float4* __restrict__ glo = A.lo[rb];
@@ -579,52 +587,97 @@ __global__ void __launch_bounds__(32 * W, 1) k_step_f32_rp(const __grid_constant
         hi4 = __ldcg(ghi + ii);
         lo4 = __ldcg(glo + ii);
       }
+      if (works && hasb) {
+        hib = __ldcg(ghi + ib);
+        lob = __ldcg(glo + ib);
+      }
       __syncthreads();
     } else {
       if (works && slot < Rg) {
         hi4 = make_float4(sself[slot], sself[R + slot], sself[2 * R + slot], 0.f);
         lo4 = make_float4(sself[3 * R + slot], sself[4 * R + slot], sself[5 * R + slot], 0.f);
       }
+      if (works && hasb) {
+        const int sb = slot + RT;
+        hib = make_float4(sself[sb], sself[R + sb], sself[2 * R + sb], 0.f);
+        lob = make_float4(sself[3 * R + sb], sself[4 * R + sb], sself[5 * R + sb], 0.f);
+      }
       if (works && !solo) bad = !mbar_wait_bounded(&bar[mybatch], (uint32_t)((t - 1) & 1), lim);
     }
-    const float2 nh[3] = {make_float2(-hi4.x, -hi4.x), make_float2(-hi4.y, -hi4.y), make_float2(-hi4.z, -hi4.z)};
-    const float2 nl[3] = {make_float2(-lo4.x, -lo4.x), make_float2(-lo4.y, -lo4.y), make_float2(-lo4.z, -lo4.z)};
+    // each of the thread's ions in both halves of the packed registers
+    float2 nh[IPT][3], nl[IPT][3];
+#pragma unroll
+    for (int k = 0; k < IPT; ++k) {
+      const float4 h = k ? hib : hi4, l = k ? lob : lo4;
+      nh[k][0] = make_float2(-h.x, -h.x), nh[k][1] = make_float2(-h.y, -h.y), nh[k][2] = make_float2(-h.z, -h.z);
+      nl[k][0] = make_float2(-l.x, -l.x), nl[k][1] = make_float2(-l.y, -l.y), nl[k][2] = make_float2(-l.z, -l.z);
+    }
     trace_mark(A.trace, tslot + 1);
 
     if (works && !bad) {
       const float* sj = sall + (size_t)part * 7 * JP;
-      float ks[3] = {0.f, 0.f, 0.f}, kcp[3] = {0.f, 0.f, 0.f};
+      // Kahan sums of the chunks, per ion of the thread ([0]: ion a, [1]: ion b)
+      float ks[IPT][3], kcp[IPT][3];
+#pragma unroll
+      for (int k = 0; k < IPT; ++k)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) ks[k][d] = kcp[k][d] = 0.f;
       for (int c0 = 0; c0 < JP; c0 += kSeg) {
         const int qn = min(kSeg, JP - c0);
-        float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        float2 acc[IPT][3];  // per ion: even and odd j
+#pragma unroll
+        for (int k = 0; k < IPT; ++k)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) acc[k][d] = make_float2(0.f, 0.f);
         // the self pair can only sit in a chunk that overlaps the CTA's own ions; the
         // variant is chosen per warp (its lanes may belong to two parts)
         const int jc = part * JP + c0;
         const bool diag = __any_sync(__activemask(), (jc < r0 + Rg) && (r0 < jc + qn));
-        if (A.unitw) {
-          if (diag)
-            rp_chunk<true, true>(sj + c0, sj + 6 * JP + c0, JP, qn, jc, ii, nh, nl, acc);
-          else
-            rp_chunk<false, true>(sj + c0, sj + 6 * JP + c0, JP, qn, jc, ii, nh, nl, acc);
+        if constexpr (IPT == 1) {
+          if (A.unitw) {
+            if (diag)
+              rp_chunk<true, true>(sj + c0, sj + 6 * JP + c0, JP, qn, jc, ii, nh[0], nl[0], acc[0]);
+            else
+              rp_chunk<false, true>(sj + c0, sj + 6 * JP + c0, JP, qn, jc, ii, nh[0], nl[0], acc[0]);
+          } else {
+            if (diag)
+              rp_chunk<true, false>(sj + c0, sj + 6 * JP + c0, JP, qn, jc, ii, nh[0], nl[0], acc[0]);
+            else
+              rp_chunk<false, false>(sj + c0, sj + 6 * JP + c0, JP, qn, jc, ii, nh[0], nl[0], acc[0]);
+          }
         } else {
-          if (diag)
-            rp_chunk<true, false>(sj + c0, sj + 6 * JP + c0, JP, qn, jc, ii, nh, nl, acc);
-          else
-            rp_chunk<false, false>(sj + c0, sj + 6 * JP + c0, JP, qn, jc, ii, nh, nl, acc);
+          if (A.unitw) {
+            if (diag)
+              rp_chunk_i2<true, true>(sj + c0, sj + 6 * JP + c0, JP, qn, jc, ii, ib, nh, nl, acc);
+            else
+              rp_chunk_i2<false, true>(sj + c0, sj + 6 * JP + c0, JP, qn, jc, ii, ib, nh, nl, acc);
+          } else {
+            if (diag)
+              rp_chunk_i2<true, false>(sj + c0, sj + 6 * JP + c0, JP, qn, jc, ii, ib, nh, nl, acc);
+            else
+              rp_chunk_i2<false, false>(sj + c0, sj + 6 * JP + c0, JP, qn, jc, ii, ib, nh, nl, acc);
+          }
         }
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          const float a = acc[d].x + acc[d].y;
-          const float y = a - kcp[d];
-          const float tt = ks[d] + y;
-          kcp[d] = (tt - ks[d]) - y;
-          ks[d] = tt;
-        }
+        for (int k = 0; k < IPT; ++k)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            // the even and odd j of the chunk added
+            const float a = acc[k][d].x + acc[k][d].y;
+            const float y = a - kcp[k][d];
+            const float tt = ks[k][d] + y;
+            kcp[k][d] = (tt - ks[k][d]) - y;
+            ks[k][d] = tt;
+          }
       }
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        ps[(part * 3 + d) * R + slot] = ks[d];
-        pc[(part * 3 + d) * R + slot] = kcp[d];
+        ps[(part * 3 + d) * R + slot] = ks[0][d];
+        pc[(part * 3 + d) * R + slot] = kcp[0][d];
+        if (IPT == 2 && slot + RT < R) {
+          ps[(part * 3 + d) * R + slot + RT] = ks[IPT - 1][d];
+          pc[(part * 3 + d) * R + slot + RT] = kcp[IPT - 1][d];
+        }
       }
     }
     if (__syncthreads_or(bad)) {  // a copy run never landed: flag, let every copy finish, stop
@@ -718,18 +771,17 @@ size_t rp_smem_bytes(int W, int R, int NP, int JP, long long K) {
 // Global scratch of a launch: the two part-major position copies (NP x 7 x JP floats each).
 size_t rp_scratch_bytes(int NP, int JP) { return 2 * (size_t)NP * 7 * JP * sizeof(float); }
 
-const void* rp_kernel(int W) {
-  switch (W) {
-    case 8: return (const void*)k_step_f32_rp<8>;
-    case 16: return (const void*)k_step_f32_rp<16>;
-    default: return nullptr;
-  }
+const void* rp_kernel(int W, int I) {
+  if (I == 1) return W == 8 ? (const void*)k_step_f32_rp<8, 1> : W == 16 ? (const void*)k_step_f32_rp<16, 1> : nullptr;
+  if (I == 2) return W == 8 ? (const void*)k_step_f32_rp<8, 2> : W == 16 ? (const void*)k_step_f32_rp<16, 2> : nullptr;
+  return nullptr;
 }
 
-// Co-resident CTAs of a launch shape with up to max_k steps per launch (the kernel's
-// dynamic shared-memory limit is raised to 227 KB once, so handles coexist).
-int rp_max_ctas(int W, int R, int NP, int JP, long long max_k, int sms) {
-  const void* fn = rp_kernel(W);
+// Co-resident CTAs of a launch shape (W warps, I ions per thread) with up to max_k steps
+// per launch (the kernel's dynamic shared-memory limit is raised to 227 KB once, so
+// handles coexist).
+int rp_max_ctas(int W, int R, int NP, int JP, int I, long long max_k, int sms) {
+  const void* fn = rp_kernel(W, I);
   if (!fn) return 0;
   const size_t smem = rp_smem_bytes(W, R, NP, JP, max_k);
   if (smem > 227 * 1024) return 0;
@@ -739,9 +791,9 @@ int rp_max_ctas(int W, int R, int NP, int JP, long long max_k, int sms) {
   return per * sms;
 }
 
-cudaError_t launch_rp(const StepArgs& a, unsigned* sync, int W, int R, int NP, int JP, int G, long long K,
+cudaError_t launch_rp(const StepArgs& a, unsigned* sync, int W, int R, int NP, int JP, int I, int G, long long K,
                       cudaStream_t st) {
-  const void* fn = rp_kernel(W);
+  const void* fn = rp_kernel(W, I);
   if (!fn) return cudaErrorInvalidValue;
   RpArgs P{sync, K, R, NP, JP};
   cudaLaunchConfig_t cfg{};

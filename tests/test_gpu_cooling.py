@@ -99,7 +99,7 @@ def _gp_cfg(n, W, S):
 
 
 @pytest.mark.parametrize("form", ["last_cta", "separate_epilogue", "cluster", "cluster_warps", "persistent",
-                                  "row_persistent", "fp64"])
+                                  "row_persistent", "row_persistent_i2", "fp64"])
 def test_two_phase_cooling_matches_oracle(it, form):
     """Per-species baths and lasers, then a changed trap and cooling, in every kernel form
     of a single simulation: 40 + 40 steps against the oracle doing the same (this cloud
@@ -110,7 +110,8 @@ def test_two_phase_cooling_matches_oracle(it, form):
     prec = 1 if form == "fp64" else 0
     cfg = {"last_cta": (128, 2, 1, -(-n // 12), 1), "separate_epilogue": (64, 4, 1, 256, 0),
            "cluster": (128, 1, 0, -(-n // 8), 2), "cluster_warps": (128, 2, 1, -(-n // 8), 3),
-           "persistent": _gp_cfg(n, 8, 25), "row_persistent": (512, 1, 1, 20, 5), "fp64": None}[form]
+           "persistent": _gp_cfg(n, 8, 25), "row_persistent": (512, 1, 1, 20, 5),
+           "row_persistent_i2": (512, 2, 1, 20, 5), "fp64": None}[form]
     with it.Simulation(w.species, w.species_of_ion, w.x0, w.v0, it.make_params(w.trap, precision=prec)) as sim:
         if cfg:
             sim.set_config(*cfg)

@@ -44,9 +44,10 @@ def _rel_rms(a, b):
     return math.sqrt(float(((a - b) ** 2).sum()) / float((b ** 2).sum()))
 
 
-# (threads, ions per thread, packed, jsplit, fused) of a row-persistent (5) and a
-# grid-persistent (4) launch of 3000 ions
-FORMS = {"row-persistent": (512, 1, 1, 20, 5), "grid-persistent": (256, 2, 1, -(-3000 // 25), 4)}
+# (threads, ions per thread, packed, jsplit, fused) of a row-persistent launch (5; also
+# with two ions per thread) and a grid-persistent one (4), of 3000 ions
+FORMS = {"row-persistent": (512, 1, 1, 20, 5), "row-persistent-2ipt": (512, 2, 1, 20, 5),
+         "grid-persistent": (256, 2, 1, -(-3000 // 25), 4)}
 
 
 @pytest.mark.parametrize("form", list(FORMS))
@@ -57,7 +58,7 @@ def test_bounded_wait_expires_with_a_timeout_status(it, form, cta, at_step):
     with it.Simulation(species, sp, x0, None, it.make_params(trap)) as sim:
         sim.set_config(*FORMS[form])
         assert sim.config()[4] == FORMS[form][4]
-        ctas = -(-n // 20) if form == "row-persistent" else (-(-n // 512)) * 25
+        ctas = -(-n // 20) if form.startswith("row-persistent") else (-(-n // 512)) * 25
         with pytest.raises(it.IonTrapError) as e:
             it.iontrap_test_stall(sim.handle, LIMIT_NS, ctas, 0)  # no such CTA
         assert e.value.code == it.IONTRAP_EINVAL
@@ -75,7 +76,7 @@ def test_bounded_wait_expires_with_a_timeout_status(it, form, cta, at_step):
         assert elapsed < 1.0, elapsed  # gave up after the 1 ms limit, not the default 2 s
         x, v, step, _ = it.iontrap_state(sim.handle, n, accept=(it.IONTRAP_ETIMEOUT,))
         assert step == 0  # the step index is not advanced by a failed launch
-        if form == "row-persistent":  # its FP64 state is written in a launch's last step only
+        if form.startswith("row-persistent"):  # its FP64 state is written in a launch's last step only
             assert np.array_equal(x, x0) and np.array_equal(v, np.zeros_like(v))
         with pytest.raises(it.IonTrapError) as e:  # the status is sticky
             sim.step(1)

@@ -87,7 +87,8 @@ def test_forces_match_oracle(it, n):
                                  (256, 4, 0, 100, 1), (128, 4, 1, 1152, 0), (128, 1, 0, 7, 1), (64, 2, 0, 1000, 0),
                                  (32, 1, 0, 376, 2), (64, 1, 0, 501, 2), (128, 4, 1, 1001, 2), (32, 2, 1, 3001, 2),
                                  (64, 1, 0, 501, 3), (128, 2, 1, 1001, 3), (128, 1, 0, 376, 3), (64, 2, 1, 3001, 3),
-                                 (64, 2, 1, 200, 3), (64, 1, 0, 188, 3), (512, 1, 1, 32, 5), (256, 1, 1, 20, 5)])
+                                 (64, 2, 1, 200, 3), (64, 1, 0, 188, 3), (512, 1, 1, 32, 5), (256, 1, 1, 20, 5),
+                                 (512, 2, 1, 28, 5), (256, 2, 1, 21, 5)])
 @pytest.mark.parametrize("unit", [False, True], ids=["z_mixed", "z_unit"])
 def test_forces_every_tile_config(it, cfg, unit):
     n = 3001
@@ -620,17 +621,37 @@ def test_row_persistent_form_trajectory_matches_oracle(it, n, W, R, steps):
     assert step == steps and rel_rms(x, xo) < FP32_TRAJ_TOL and rel_rms(v, vo) < 10 * FP32_TRAJ_TOL
 
 
+@pytest.mark.parametrize("n,W,R,steps", [(300, 8, 2, 100), (1000, 16, 7, 100), (1200, 8, 85, 100),
+                                         (2049, 8, 14, 100), (3000, 16, 21, 100), (4096, 16, 28, 60),
+                                         (4096, 16, 27, 60), (6000, 16, 40, 40), (2500, 16, 170, 60)])
+def test_row_persistent_two_ions_per_thread_matches_oracle(it, n, W, R, steps):
+    """The row-persistent form with two ions per thread (ions s and s + ceil(R/2) of the
+    CTA against one broadcast j) against the oracle: one ion per CTA half (R = 2), odd R
+    (a thread with one ion), short last CTAs, both warp counts, mixed charges."""
+    w = _cloud(n, 2700 + n)
+    q, m, p = _oracle_side(w)
+    xo, vo, _ = oracle.run(w.x0, w.v0, q, m, p, steps)
+    cfg = (32 * W, 2, 1, R, 5)
+    with _sim(it, w, 0) as sim:
+        sim.set_config(*cfg)
+        assert sim.config()[:5] == cfg
+        sim.step(steps)
+        x, v, step, _ = sim.state()
+    assert step == steps and rel_rms(x, xo) < FP32_TRAJ_TOL and rel_rms(v, vo) < 10 * FP32_TRAJ_TOL
+
+
+@pytest.mark.parametrize("ipt", [1, 2])
 @pytest.mark.parametrize("n", [1, 2, 37, 64, 100, 128, 170])
-def test_single_cta_row_persistent_form(it, n):
+def test_single_cta_row_persistent_form(it, n, ipt):
     """Up to 170 ions the row-persistent form can hold every ion in one CTA, which then
     exchanges positions through its own shared memory (no grid barrier); the default for
     N <= 112.  Against the oracle over 100 steps, and launch splits bit for bit."""
     w = _cloud(n, 900 + n)
     q, m, p = _oracle_side(w)
     xo, vo, _ = oracle.run(w.x0, w.v0, q, m, p, 100)
-    cfg = (512, 1, 1, n, 5)
+    cfg = (512, ipt, 1, n, 5)
     with _sim(it, w, 0) as a, _sim(it, w, 0) as b:
-        if n <= 112:
+        if n <= 112 and ipt == 1:
             assert a.config()[:5] == cfg  # the default
         for s in (a, b):
             s.set_config(*cfg)
@@ -646,13 +667,15 @@ def test_single_cta_row_persistent_form(it, n):
         assert rel_rms(xa, xo) < 1e-9
 
 
-def test_row_persistent_form_bitwise_across_launches_and_restore(it):
+@pytest.mark.parametrize("ipt", [1, 2])
+def test_row_persistent_form_bitwise_across_launches_and_restore(it, ipt):
     """Launch splits of the row-persistent form give the bits of one launch; a checkpoint
     restored into a second handle continues bit for bit; unit-charge clouds take the loop
-    without the z_j product with the same bits as the general loop."""
+    without the z_j product with the same bits as the general loop (one and two ions per
+    thread)."""
     n = 2500
     w = _cloud(n, 37)
-    cfg = _rp_cfg(16, 17)
+    cfg = (512, ipt, 1, 17, 5)
     with _sim(it, w, 0) as a, _sim(it, w, 0) as b, _sim(it, w, 0) as c:
         for s in (a, b, c):
             s.set_config(*cfg)
@@ -683,7 +706,7 @@ def test_row_persistent_form_bitwise_across_launches_and_restore(it):
     out = []
     for ww in (wu, w2):
         with _sim(it, ww, 0) as s:
-            s.set_config(*_rp_cfg(16, 10))
+            s.set_config(512, ipt, 1, 10, 5)
             s.step(120)
             out.append(s.state()[:2])
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
@@ -699,7 +722,7 @@ def test_row_persistent_shape_limits(it):
         with pytest.raises(it.IonTrapError):
             s.set_config(256, 1, 1, 86, 5)
         with pytest.raises(it.IonTrapError):
-            s.set_config(512, 2, 1, 16, 5)
+            s.set_config(512, 3, 1, 16, 5)
     w2 = _cloud(9000, 4, species=(iongen.CA40,))
     with _sim(it, w2, 0) as s:
         with pytest.raises(it.IonTrapError):

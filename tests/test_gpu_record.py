@@ -58,7 +58,8 @@ def _record(it, torch, sim, n, n_steps, every, fields, W):
 
 
 @pytest.mark.parametrize("n,prec,cfg", [(500, 0, None), (2500, 0, None), (700, 0, (128, 2, 1, 100, 3)),
-                                        (1500, 0, (512, 1, 1, 10, 5)), (300, 1, None)])
+                                        (1500, 0, (512, 1, 1, 10, 5)), (1500, 0, (512, 2, 1, 10, 5)),
+                                        (300, 1, None)])
 def test_records_are_the_states_passed_through(it, torch, n, prec, cfg):
     """x and v records equal the states of a twin handle stepped to the same indices (bit
     for bit); the device time average equals the mean of the twin's velocities read after
