@@ -52,9 +52,9 @@ NOMINAL_SM_MHZ = 2070.0
 # built from and by its launch shape (threads, ions per thread, packed, jsplit, fused); the
 # bench reports it only while both still match, and null otherwise.
 KERNEL_DRAM_TRAFFIC = {
-    # row-persistent form, 28 ions per CTA: 506 112 B read + 2 304 B written over the second
+    # row-persistent form, 28 ions per CTA: 505 856 B read + 1 792 B written over the second
     # 20-timestep launch of mix_n4096 (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum)
-    ("4e235356952e63db", (512, 1, 1, 28, 5)): 25420.8,
+    ("5161dcdda9021abe", (512, 1, 1, 28, 5)): 25382.4,
 }
 KERNEL_SOURCES = ("persistent.cu", "iontrap_internal.cuh")
 
@@ -595,10 +595,11 @@ def aggregate_batched(parts):
             "launches_per_rank": 2 * ((steps + 999) // 1000)}
 
 
-def _serve_run(it, torch, work, arrivals, budget_bytes, keep=(), chunk_steps=100):
+def _serve_run(it, torch, work, arrivals, budget_bytes, keep=(), chunk_steps=100, max_parallel=0):
     """Submit each request at its arrival time (s after the start) to a fresh serving
     loop and poll it; returns (latencies s, wall s, {index: final x} for ``keep``)."""
-    srv = it.iontrap_server_create(mem_budget_bytes=budget_bytes, max_resident=4096, chunk_steps=chunk_steps)
+    srv = it.iontrap_server_create(mem_budget_bytes=budget_bytes, max_resident=4096, chunk_steps=chunk_steps,
+                                   max_parallel=max_parallel)
     lat = [None] * len(work)
     kept, index, ns = {}, {}, {}
     try:
@@ -691,14 +692,14 @@ def serve_measurement(it, torch, args, rank=0, world=1):
     budget = args.serve_budget_mb << 20
     # sampled results whose error against the oracle is stated (their final state's forces)
     keep = set(np.random.default_rng(11).choice(len(work), min(6, len(work)), replace=False).tolist())
-    lat, wall, kept = _serve_run(it, torch, work, arrivals, budget, keep, args.serve_chunk_steps)
+    lat, wall, kept = _serve_run(it, torch, work, arrivals, budget, keep, args.serve_chunk_steps, args.serve_parallel)
     cap_mine = sum(pairs_of) / wall
     # the companion run: the same requests, arrivals stretched so that the offered load is
     # 0.7 of the capacity the first run sustained
     span = max(arrivals) if arrivals else 0.0
     stretch = (sum(pairs_of) / (0.7 * cap_mine)) / span if span > 0 else 1.0
     arr07 = [a * stretch for a in arrivals]
-    lat07, wall07, _ = _serve_run(it, torch, work, arr07, budget, (), args.serve_chunk_steps)
+    lat07, wall07, _ = _serve_run(it, torch, work, arr07, budget, (), args.serve_chunk_steps, args.serve_parallel)
     lat64, wall64 = _fifo_fp64(it, torch, work, arrivals, args.serve_fp64_cap_s)
     errs = []
     for i, (x, step, status) in sorted(kept.items()):
@@ -723,7 +724,8 @@ def serve_measurement(it, torch, args, rank=0, world=1):
         return None
     meta = {"requests": K, "step_scale": scale, "mem_budget_bytes": budget, "full_stream_requests": len(full),
             "full_stream_offered_pairs_per_s": full_pairs / full[-1].arrival_s, "arrival_span_s": reqs[-1].arrival_s,
-            "fp64_cap_s": args.serve_fp64_cap_s, "chunk_steps": args.serve_chunk_steps}
+            "fp64_cap_s": args.serve_fp64_cap_s, "chunk_steps": args.serve_chunk_steps,
+            "max_parallel": args.serve_parallel or 3}
     return aggregate_serve(parts, meta)
 
 
@@ -765,6 +767,7 @@ def aggregate_serve(parts, meta):
             "step_scale": meta["step_scale"],
             "step_budgets": f"the stream's budgets (1e3 .. 1e5) divided by {meta['step_scale']:g}",
             "mem_budget_bytes": meta["mem_budget_bytes"], "chunk_steps": meta.get("chunk_steps"),
+            "max_parallel": meta.get("max_parallel"),
             "full_stream_requests": meta["full_stream_requests"],
             "full_stream_offered_pairs_per_s": meta["full_stream_offered_pairs_per_s"],
             "unstable_trap_redraws": sum(p["redraws"] for p in parts),
@@ -862,6 +865,8 @@ def main():
     ap.add_argument("--serve-budget-mb", type=int, default=2048)
     ap.add_argument("--serve-fp64-cap-s", type=float, default=20.0)
     ap.add_argument("--serve-chunk-steps", type=int, default=100)
+    ap.add_argument("--serve-parallel", type=int, default=0,
+                    help="shared streams of the served requests the batched kernel does not take (0: 3)")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--only", choices=["serve"], default=None,

@@ -381,19 +381,26 @@ int iontrap_estimate_bytes(int64_t n, int precision, int64_t *bytes);
  * memory budget are free, then stay resident until their last step.  Each
  * iontrap_server_poll is one scheduling round: retire requests whose last chunk
  * finished (final state copied to the host, memory returned), admit waiting requests
- * that fit, and enqueue the next chunk (chunk_steps) of every idle resident request --
- * FP32-form requests with n <= 2048 through the batched kernel, one launch per size class
- * (up to 64, 256, 512, 1024, 2048 ions) on a stream of its own, smaller classes at higher
- * stream priority, so that a small request's chunk does not wait for a large one's; the
- * others each on a stream of their own -- so the work overlaps.  A
- * request's result does not depend on what else is resident (batched ones are bitwise
- * independent of the mix).  Poll is non-blocking except for the host copies of
- * admission and retirement.  A server and its requests are used from one host thread. */
+ * that fit (each created on the server's own stream, so admission does not wait for
+ * chunks in flight), and enqueue the next chunks -- FP32-form requests with n <= 2048
+ * through the batched kernel, chunk_steps steps of every idle one, one launch per size
+ * class (up to 64, 256, 512, 1024, 2048 ions) on a stream of its own, smaller classes at
+ * higher stream priority, so that a small request's chunk does not wait for a large
+ * one's; the others on max_parallel shared streams, each idle stream taking the request
+ * with the least remaining pair work (n^2 x steps left), in chunks of at most
+ * chunk_steps x (4096 / n)^2 steps (at least one).  Handle memory comes from the
+ * library's stream-ordered pool, so admission and retirement do not synchronise the
+ * device.  A request's result does not depend on what else is resident (batched ones are
+ * bitwise independent of the mix, the others are stepped one chunk at a time).  Poll is
+ * non-blocking except for the host copies of admission and retirement.  A server and its
+ * requests are used from one host thread. */
 typedef struct iontrap_server iontrap_server_t;
 typedef struct {
     int64_t mem_budget_bytes; /* device bytes resident requests may hold; 0 = 2 GiB */
     int32_t max_resident;     /* resident request limit; 0 = 4096 */
     int32_t chunk_steps;      /* steps per request per scheduling round; 0 = 100 */
+    int32_t max_parallel;     /* shared streams of the requests the batched kernel does not
+                                 take (each steps one request at a time); 0 = 3 */
 } iontrap_server_config;
 typedef struct {
     int64_t waiting, resident, completed, device_bytes;

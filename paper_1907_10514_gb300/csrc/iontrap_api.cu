@@ -520,6 +520,42 @@ void destroy_graph(iontrap* h) {
   h->graph = nullptr;
 }
 
+// Device buffers of a handle come from a per-device pool of the stream-ordered allocator
+// and are allocated and freed in order on the handle's stream: unlike cudaMalloc and
+// cudaFree neither synchronises the device, so a handle created or destroyed while others
+// run (the serving loop admits and retires requests between their chunks) does not stall
+// them.  The pool keeps up to kPoolKeepBytes of freed memory for reuse.
+constexpr uint64_t kPoolKeepBytes = (uint64_t)4 << 30;
+
+cudaMemPool_t handle_pool(int dev) {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  std::lock_guard<std::mutex> lock(mu);
+  auto f = pools.find(dev);
+  if (f != pools.end()) return f->second;
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+  uint64_t keep = kPoolKeepBytes;
+  cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  pools[dev] = pool;
+  return pool;
+}
+
+template <typename T>
+cudaError_t dev_alloc(const iontrap* h, T** p, size_t bytes) {
+  cudaMemPool_t pool = handle_pool(h->device);
+  if (!pool) return cudaErrorMemoryAllocation;
+  return cudaMallocFromPoolAsync(reinterpret_cast<void**>(p), bytes, pool, h->stream);
+}
+
+void dev_free(const iontrap* h, void* p) {
+  if (p) cudaFreeAsync(p, h->stream);
+}
+
 // (Re)allocate the scratch that depends on the tile configuration.
 int alloc_scratch(iontrap* h) {
   const int64_t splits = splits_of(h);
@@ -532,17 +568,17 @@ int alloc_scratch(iontrap* h) {
   if (h->fused == 5) part = std::max(part, rp_scratch_bytes(h->rp.NP, h->rp.JP));
   const size_t cnt = (size_t)cdiv(h->n, iblock_ions(h));
   if (part > h->part_bytes) {
-    if (h->d_part) cudaFree(h->d_part);
+    dev_free(h, h->d_part);
     h->d_part = nullptr;
     h->part_bytes = 0;
-    if (cudaMalloc(&h->d_part, part) != cudaSuccess) return IONTRAP_ENOMEM;
+    if (dev_alloc(h, &h->d_part, part) != cudaSuccess) return IONTRAP_ENOMEM;
     h->part_bytes = part;
   }
   if (cnt > h->cnt_len) {
-    if (h->d_cnt) cudaFree(h->d_cnt);
+    dev_free(h, h->d_cnt);
     h->d_cnt = nullptr;
     h->cnt_len = 0;
-    if (cudaMalloc(&h->d_cnt, cnt * sizeof(unsigned)) != cudaSuccess) return IONTRAP_ENOMEM;
+    if (dev_alloc(h, &h->d_cnt, cnt * sizeof(unsigned)) != cudaSuccess) return IONTRAP_ENOMEM;
     h->cnt_len = cnt;
   }
   if (cudaMemsetAsync(h->d_cnt, 0, h->cnt_len * sizeof(unsigned), h->stream) != cudaSuccess)
@@ -552,7 +588,7 @@ int alloc_scratch(iontrap* h) {
         !gp_shape(h->n, h->f64, h->p.flags, h->sms, h->T, h->I, h->packed, h->jsplit, &h->gp))
       return IONTRAP_EINVAL;
     if (!h->d_gsync) {
-      if (cudaMalloc(&h->d_gsync, kGpSyncBytes) != cudaSuccess) return IONTRAP_ENOMEM;
+      if (dev_alloc(h, &h->d_gsync, kGpSyncBytes) != cudaSuccess) return IONTRAP_ENOMEM;
       if (cudaMemsetAsync(h->d_gsync, 0, kGpSyncBytes, h->stream) != cudaSuccess) return IONTRAP_ECUDA;
     }
   }
@@ -691,8 +727,7 @@ void free_all(iontrap* h) {
   destroy_graph(h);
   void* ptrs[] = {h->d_x, h->d_v, h->d_a, h->d_out, h->d_sp, h->d_pair[0], h->d_pair[1],
                   h->d_part, h->d_cnt, h->d_done, h->d_step, h->d_err, h->d_gsync, h->d_snap};
-  for (void* q : ptrs)
-    if (q) cudaFree(q);
+  for (void* q : ptrs) dev_free(h, q);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   if (h->cap) cudaStreamDestroy(h->cap);
 }
@@ -709,6 +744,16 @@ bool batched_tuned_shape(int dev, long long n, int* C, int* NP) {
   *C = f->second.splits;
   *NP = f->second.ions_per_thread;
   return true;
+}
+
+// Move an idle handle that does not own its stream onto another stream of its device; its
+// later work (and the release of its buffers) is enqueued there.  The serving loop
+// creates handles on a private stream, so that admission never waits for a chunk in
+// flight, and then steps them on shared ones.
+int rebind_stream(iontrap* h, cudaStream_t st) {
+  if (!h || !st || h->own_stream) return IONTRAP_EINVAL;
+  h->stream = st;
+  return IONTRAP_OK;
 }
 
 // Give a handle the default configuration without the grid-persistent form (for callers
@@ -852,12 +897,12 @@ int iontrap_create(const iontrap_species* species, int n_species, const uint8_t*
 
   const size_t vec = 3 * (size_t)n * sizeof(double);
   const size_t pair = (size_t)n * (h->f64 ? sizeof(double4_32a) : 2 * sizeof(float4));
-  bool ok = cudaMalloc(&h->d_x, vec) == cudaSuccess && cudaMalloc(&h->d_v, vec) == cudaSuccess &&
-            cudaMalloc(&h->d_a, vec) == cudaSuccess && cudaMalloc(&h->d_sp, (size_t)n) == cudaSuccess &&
-            cudaMalloc(&h->d_pair[0], pair) == cudaSuccess && cudaMalloc(&h->d_pair[1], pair) == cudaSuccess &&
-            cudaMalloc(&h->d_done, sizeof(unsigned)) == cudaSuccess &&
-            cudaMalloc(&h->d_step, sizeof(long long)) == cudaSuccess &&
-            cudaMalloc(&h->d_err, sizeof(int)) == cudaSuccess;
+  bool ok = dev_alloc(h, &h->d_x, vec) == cudaSuccess && dev_alloc(h, &h->d_v, vec) == cudaSuccess &&
+            dev_alloc(h, &h->d_a, vec) == cudaSuccess && dev_alloc(h, &h->d_sp, (size_t)n) == cudaSuccess &&
+            dev_alloc(h, &h->d_pair[0], pair) == cudaSuccess && dev_alloc(h, &h->d_pair[1], pair) == cudaSuccess &&
+            dev_alloc(h, &h->d_done, sizeof(unsigned)) == cudaSuccess &&
+            dev_alloc(h, &h->d_step, sizeof(long long)) == cudaSuccess &&
+            dev_alloc(h, &h->d_err, sizeof(int)) == cudaSuccess;
   if (!ok) {
     free_all(h);
     delete h;
@@ -1025,7 +1070,7 @@ int iontrap_minimize(iontrap_t* h, int64_t max_iters, double dt, double dmax, do
   if (st) return st;
   DeviceGuard g(h->device);
   const size_t vec = 3 * (size_t)h->n * sizeof(double);
-  if (!h->d_out && cudaMalloc(&h->d_out, vec) != cudaSuccess) return IONTRAP_ENOMEM;
+  if (!h->d_out && dev_alloc(h, &h->d_out, vec) != cudaSuccess) return IONTRAP_ENOMEM;
   void* scratch = nullptr;
   if (cudaMalloc(&scratch, min_scratch_bytes(h->n)) != cudaSuccess) return IONTRAP_ENOMEM;
   const double step_dt = dt > 0 ? dt : h->p.dt;
@@ -1110,7 +1155,7 @@ int iontrap_step_record(iontrap_t* h, int64_t n_steps, int64_t every, uint32_t f
   if (h->status) return h->status;
   DeviceGuard g(h->device);
   const size_t n3 = 3 * (size_t)h->n;
-  if (avg && !h->d_snap && cudaMalloc(&h->d_snap, 2 * n3 * sizeof(double)) != cudaSuccess) return IONTRAP_ENOMEM;
+  if (avg && !h->d_snap && dev_alloc(h, &h->d_snap, 2 * n3 * sizeof(double)) != cudaSuccess) return IONTRAP_ENOMEM;
   const int nf = ((fields & IONTRAP_REC_X) ? 1 : 0) + ((fields & IONTRAP_REC_V) ? 1 : 0) + (avg ? 1 : 0);
   for (int64_t k = 0; k < n_steps / every; ++k) {
     int st;
@@ -1167,7 +1212,7 @@ int iontrap_forces(iontrap_t* h, double* acc) {
   if (st) return st;
   DeviceGuard g(h->device);
   const size_t vec = 3 * (size_t)h->n * sizeof(double);
-  if (!h->d_out && cudaMalloc(&h->d_out, vec) != cudaSuccess) return IONTRAP_ENOMEM;
+  if (!h->d_out && dev_alloc(h, &h->d_out, vec) != cudaSuccess) return IONTRAP_ENOMEM;
   if (h->p.flags & IONTRAP_COULOMB_OFF) {
     std::memset(acc, 0, vec);
     return IONTRAP_OK;

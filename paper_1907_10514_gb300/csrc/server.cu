@@ -7,15 +7,21 @@
 //   1. requests whose enqueued chunk has finished (CUDA event) advance their count; a
 //      request at its budget is retired: its final state is copied out and its device
 //      memory returned to the budget;
-//   2. waiting requests are admitted, first come first served, while they fit;
-//   3. every idle resident request gets its next chunk of steps: requests the batched
-//      kernel accepts (FP32 form, N <= 2048) go into one iontrap_step_many per size class
-//      (up to 64, 256, 512, 1024 and 2048 ions), each class on a stream of its own --
-//      smaller classes at higher stream priority -- so that a small request's chunk does
-//      not wait for a large one's; the others each run on their own stream, so their work
-//      overlaps with the batches and with each other.
+//   2. waiting requests are admitted, first come first served, while they fit; a handle
+//      is created on the server's own admission stream (so admission never waits for a
+//      chunk in flight) and then moved to the stream it is stepped on, and its device
+//      buffers come from the library's stream-ordered pool (no device-wide
+//      synchronisation at admission or retirement);
+//   3. the next chunks: requests the batched kernel accepts (FP32 form, N <= 2048) go
+//      into one iontrap_step_many per size class (up to 64, 256, 512, 1024 and 2048
+//      ions), each class on a stream of its own -- smaller classes at higher stream
+//      priority -- so that a small request's chunk does not wait for a large one's; the
+//      others share max_parallel streams, each idle one taking the request with the least
+//      remaining pair work (N^2 x steps left: shortest remaining work first, preempting at
+//      chunk boundaries), in chunks of at most chunk_steps x (4096 / N)^2 steps, so that
+//      every chunk is short and no stream queues a large one ahead of the others.
 // A request's trajectory does not depend on what else is resident: batched requests are
-// bitwise independent of the mix, the others run alone on their stream.
+// bitwise independent of the mix, the others run one chunk at a time on one stream.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,7 +36,8 @@
 #include "iontrap.h"
 
 namespace it {
-int use_nonpersistent_default(iontrap_t* h);  // iontrap_api.cu
+int use_nonpersistent_default(iontrap_t* h);       // iontrap_api.cu
+int rebind_stream(iontrap_t* h, cudaStream_t st);  // iontrap_api.cu
 }
 
 namespace {
@@ -53,11 +60,10 @@ struct Request {
   iontrap_params p{};
   int64_t steps = 0, done = 0, inflight = 0;
   iontrap_t* h = nullptr;
-  cudaStream_t own = nullptr;  // stream of a request stepped on its own
+  int solo = -1;  // the shared stream its chunk in flight runs on (requests stepped alone)
   bool batched = false;
   int lane = 0;  // batched size class
   int64_t bytes = 0;
-  std::shared_ptr<Event> ev;
   int status = IONTRAP_OK;
   std::vector<double> xo, vo;
   int64_t final_step = 0;
@@ -82,9 +88,14 @@ struct Lane {
   bool inflight = false;
 };
 
+// Chunks of a request stepped alone: at most chunk_steps x (kSoloChunkIons / N)^2 steps.
+constexpr int64_t kSoloChunkIons = 4096;
+
 struct iontrap_server {
   iontrap_server_config cfg{};
   Lane lanes[kLanes];
+  std::vector<Lane> solo;        // the shared streams of the requests stepped alone
+  cudaStream_t admit = nullptr;  // where handles are created
   std::deque<std::unique_ptr<Request>> waiting;
   std::vector<std::unique_ptr<Request>> resident;
   std::map<int64_t, std::unique_ptr<Request>> completed;
@@ -102,8 +113,6 @@ static void retire(iontrap_server* s, std::unique_ptr<Request>& r) {
   if (st && !r->status) r->status = st;
   iontrap_destroy(r->h);
   r->h = nullptr;
-  if (r->own) cudaStreamDestroy(r->own);
-  r->own = nullptr;
   s->bytes_in_use -= r->bytes;
   r->x0.clear();
   r->v0.clear();
@@ -123,16 +132,21 @@ int iontrap_server_create(const iontrap_server_config* cfg, iontrap_server_t** o
   if (s->cfg.mem_budget_bytes <= 0) s->cfg.mem_budget_bytes = (int64_t)2 << 30;
   if (s->cfg.max_resident <= 0) s->cfg.max_resident = 4096;
   if (s->cfg.chunk_steps <= 0) s->cfg.chunk_steps = 100;
-  // stream priorities: the smallest class highest (lower numbers are higher priorities)
+  if (s->cfg.max_parallel <= 0) s->cfg.max_parallel = 3;
+  // stream priorities: the smallest class highest (lower numbers are higher priorities),
+  // the requests stepped alone lowest
   int least = 0, greatest = 0;
   if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) least = greatest = 0;
-  for (int c = 0; c < kLanes; ++c) {
-    const int prio = std::min(least, greatest + c);
-    if (cudaStreamCreateWithPriority(&s->lanes[c].stream, cudaStreamNonBlocking, prio) != cudaSuccess) {
-      for (int d = 0; d < c; ++d) cudaStreamDestroy(s->lanes[d].stream);
-      delete s;
-      return IONTRAP_ECUDA;
-    }
+  bool ok = cudaStreamCreateWithFlags(&s->admit, cudaStreamNonBlocking) == cudaSuccess;
+  for (int c = 0; c < kLanes && ok; ++c)
+    ok = cudaStreamCreateWithPriority(&s->lanes[c].stream, cudaStreamNonBlocking, std::min(least, greatest + c)) ==
+         cudaSuccess;
+  s->solo.resize((size_t)s->cfg.max_parallel);
+  for (Lane& l : s->solo)
+    if (ok) ok = cudaStreamCreateWithPriority(&l.stream, cudaStreamNonBlocking, least) == cudaSuccess;
+  if (!ok) {
+    iontrap_server_destroy(s);
+    return IONTRAP_ECUDA;
   }
   *out = s;
   return IONTRAP_OK;
@@ -174,14 +188,16 @@ int iontrap_server_poll(iontrap_server_t* s, int64_t* completed_ids, int64_t cap
   // 1. finished chunks
   for (Lane& l : s->lanes)
     if (l.inflight && cudaEventQuery(l.ev->ev) == cudaSuccess) l.inflight = false;
+  for (Lane& l : s->solo)
+    if (l.inflight && cudaEventQuery(l.ev->ev) == cudaSuccess) l.inflight = false;
   for (size_t k = 0; k < s->resident.size();) {
     auto& r = s->resident[k];
     if (r->inflight) {
-      const bool fin = r->batched ? !s->lanes[r->lane].inflight : (cudaEventQuery(r->ev->ev) == cudaSuccess);
+      const bool fin = r->batched ? !s->lanes[r->lane].inflight : !s->solo[r->solo].inflight;
       if (fin) {
         r->done += r->inflight;
         r->inflight = 0;
-        r->ev.reset();
+        r->solo = -1;
       }
     }
     if (!r->inflight && (r->done >= r->steps || r->status)) {
@@ -200,18 +216,14 @@ int iontrap_server_poll(iontrap_server_t* s, int64_t* completed_ids, int64_t cap
          (s->bytes_in_use + s->waiting.front()->bytes <= s->cfg.mem_budget_bytes || s->resident.empty())) {
     auto r = std::move(s->waiting.front());
     s->waiting.pop_front();
-    cudaStream_t st = s->lanes[r->lane].stream;
-    if (!r->batched) {
-      if (cudaStreamCreateWithFlags(&r->own, cudaStreamNonBlocking) != cudaSuccess) r->status = IONTRAP_ECUDA;
-      st = r->own;
-    }
-    if (!r->status)
-      r->status = iontrap_create(r->species.data(), (int)r->species.size(), r->soi.data(), r->x0.data(),
-                                 r->has_v0 ? r->v0.data() : nullptr, r->n, &r->p, 0, (void*)st, &r->h);
+    r->status = iontrap_create(r->species.data(), (int)r->species.size(), r->soi.data(), r->x0.data(),
+                               r->has_v0 ? r->v0.data() : nullptr, r->n, &r->p, 0, (void*)s->admit, &r->h);
     if (!r->status && !r->batched) r->status = it::use_nonpersistent_default(r->h);
+    // the batched ones live on their class's stream; the others move at each chunk
+    if (!r->status && r->batched) r->status = it::rebind_stream(r->h, s->lanes[r->lane].stream);
     if (r->status) {  // rejected (unstable trap, bad input, no memory): completes at once
-      if (r->own) cudaStreamDestroy(r->own);
-      r->own = nullptr;
+      if (r->h) iontrap_destroy(r->h);
+      r->h = nullptr;
       ++s->completed_total;
       const int64_t rid = r->id;
       report(rid);
@@ -223,8 +235,8 @@ int iontrap_server_poll(iontrap_server_t* s, int64_t* completed_ids, int64_t cap
     s->bytes_in_use += r->bytes;
     s->resident.push_back(std::move(r));
   }
-  // 3. next chunks: each batched size class together on its stream, the others each on
-  // its own stream
+  // 3. next chunks: each batched size class together on its stream, then the shared
+  // streams of the others, least remaining work first
   for (int c = 0; c < kLanes; ++c) {
     Lane& l = s->lanes[c];
     if (l.inflight) continue;
@@ -249,18 +261,34 @@ int iontrap_server_poll(iontrap_server_t* s, int64_t* completed_ids, int64_t cap
       }
     }
   }
-  for (auto& r : s->resident)
-    if (!r->batched && !r->inflight && r->done < r->steps && !r->status) {
-      const int64_t k = std::min<int64_t>(s->cfg.chunk_steps, r->steps - r->done);
-      const int st = iontrap_step(r->h, k);
-      if (st) {
-        r->status = st;
-        continue;
+  for (size_t q = 0; q < s->solo.size(); ++q) {
+    Lane& l = s->solo[q];
+    if (l.inflight) continue;
+    Request* best = nullptr;
+    double best_work = 0.0;
+    for (auto& r : s->resident)
+      if (!r->batched && !r->inflight && r->done < r->steps && !r->status) {
+        const double work = (double)r->n * (double)r->n * (double)(r->steps - r->done);
+        if (!best || work < best_work) best = r.get(), best_work = work;
       }
-      r->ev = std::make_shared<Event>();
-      cudaEventRecord(r->ev->ev, r->own);
-      r->inflight = k;
+    if (!best) break;
+    const double scale = (double)kSoloChunkIons / (double)best->n;
+    const int64_t chunk =
+        std::max<int64_t>(1, std::min<int64_t>(s->cfg.chunk_steps, (int64_t)(s->cfg.chunk_steps * scale * scale)));
+    const int64_t k = std::min<int64_t>(chunk, best->steps - best->done);
+    int st = it::rebind_stream(best->h, l.stream);
+    if (!st) st = iontrap_step(best->h, k);
+    if (st) {
+      best->status = st;
+      --q;  // the stream is still idle: offer it to the next request
+      continue;
     }
+    l.ev = std::make_shared<Event>();
+    cudaEventRecord(l.ev->ev, l.stream);
+    l.inflight = true;
+    best->inflight = k;
+    best->solo = (int)q;
+  }
   return IONTRAP_OK;
 }
 
@@ -288,15 +316,23 @@ int iontrap_server_stats(const iontrap_server_t* s, iontrap_server_counters* out
 
 void iontrap_server_destroy(iontrap_server_t* s) {
   if (!s) return;
-  for (Lane& l : s->lanes) cudaStreamSynchronize(l.stream);
-  for (auto& r : s->resident) {
-    if (r->own) cudaStreamSynchronize(r->own);
+  for (Lane& l : s->lanes)
+    if (l.stream) cudaStreamSynchronize(l.stream);
+  for (Lane& l : s->solo)
+    if (l.stream) cudaStreamSynchronize(l.stream);
+  for (auto& r : s->resident)
     if (r->h) iontrap_destroy(r->h);
-    if (r->own) cudaStreamDestroy(r->own);
-  }
   for (Lane& l : s->lanes) {
     l.ev.reset();
-    cudaStreamDestroy(l.stream);
+    if (l.stream) cudaStreamDestroy(l.stream);
+  }
+  for (Lane& l : s->solo) {
+    l.ev.reset();
+    if (l.stream) cudaStreamDestroy(l.stream);
+  }
+  if (s->admit) {
+    cudaStreamSynchronize(s->admit);
+    cudaStreamDestroy(s->admit);
   }
   delete s;
 }

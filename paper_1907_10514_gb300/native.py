@@ -66,7 +66,7 @@ class iontrap_config(ctypes.Structure):
 
 class iontrap_server_config(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_int64), ("max_resident", ctypes.c_int32),
-                ("chunk_steps", ctypes.c_int32)]
+                ("chunk_steps", ctypes.c_int32), ("max_parallel", ctypes.c_int32)]
 
 
 class iontrap_server_counters(ctypes.Structure):
@@ -441,8 +441,9 @@ def iontrap_estimate_bytes(n: int, precision: int = IONTRAP_PREC_FP32) -> int:
     return b.value
 
 
-def iontrap_server_create(mem_budget_bytes: int = 0, max_resident: int = 0, chunk_steps: int = 0):
-    cfg = iontrap_server_config(int(mem_budget_bytes), int(max_resident), int(chunk_steps))
+def iontrap_server_create(mem_budget_bytes: int = 0, max_resident: int = 0, chunk_steps: int = 0,
+                          max_parallel: int = 0):
+    cfg = iontrap_server_config(int(mem_budget_bytes), int(max_resident), int(chunk_steps), int(max_parallel))
     s = ctypes.c_void_p()
     _check(_lib.iontrap_server_create(ctypes.byref(cfg), ctypes.byref(s)), "iontrap_server_create")
     return s

@@ -889,14 +889,17 @@ def test_estimate_bytes_matches_handle(it):
                 assert it.iontrap_device_bytes(s.handle) == it.iontrap_estimate_bytes(n, prec)
 
 
-def test_server_results_equal_alone_and_respect_budget(it):
+@pytest.mark.parametrize("max_parallel", [0, 1], ids=["default_streams", "one_stream"])
+def test_server_results_equal_alone_and_respect_budget(it, max_parallel):
     """Continuous batching: requests of different sizes and step budgets (one with an
     unstable trap) submitted while others run, under a memory budget small enough that
     some must wait.  Each result equals the same request run alone through the same
-    kernel path (bitwise), the budget is never exceeded, every request completes."""
+    kernel path (bitwise) -- those stepped alone in chunks of every size (6000 ions: 46
+    steps per chunk) on the shared streams, three or one --, the budget is never exceeded,
+    every request completes."""
     import time
-    sizes = [16, 90, 300, 1100, 2048, 2500, 40, 700, 5000, 64]
-    steps = [250, 130, 310, 120, 100, 150, 90, 210, 100, 180]
+    sizes = [16, 90, 300, 1100, 2048, 2500, 40, 700, 5000, 64, 6000]
+    steps = [250, 130, 310, 120, 100, 150, 90, 210, 100, 180, 120]
     reqs = []
     for k, (n, st) in enumerate(zip(sizes, steps)):
         w = _cloud(n, 500 + k, species=(iongen.CA40, iongen.NH3) if k % 3 == 0 else (iongen.CA40,))
@@ -904,7 +907,8 @@ def test_server_results_equal_alone_and_respect_budget(it):
     bad = _cloud(50, 999)
     bad.trap.q = 0.95  # outside the stability region
     budget = 12 << 20
-    srv = it.iontrap_server_create(mem_budget_bytes=budget, max_resident=6, chunk_steps=100)
+    srv = it.iontrap_server_create(mem_budget_bytes=budget, max_resident=6, chunk_steps=100,
+                                   max_parallel=max_parallel)
     try:
         ids = {}
         done = {}
@@ -942,6 +946,38 @@ def test_server_results_equal_alone_and_respect_budget(it):
                     alone.step(st)
                 xa, va, _, _ = alone.state()
             assert np.array_equal(x, xa) and np.array_equal(v, va), (k, w.n)
+    finally:
+        it.iontrap_server_destroy(srv)
+
+
+def test_server_steps_least_remaining_work_first(it):
+    """Requests the batched kernel does not take share the server's streams: with one
+    stream, the request with the least remaining pair work (N^2 x steps left) is stepped
+    first, so a short request submitted with a long one completes first, both bitwise as
+    alone."""
+    import time
+    long_w, short_w = _cloud(3000, 611), _cloud(2600, 612)
+    srv = it.iontrap_server_create(chunk_steps=100, max_parallel=1)
+    order = []
+    try:
+        rl = it.iontrap_server_submit(srv, long_w.species, long_w.species_of_ion, long_w.x0, long_w.v0,
+                                      it.make_params(long_w.trap), 600)
+        rs = it.iontrap_server_submit(srv, short_w.species, short_w.species_of_ion, short_w.x0, short_w.v0,
+                                      it.make_params(short_w.trap), 60)
+        t0 = time.time()
+        while len(order) < 2:
+            order += it.iontrap_server_poll(srv)
+            assert time.time() - t0 < 120
+            time.sleep(0.0005)
+        assert order == [rs, rl]
+        for rid, w, st in ((rl, long_w, 600), (rs, short_w, 60)):
+            x, v, step, status = it.iontrap_server_result(srv, rid, w.n)
+            assert status == 0 and step == st
+            with _sim(it, w, 0) as alone:
+                alone.set_config(*it.iontrap_default_config(w.n, 0, 0, 0))
+                alone.step(st)
+                xa, va, _, _ = alone.state()
+            assert np.array_equal(x, xa) and np.array_equal(v, va)
     finally:
         it.iontrap_server_destroy(srv)
 
