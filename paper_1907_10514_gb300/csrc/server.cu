@@ -263,31 +263,31 @@ int iontrap_server_poll(iontrap_server_t* s, int64_t* completed_ids, int64_t cap
   }
   for (size_t q = 0; q < s->solo.size(); ++q) {
     Lane& l = s->solo[q];
-    if (l.inflight) continue;
-    Request* best = nullptr;
-    double best_work = 0.0;
-    for (auto& r : s->resident)
-      if (!r->batched && !r->inflight && r->done < r->steps && !r->status) {
-        const double work = (double)r->n * (double)r->n * (double)(r->steps - r->done);
-        if (!best || work < best_work) best = r.get(), best_work = work;
+    while (!l.inflight) {  // a request whose launch fails is retired; the stream goes to the next
+      Request* best = nullptr;
+      double best_work = 0.0;
+      for (auto& r : s->resident)
+        if (!r->batched && !r->inflight && r->done < r->steps && !r->status) {
+          const double work = (double)r->n * (double)r->n * (double)(r->steps - r->done);
+          if (!best || work < best_work) best = r.get(), best_work = work;
+        }
+      if (!best) return IONTRAP_OK;
+      const double scale = (double)kSoloChunkIons / (double)best->n;
+      const int64_t chunk = std::max<int64_t>(
+          1, std::min<int64_t>(s->cfg.chunk_steps, (int64_t)(s->cfg.chunk_steps * scale * scale)));
+      const int64_t k = std::min<int64_t>(chunk, best->steps - best->done);
+      int st = it::rebind_stream(best->h, l.stream);
+      if (!st) st = iontrap_step(best->h, k);
+      if (st) {
+        best->status = st;
+        continue;
       }
-    if (!best) break;
-    const double scale = (double)kSoloChunkIons / (double)best->n;
-    const int64_t chunk =
-        std::max<int64_t>(1, std::min<int64_t>(s->cfg.chunk_steps, (int64_t)(s->cfg.chunk_steps * scale * scale)));
-    const int64_t k = std::min<int64_t>(chunk, best->steps - best->done);
-    int st = it::rebind_stream(best->h, l.stream);
-    if (!st) st = iontrap_step(best->h, k);
-    if (st) {
-      best->status = st;
-      --q;  // the stream is still idle: offer it to the next request
-      continue;
+      l.ev = std::make_shared<Event>();
+      cudaEventRecord(l.ev->ev, l.stream);
+      l.inflight = true;
+      best->inflight = k;
+      best->solo = (int)q;
     }
-    l.ev = std::make_shared<Event>();
-    cudaEventRecord(l.ev->ev, l.stream);
-    l.inflight = true;
-    best->inflight = k;
-    best->solo = (int)q;
   }
   return IONTRAP_OK;
 }
