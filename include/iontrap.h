@@ -111,6 +111,9 @@ typedef struct iontrap iontrap_t;
  *   step0                  index of the initial state: t0 = step0 dt, noise counter step0
  *   cuda_stream            cudaStream_t to run on, or NULL for a stream the handle owns
  * Copies the inputs to the device, evaluates a_{step0} and returns the handle in *out.
+ * The handle's device buffers come from a per-device pool of CUDA's stream-ordered
+ * allocator, allocated and later freed in order on the handle's stream (neither
+ * synchronises the device); the pool keeps up to 4 GiB of freed memory for reuse.
  * EINVAL on bad arguments, EUNSTABLE if the trap cannot hold a species (unless
  * IONTRAP_ALLOW_UNSTABLE), ENOMEM / ECUDA on device failure.  Synchronous. */
 int iontrap_create(const iontrap_species *species, int n_species,
