@@ -950,6 +950,31 @@ def test_server_results_equal_alone_and_respect_budget(it, max_parallel):
         it.iontrap_server_destroy(srv)
 
 
+def test_handle_create_and_destroy_do_not_wait_for_other_streams(it):
+    """Handle memory comes from a stream-ordered pool: creating and destroying a handle
+    waits for nothing but its own stream (cudaMalloc / cudaFree would synchronise the
+    device), so the serving loop's admissions and retirements do not stall the requests
+    running beside them.  A 20 000-step run on one stream is still in flight after another
+    handle has been created, stepped, read and destroyed, and ends with the bits of the
+    same run done alone."""
+    import torch
+    w = _cloud(4096, 77, species=(iongen.CA40,))
+    small = _cloud(300, 78)
+    st = torch.cuda.Stream()
+    with it.Simulation(w.species, w.species_of_ion, w.x0, w.v0, it.make_params(w.trap), stream=st) as big:
+        big.step(20000)  # ~0.26 s of cooperative launches queued on st
+        with _sim(it, small, 0) as s:
+            s.step(10)
+            s.state()
+        assert not st.query()  # the long run is still going
+        big.sync()
+        xb, vb, sb, _ = big.state()
+    with _sim(it, w, 0) as alone:
+        alone.step(20000)
+        xa, va, sa, _ = alone.state()
+    assert sb == sa == 20000 and np.array_equal(xb, xa) and np.array_equal(vb, va)
+
+
 def test_server_steps_least_remaining_work_first(it):
     """Requests the batched kernel does not take share the server's streams: with one
     stream, the request with the least remaining pair work (N^2 x steps left) is stepped
