@@ -365,9 +365,10 @@ int iontrap_set_config(iontrap_t *h, const iontrap_config *cfg);
 
 /* The configuration a handle of n ions in the given precision form, with the given
  * IONTRAP_* flags, starts with on the current device when no autotuned entry applies.
- * allow_persistent = 0 excludes the grid-persistent form (fused = 4): the serving loop
- * gives that configuration to the requests it runs on their own streams, since a
- * cooperative grid holding every SM would serialise against the others.  EINVAL for
+ * allow_persistent = 0 excludes the persistent forms (fused = 4 and 5): the serving loop
+ * gives that configuration to the requests the batched kernel does not take, which it
+ * steps on shared streams beside the batches, since a cooperative grid holding every SM
+ * would serialise against them.  EINVAL for
  * n < 1 or an unknown precision; ECUDA without a device. */
 int iontrap_default_config(int64_t n, int precision, uint32_t flags, int allow_persistent, iontrap_config *cfg);
 
