@@ -895,11 +895,12 @@ def test_server_results_equal_alone_and_respect_budget(it, max_parallel):
     unstable trap) submitted while others run, under a memory budget small enough that
     some must wait.  Each result equals the same request run alone through the same
     kernel path (bitwise) -- those stepped alone in chunks of every size (6000 ions: 46
-    steps per chunk) on the shared streams, three or one --, the budget is never exceeded,
-    every request completes."""
+    steps per chunk) on the shared streams, three or one, FP64-form requests among them --,
+    the budget is never exceeded, every request completes."""
     import time
-    sizes = [16, 90, 300, 1100, 2048, 2500, 40, 700, 5000, 64, 6000]
-    steps = [250, 130, 310, 120, 100, 150, 90, 210, 100, 180, 120]
+    sizes = [16, 90, 300, 1100, 2048, 2500, 40, 700, 5000, 64, 6000, 200, 1500]
+    steps = [250, 130, 310, 120, 100, 150, 90, 210, 100, 180, 120, 140, 60]
+    prec = [0] * 11 + [1, 1]  # the last two in the plain FP64 form (never batched)
     reqs = []
     for k, (n, st) in enumerate(zip(sizes, steps)):
         w = _cloud(n, 500 + k, species=(iongen.CA40, iongen.NH3) if k % 3 == 0 else (iongen.CA40,))
@@ -914,7 +915,7 @@ def test_server_results_equal_alone_and_respect_budget(it, max_parallel):
         done = {}
         for k, (w, st) in enumerate(reqs[:5]):
             ids[it.iontrap_server_submit(srv, w.species, w.species_of_ion, w.x0, w.v0,
-                                         it.make_params(w.trap), st)] = k
+                                         it.make_params(w.trap, precision=prec[k]), st)] = k
         bad_id = it.iontrap_server_submit(srv, bad.species, bad.species_of_ion, bad.x0, bad.v0,
                                           it.make_params(bad.trap), 100)
         polls, t0 = 0, time.time()
@@ -922,7 +923,7 @@ def test_server_results_equal_alone_and_respect_budget(it, max_parallel):
             if polls == 3:  # later arrivals join while the first ones run
                 for k, (w, st) in enumerate(reqs[5:], start=5):
                     ids[it.iontrap_server_submit(srv, w.species, w.species_of_ion, w.x0, w.v0,
-                                                 it.make_params(w.trap), st)] = k
+                                                 it.make_params(w.trap, precision=prec[k]), st)] = k
             for rid in it.iontrap_server_poll(srv):
                 done[rid] = True
             stats = it.iontrap_server_stats(srv)
@@ -937,11 +938,11 @@ def test_server_results_equal_alone_and_respect_budget(it, max_parallel):
             w, st = reqs[k]
             x, v, step, status = it.iontrap_server_result(srv, rid, w.n)
             assert status == 0 and step == st
-            with _sim(it, w, 0) as alone:
-                if w.n <= 2048:
+            with _sim(it, w, prec[k]) as alone:
+                if w.n <= 2048 and prec[k] == 0:
                     it.iontrap_step_many([alone.handle], [st])
-                else:  # the server's configuration for requests on their own streams
-                    alone.set_config(*it.iontrap_default_config(w.n, 0, 0, 0))
+                else:  # the server's configuration for requests stepped alone
+                    alone.set_config(*it.iontrap_default_config(w.n, prec[k], 0, 0))
                     assert alone.config()[4] < 4
                     alone.step(st)
                 xa, va, _, _ = alone.state()
